@@ -1,0 +1,313 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each test names what fixes the expected value: scipy's dense expm of the Theorem 1 augmented matrix,
+the tail of eq 15, DST-I closed forms, phi closed forms / quadrature of eq 3, A = 0, p = 0, A = lambda I,
+diagonal A, the Arnoldi-like relation eq 30, Theorem 2, and full-Arnoldi equivalence.
+"""
+from math import factorial
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+import oracle
+from paper_1804_05126_gb300 import workloads as W
+from tests.exact import augmented, exact_dense, exact_dst_1d, exact_dst_3d, phi
+from tests.golden_util import paper_constants
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def err_ok(w, ref, tol, factor=10.0):
+    """Reading c9: absolute 2-norm error within factor*tol*max(1, ||w||)."""
+    return np.linalg.norm(w - ref) <= factor * tol * max(1.0, np.linalg.norm(ref))
+
+
+# ---------------------------------------------------------------- phi functions and eq 3
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("z", [-643.0, -20.0, -1.5, -0.3, 0.0, 0.7, 2.5])
+def test_phi_helper_matches_quadrature_of_eq3(k, z):
+    val, _ = scipy.integrate.quad(lambda t: np.exp(z * (1 - t)) * t ** (k - 1) / factorial(k - 1), 0.0, 1.0,
+                                  epsabs=0, epsrel=1e-13, limit=200)
+    assert abs(phi(k, np.array([z]))[0] - val) <= 1e-12 * max(1.0, abs(val))
+
+
+def test_phi_recurrence_continuity_at_switch():
+    # series (|z| < 1) and recurrence (|z| >= 1) agree on both sides of the switch point
+    for k in range(5):
+        lo, hi = phi(k, np.array([-0.999999999])), phi(k, np.array([-1.0]))
+        assert abs(lo - hi)[0] < 1e-8
+
+
+# ---------------------------------------------------------------- dense exponential (section 3.3.1)
+@pytest.mark.parametrize("scale", [1e-3, 0.2, 1.0, 5.0, 40.0, 700.0])
+def test_expm_matches_scipy_random(scale):
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 5, 17, 40):
+        # spectrum shifted left so exp(a) stays finite at every scale
+        a = rng.standard_normal((n, n)) * scale / np.sqrt(n) - scale * np.eye(n)
+        ref = scipy.linalg.expm(a)
+        assert rel(oracle.expm(a), ref) < 1e-12 * max(1.0, scale)
+
+
+def test_expm_diagonal_closed_form():
+    d = np.array([-500.0, -3.0, 0.0, 0.5, 2.0])
+    # e^-500 comes out of 7 squarings: its relative error grows with 2^s, still far below 1e-11
+    assert np.allclose(np.diag(oracle.expm(np.diag(d))), np.exp(d), rtol=1e-11, atol=0)
+
+
+def test_expm_nilpotent_closed_form():
+    # shift matrix K of Theorem 1: e^{tau K} is eq 17 (entries tau^k/k! on the k-th superdiagonal)
+    p, tau = 5, 0.7
+    K = np.diag(np.ones(p - 1), 1)
+    F = oracle.expm(tau * K)
+    for i in range(p):
+        for j in range(p):
+            want = tau ** (j - i) / factorial(j - i) if j >= i else 0.0
+            assert abs(F[i, j] - want) < 1e-15
+
+
+def test_expm_hessenberg_augmented_block_eq38():
+    # eq 38: exp(tau [[H, e1], [0, 0]]) carries tau*phi_1(tau H) e1 in its last column
+    rng = np.random.default_rng(3)
+    m, tau = 12, 0.4
+    H = np.triu(rng.standard_normal((m, m)), -1)
+    Ht = np.zeros((m + 1, m + 1))
+    Ht[:m, :m] = H
+    Ht[0, m] = 1.0
+    F = oracle.expm(tau * Ht)
+    # tau phi_1(tau H) e1 = integral_0^tau e^{sH} e1 ds, computed by scipy on the same block structure
+    ref = scipy.linalg.expm(tau * Ht)
+    assert rel(F, ref) < 1e-13
+    assert abs(F[m, m] - 1.0) < 1e-15 and np.all(F[m, :m] == 0.0)
+
+
+# ---------------------------------------------------------------- Theorem 1 (test helpers pinned)
+def test_theorem1_augmented_exponential_top_and_tail():
+    rng = np.random.default_rng(11)
+    n, p, tau = 6, 4, 0.3
+    a = -np.diag(rng.uniform(0.5, 5.0, n)) + 0.1 * rng.standard_normal((n, n))
+    a = 0.5 * (a + a.T)
+    b = rng.standard_normal((p + 1, n))
+    y = exact_dense(a, b, tau, full=True)
+    lam, Q = np.linalg.eigh(a)
+    want = sum(Q @ (tau**k * phi(k, tau * lam) * (Q.T @ b[k])) for k in range(p + 1))
+    assert rel(y[:n], want) < 1e-12                      # eq 14
+    tail = [tau ** (p - 1 - t) / factorial(p - 1 - t) for t in range(p)]
+    assert np.allclose(y[n:], tail, rtol=1e-14, atol=1e-16)  # eq 15
+
+
+# ---------------------------------------------------------------- KIOPS against exact references
+def _dense_op(a):
+    return {"kind": "dense", "n": a.shape[0], "a": np.ascontiguousarray(a)}
+
+
+def test_kiops_lap1d_full_config_vs_dense_expm_and_dst():
+    P = W.problem_lap1d()  # N = 400, p = 2, tau = 1e-3, tol = 1e-8
+    w, st, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+    assert st["status"] == 0
+    A = oracle.dense_matrix(P.op)
+    ref = exact_dense(A, P.b, P.tau)
+    ref_dst = exact_dst_1d(P.n, 1.0, P.b, P.tau)
+    assert rel(ref, ref_dst) < 1e-11                       # two independent exact references agree
+    assert err_ok(w, ref, P.tol)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-8, 1e-10])
+def test_kiops_dense_random_negative_spectrum(tol):
+    rng = np.random.default_rng(5)
+    n, p = 30, 3
+    a = -np.diag(rng.uniform(0.0, 200.0, n)) + 5.0 * rng.standard_normal((n, n))
+    b = rng.standard_normal((p + 1, n))
+    for tau in (1e-3, 1e-2, 0.1):
+        w, st, _ = oracle.kiops(_dense_op(a), tau, b, tol, m_min=5, m_max=24)
+        assert st["status"] == 0
+        assert err_ok(w, exact_dense(a, b, tau), tol)
+
+
+def test_kiops_adr2d_small_vs_dense_expm():
+    P = W.problem_adr2d(n=10, seed=42)
+    w, st, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+    assert st["status"] == 0
+    assert err_ok(w, exact_dense(oracle.dense_matrix(P.op), P.b, P.tau), P.tol)
+
+
+def test_kiops_gray_scott_small_vs_dense_expm():
+    P = W.problem_gray_scott(n=6, seed=43, precision="fp64")
+    P.tau = 50.0  # makes the diffusion visible on a tiny grid (||tau J|| ~ 1e-1..1e1)
+    w, st, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+    assert st["status"] == 0
+    assert err_ok(w, exact_dense(oracle.dense_matrix(P.op), P.b, P.tau), P.tol)
+
+
+def test_kiops_3d_diffusion_reaction_vs_dst():
+    n, shift, tau, tol = 9, -20.0, 5e-3, 1e-9
+    op = W.adr3d(n, shift)
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal((4, n**3))
+    w, st, _ = oracle.kiops(op, tau, b, tol)
+    assert st["status"] == 0
+    assert err_ok(w, exact_dst_3d(n, 1.0, shift, b, tau), tol)
+
+
+def test_kiops_3d_advection_vs_dense():
+    op = W.adr3d(5, -10.0, adv=(8.0, -6.0, 3.0))
+    rng = np.random.default_rng(10)
+    b = rng.standard_normal((3, 125))
+    w, st, _ = oracle.kiops(op, 0.02, b, 1e-9)
+    assert err_ok(w, exact_dense(oracle.dense_matrix(op), b, 0.02), 1e-9)
+
+
+def test_kiops_diagonal_closed_form():
+    rng = np.random.default_rng(4)
+    lam = -np.sort(rng.uniform(0.0, 1e3, 50))
+    b = rng.standard_normal((5, 50))
+    tau, tol = 0.01, 1e-10
+    w, st, _ = oracle.kiops(_dense_op(np.diag(lam)), tau, b, tol)
+    want = sum(tau**k * phi(k, tau * lam) * b[k] for k in range(5))
+    assert err_ok(w, want, tol)
+
+
+def test_kiops_zero_matrix_taylor_and_breakdown():
+    rng = np.random.default_rng(6)
+    n, p, tau = 20, 4, 0.8
+    b = rng.standard_normal((p + 1, n))
+    want = sum(tau**k / factorial(k) * b[k] for k in range(p + 1))
+    # IOP(2): the Krylov space has dimension p+1, but a length-2 orthogonalisation cannot see that
+    w, st, tr = oracle.kiops(_dense_op(np.zeros((n, n))), tau, b, 1e-10)
+    assert rel(w, want) < 1e-11 and st["substeps"] == 1
+    # orthogonalising against >= p+1 vectors detects the invariant subspace: happy breakdown at j = p+1
+    w, st, tr = oracle.kiops(_dense_op(np.zeros((n, n))), tau, b, 1e-10, m_o=p + 1)
+    assert rel(w, want) < 1e-13
+    assert tr[0]["breakdown"] and tr[0]["j"] == p + 1 and tr[0]["omega"] == 0.0 and st["substeps"] == 1
+
+
+def test_kiops_p0_is_plain_exponential():
+    rng = np.random.default_rng(8)
+    a = -np.diag(rng.uniform(0, 50, 25)) + rng.standard_normal((25, 25))
+    b = rng.standard_normal((1, 25))
+    w, st, _ = oracle.kiops(_dense_op(a), 0.05, b, 1e-10)
+    assert err_ok(w, scipy.linalg.expm(0.05 * a) @ b[0], 1e-10)
+
+
+def test_kiops_scalar_multiple_of_identity():
+    lam, n, p, tau = -37.0, 15, 3, 0.02
+    rng = np.random.default_rng(12)
+    b = rng.standard_normal((p + 1, n))
+    w, _, _ = oracle.kiops(_dense_op(lam * np.eye(n)), tau, b, 1e-11)
+    want = sum(tau**k * phi(k, np.array([tau * lam]))[0] * b[k] for k in range(p + 1))
+    assert rel(w, want) < 1e-10
+
+
+def test_kiops_tau_zero_returns_b0():
+    P = W.problem_lap1d(n=50)
+    w, st, _ = oracle.kiops(P.op, 0.0, P.b, P.tol)
+    assert np.array_equal(w, P.b[0]) and st["matvecs"] == 0
+
+
+def test_kiops_normalisation_has_no_effect_in_exact_arithmetic():
+    P = W.problem_adr2d(n=12, seed=3)
+    w1, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, normalize=True)
+    w0, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, normalize=False)
+    ref = exact_dense(oracle.dense_matrix(P.op), P.b, P.tau)
+    assert err_ok(w1, ref, P.tol) and err_ok(w0, ref, P.tol)
+
+
+def test_kiops_full_arnoldi_equivalence():
+    P = W.problem_adr2d(n=10, seed=5)
+    ref = exact_dense(oracle.dense_matrix(P.op), P.b, P.tau)
+    w_iop, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_o=2)
+    w_arn, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_o=200)
+    assert err_ok(w_iop, ref, P.tol) and err_ok(w_arn, ref, P.tol)
+
+
+def test_kiops_substepping_when_m_max_is_small():
+    P = W.problem_lap1d(n=200)
+    w, st, tr = oracle.kiops(P.op, P.tau, P.b, P.tol, m_min=5, m_max=20)
+    assert st["substeps"] > 1
+    ref = exact_dst_1d(P.n, 1.0, P.b, P.tau)
+    assert err_ok(w, ref, P.tol)
+
+
+# ---------------------------------------------------------------- IOP invariants (eq 30, Thm 2)
+def _iop_case(m_o=2, m=25):
+    P = W.problem_adr2d(n=9, seed=21)
+    A = oracle.dense_matrix(P.op)
+    At, v = augmented(A, P.b)
+    V, H, j, bd = oracle.iop(P.op, P.b, v, m, m_o=m_o)
+    return At, v, V, H, j, bd
+
+
+def test_iop_arnoldi_like_relation_eq30():
+    At, v, V, H, j, bd = _iop_case()
+    assert not bd and j == 25
+    Vm, Hm = V[:, :j], H[:j, :j]
+    R = At @ Vm - Vm @ Hm - H[j, j - 1] * np.outer(V[:, j], np.eye(j)[j - 1])
+    assert np.linalg.norm(R) <= 1e-12 * np.linalg.norm(At, 2) * np.sqrt(j)
+
+
+def test_iop_theorem2_polynomial_exactness():
+    At, v, V, H, j, bd = _iop_case(m=16)
+    beta = np.linalg.norm(v)
+    Vm, Hm = V[:, :j], H[:j, :j]
+    x = v.copy()
+    e1 = np.eye(j)[0]
+    hk = e1.copy()
+    scale = 1.0
+    for k in range(1, j - 1):  # degree k < m-1
+        x = At @ x
+        hk = Hm @ hk
+        scale = np.linalg.norm(x)
+        assert np.linalg.norm(x - beta * Vm @ hk) <= 1e-9 * scale
+
+
+def test_iop_local_orthogonality_and_unit_norm():
+    At, v, V, H, j, bd = _iop_case(m_o=2, m=30)
+    for c in range(j):
+        assert abs(np.linalg.norm(V[:, c]) - 1.0) < 1e-13
+        if c + 1 <= j:
+            assert abs(V[:, c] @ V[:, c + 1]) < 1e-12
+        if c + 2 <= j:
+            assert abs(V[:, c] @ V[:, c + 2]) < 1e-12
+    # H is tridiagonal for m_o = 2 (rows j-1..j+1 only)
+    assert np.all(np.triu(H[:j, :j], 2) == 0)
+
+
+def test_iop_full_orthogonalisation_is_orthonormal():
+    At, v, V, H, j, bd = _iop_case(m_o=40, m=30)
+    Q = V[:, : j + 1]
+    assert np.linalg.norm(Q.T @ Q - np.eye(j + 1)) < 1e-10
+
+
+# ---------------------------------------------------------------- Algorithm 4 decision properties
+def test_trace_obeys_acceptance_and_clipping_rules():
+    P = W.problem_lap1d(n=300)
+    _, st, tr = oracle.kiops(P.op, P.tau, P.b, P.tol, m_max=40, m_min=10)
+    assert st["status"] == 0 and st["substeps"] >= 2
+    for t in tr:
+        assert t["accepted"] == (t["omega"] <= paper_constants()["delta"])  # eq 39
+        if not t["breakdown"] and t["j"] < 40:                         # vary m (section 3.6.2)
+            assert t["tau_new"] == t["tau"]
+            assert int(np.floor(0.75 * t["j"])) <= t["m_new"] <= int(np.ceil(4 * t["j"] / 3)) or t["m_new"] in (10, 40)
+            if not t["accepted"]:
+                assert t["m_new"] > t["j"]
+        elif not t["breakdown"]:                                       # vary tau at m_max (3.6.1)
+            remaining = P.tau - (t["t_now"] + t["tau"] if t["accepted"] else t["t_now"])
+            assert t["tau_new"] <= 5 * t["tau"] * (1 + 1e-15)
+            assert t["tau_new"] >= t["tau"] / 5 * (1 - 1e-15) or t["tau_new"] == remaining
+            if not t["accepted"]:
+                assert t["tau_new"] < t["tau"] and t["m_new"] == 40
+    assert abs(sum(t["tau"] for t in tr if t["accepted"]) - P.tau) <= 1e-15 * P.tau * len(tr)
+
+
+def test_matvec_count_equals_basis_growth():
+    P = W.problem_lap1d(n=300)
+    _, st, tr = oracle.kiops(P.op, P.tau, P.b, P.tol, m_max=40)
+    # every substep builds its basis from zero; rejections extend it: matvecs = sum of final j per substep
+    last_j = {}
+    for t in tr:
+        last_j[t["substep"]] = t["j"]
+    assert st["matvecs"] == sum(last_j.values())
