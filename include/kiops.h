@@ -1,0 +1,208 @@
+/*
+ * kiops.h — C ABI of the GB300 (sm_103a) KIOPS solver.
+ *
+ * Computes  w = sum_{k=0}^{p} tau^k phi_k(tau A) b_k                        (paper eq 12 / eq 20)
+ * with the adaptive Krylov method KIOPS of Gaudreault, Rainwater & Tokman, "KIOPS: A fast adaptive
+ * Krylov subspace solver for exponential integrators", J. Comput. Phys. 372 (2018):
+ *   - one exponential of the augmented matrix A~ = [[A, B], [0, K]], B = [b_p..b_1]   (Theorem 1, eq 13)
+ *   - Krylov basis by incomplete orthogonalisation of length m_o                      (Algorithm 2)
+ *   - projection beta V_m exp(tau H~) e_1 with H~ = [[H_m, e_1], [0, 0]]             (eqs 33, 37, 38)
+ *   - a-posteriori estimate and acceptance omega <= 1.4                              (eqs 36, 39)
+ *   - adaptive substep tau and Krylov dimension m                                    (Alg 1, Alg 4, 3.6)
+ *   - exact tail reset and power-of-two scaling of B                                 (section 3.7)
+ * Only Task II (a single output time, eq 12) is provided.
+ *
+ * Conventions for every entry point
+ *   - Return value: KIOPS_OK or an error status; kiops_last_error(ctx) holds a message for the most
+ *     recent failure on that context.  No entry point aborts the process.
+ *   - "device" pointers are CUDA device (or managed) addresses on the context's device; "host" pointers
+ *     are ordinary host memory.  The caller owns every input and output buffer; the library borrows
+ *     them for the duration of the call (operators borrow theirs until kiops_op_destroy).
+ *   - Vectors of length N are contiguous FP64 arrays in the operator's unknown ordering.
+ *   - The context owns its device workspace (Krylov basis, small dense matrices, barrier words).  It is
+ *     allocated with cudaMalloc on first use and grown on demand, unless the caller attaches a buffer
+ *     with kiops_attach_workspace.
+ *   - A context is used by one host thread at a time.  Work is issued on cfg.stream; calls return after
+ *     the work has completed (they synchronise that stream).
+ */
+#ifndef KIOPS_H
+#define KIOPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KIOPS_MAX_P 16   /* largest p (number of phi terms beyond phi_0) */
+#define KIOPS_MAX_M 256  /* largest m_max (Krylov dimension cap) */
+
+typedef enum {
+  KIOPS_OK = 0,
+  KIOPS_EINVAL = 1,    /* invalid argument (NULL pointer, p out of range, tol <= 0, tau < 0, ...) */
+  KIOPS_ENOMEM = 2,    /* device memory or attached workspace too small */
+  KIOPS_ENOTCONV = 3,  /* max_substeps / max_iterations reached before T_end */
+  KIOPS_ETIMEOUT = 4,  /* a device-side wait exceeded cfg.timeout_s; the result is invalid */
+  KIOPS_ECUDA = 5,     /* a CUDA runtime call failed; see kiops_last_error */
+  KIOPS_EBUSY = 6      /* the context is in use */
+} kiops_status;
+
+typedef enum {
+  KIOPS_FP64 = 0,        /* basis, matvec and all reductions in FP64 */
+  KIOPS_FP32_BASIS = 1   /* basis and matvec in FP32; dot products, norms, H, exponential and control in FP64 */
+} kiops_precision;
+
+typedef enum {
+  KIOPS_ENGINE_AUTO = 0, /* grid engine for large N, single-CTA engine for small N */
+  KIOPS_ENGINE_GRID = 1, /* one persistent cooperative kernel over the whole GPU per solve */
+  KIOPS_ENGINE_CTA = 2   /* one thread block per solve (used for batches) */
+} kiops_engine;
+
+typedef struct {
+  int device;              /* CUDA device ordinal (default 0) */
+  void* stream;            /* cudaStream_t to issue work on; NULL = the legacy default stream */
+  int m_min, m_max;        /* Krylov dimension bounds (Algorithm 1 defaults 10, 128); m_max <= KIOPS_MAX_M */
+  int normalize_B;         /* section 3.7 power-of-two scaling of B (default 1) */
+  double breakdown_tol;    /* happy breakdown when ||x|| <= breakdown_tol * ||A~ v_j|| (default 1e-12) */
+  int64_t max_substeps;    /* accepted substeps before KIOPS_ENOTCONV (default 1e6) */
+  int64_t max_iterations;  /* accepted + rejected iterations before KIOPS_ENOTCONV (default 1e5) */
+  double timeout_s;        /* limit on any single device-side wait (default 10 s) */
+  int engine;              /* kiops_engine (default AUTO) */
+  int grid_blocks;         /* grid engine block count; 0 = as many as are co-resident */
+} kiops_config;
+
+typedef struct {
+  int64_t substeps;        /* accepted substeps */
+  int64_t rejected;        /* rejected iterations */
+  int64_t matvecs;         /* applications of A~ (Algorithm 2 line 4), basis extensions included */
+  int64_t iterations;      /* accepted + rejected */
+  int64_t expm_calls;      /* small dense exponentials (one per iteration) */
+  int m_last;              /* Krylov dimension suggested for the next call (warm start, section 3.6) */
+  int engine;              /* engine that ran the solve */
+  int grid_blocks;         /* blocks of the launch */
+  int status;              /* kiops_status of the device run */
+  double err_est;          /* last error estimate eps_m (eq 36) */
+} kiops_stats;
+
+/* One record per iteration (accepted or rejected) when a trace buffer is given. */
+typedef struct {
+  int64_t substep;
+  int j;                   /* Krylov dimension of the iteration */
+  int accepted;
+  int breakdown;
+  int m_new;               /* Algorithm 4 suggestion */
+  double tau, t_now, eps, omega, tau_new;
+} kiops_trace_rec;
+
+typedef struct kiops_ctx kiops_ctx;
+typedef struct kiops_op kiops_op;
+
+/* 5-point 2D stencil (1 or 2 species) with a pointwise coupling block: unknowns species-blocked
+ * [u; v], each x-fastest (index = s*nx*ny + iy*nx + ix).  For species s:
+ *   (A x)_s(ix,iy) = coef[s][0] x_s(ix,iy) + coef[s][1] x_s(ix-1,iy) + coef[s][2] x_s(ix+1,iy)
+ *                  + coef[s][3] x_s(ix,iy-1) + coef[s][4] x_s(ix,iy+1) + sum_r diag[s][r][pt] x_r(ix,iy)
+ * Outside the grid x = 0 (periodic = 0, homogeneous Dirichlet) or indices wrap (periodic = 1).
+ * diag[s][r] are device pointers of nx*ny FP64 values or NULL (= 0).  This covers the Jacobians of the
+ * paper's 2D ADR and Gray-Scott test problems (section 4). */
+typedef struct {
+  int64_t nx, ny;
+  int nspecies;            /* 1 or 2 */
+  int periodic;
+  double coef[2][5];
+  const double* diag[2][2];
+} kiops_stencil2d_desc;
+
+/* 7-point 3D stencil, one species, x-fastest (index = (iz*ny + iy)*nx + ix):
+ *   (A x)(i) = c[0] x(i) + c[1] x(i-ex) + c[2] x(i+ex) + c[3] x(i-ey) + c[4] x(i+ey) + c[5] x(i-ez)
+ *            + c[6] x(i+ez) + diag[i] x(i);  diag is a device pointer of N FP64 values or NULL. */
+typedef struct {
+  int64_t nx, ny, nz;
+  int periodic;
+  double coef[7];
+  const double* diag;
+} kiops_stencil3d_desc;
+
+/* One solve of a batch (kiops_solve_batch). */
+typedef struct {
+  const kiops_op* A;
+  double tau;
+  int p;
+  const double* const* b;  /* host array of p+1 device pointers b_0..b_p (natural order) */
+  double tol;
+  int m_init;
+  int m_o;
+  kiops_precision prec;
+  double* w;               /* device, N */
+} kiops_request;
+
+/* Defaults: m_min 10, m_max 128, normalize_B 1, breakdown_tol 1e-12 (Algorithm 1 line 1, section 3.7). */
+kiops_status kiops_config_default(kiops_config* cfg);
+
+/* Constants of the method as implemented: out[0..5] = delta (eq 39), gamma (eq 44), gamma_max
+ * (Algorithm 4), kappa default (section 3.6.2), tau clip factor 5 (section 3.6.1), m_o default 2. */
+kiops_status kiops_constants(double out[6]);
+
+/* Create a context on cfg->device (cfg == NULL: defaults).  *ctx is set on success. */
+kiops_status kiops_create(kiops_ctx** ctx, const kiops_config* cfg);
+kiops_status kiops_destroy(kiops_ctx* ctx);
+const char* kiops_last_error(const kiops_ctx* ctx);
+const char* kiops_status_string(kiops_status s);
+
+/* Attach a caller-owned device buffer of `bytes` bytes as the workspace (NULL detaches; the context then
+ * allocates its own).  kiops_workspace_size reports the bytes a solve needs. */
+kiops_status kiops_attach_workspace(kiops_ctx* ctx, void* dptr, size_t bytes);
+kiops_status kiops_workspace_size(kiops_ctx* ctx, const kiops_op* A, int p, int m_o, kiops_precision prec,
+                                  size_t* bytes);
+
+/* Operators (the matrix A of eq 12, applied matrix-free, Algorithm 2 lines 4-6).
+ * CSR: n x n, rowptr[n+1], colind[nnz] (int32), vals[nnz] (FP64), all device pointers, borrowed. */
+kiops_status kiops_op_csr(kiops_ctx* ctx, kiops_op** op, int64_t n, int64_t nnz, const int32_t* rowptr,
+                          const int32_t* colind, const double* vals);
+kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stencil2d_desc* desc);
+kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stencil3d_desc* desc);
+kiops_status kiops_op_destroy(kiops_op* op);
+int64_t kiops_op_size(const kiops_op* op);
+
+/* y = A x (device vectors of length N) — the operator alone, for checks. */
+kiops_status kiops_op_apply(kiops_ctx* ctx, const kiops_op* A, const double* x, double* y);
+
+/* The solve (Algorithm 1, Task II, T = [tau]).
+ *   tau     >= 0 (tau == 0 returns w = b_0 without any matvec)
+ *   p       0..KIOPS_MAX_P
+ *   b       host array of p+1 DEVICE pointers b_0..b_p, each N FP64 values (natural order)
+ *   tol     > 0, absolute tolerance of eq 39
+ *   m_init  >= 1, first Krylov dimension (clipped to [m_min, m_max], Algorithm 1 line 3)
+ *   m_o     >= 1, orthogonalisation length (2 = the paper's IOP; >= m_max = full Arnoldi)
+ *   prec    KIOPS_FP64 or KIOPS_FP32_BASIS
+ *   w       DEVICE output of N FP64 values (may alias b[0])
+ *   stats   host, may be NULL
+ * Errors: EINVAL for bad arguments, ENOMEM, ENOTCONV, ETIMEOUT, ECUDA. */
+kiops_status kiops_solve(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b, double tol,
+                         int m_init, int m_o, kiops_precision prec, double* w, kiops_stats* stats);
+
+/* kiops_solve with a per-iteration trace (host buffer of trace_cap records; *trace_len = records written). */
+kiops_status kiops_solve_traced(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b,
+                                double tol, int m_init, int m_o, kiops_precision prec, double* w,
+                                kiops_stats* stats, kiops_trace_rec* trace, int64_t trace_cap,
+                                int64_t* trace_len);
+
+/* Same as kiops_solve but b (p+1 pointers to N values each) and w are HOST buffers; the host-device
+ * copies happen inside the call (pinned staging owned by the context). */
+kiops_status kiops_solve_host(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b_host,
+                              double tol, int m_init, int m_o, kiops_precision prec, double* w_host,
+                              kiops_stats* stats);
+
+/* Independent solves in one launch, one thread block per request (single-CTA engine). stats: host array
+ * of `count` entries or NULL.  Every request's operator must belong to ctx. */
+kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats);
+
+/* Dense exponential F = exp(A) of an n x n row-major FP64 matrix (device pointers), n <= KIOPS_MAX_M + 1,
+ * computed by the same on-device scaling-and-squaring code the solver uses for exp(tau H~). */
+kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIOPS_H */

@@ -1,0 +1,716 @@
+// Host side of the C ABI declared in include/kiops.h: contexts, operators, workspace, launches.
+//
+// A solve is one launch: the grid engine is a cooperative launch of as many blocks as are co-resident
+// (the whole GPU works on one solve), the CTA engine launches one block per request of a batch.  The
+// host only validates arguments, lays out the workspace, uploads the argument block and reads back the
+// statistics; every step of Algorithm 1 runs in the kernel of kiops_device.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kiops.h"
+#include "kiops_device.cuh"
+
+using namespace kiops_dev;
+
+struct kiops_ctx {
+  kiops_config cfg;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  std::string err;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  void* host_pinned = nullptr;  // argument block + stats + trace staging
+  size_t host_pinned_bytes = 0;
+  double* stage_dev = nullptr;  // device staging of host-buffer solves
+  size_t stage_bytes = 0;
+  TaylorTable tt{};
+  bool busy = false;
+};
+
+struct kiops_op {
+  kiops_ctx* ctx;
+  OpDesc d;
+};
+
+namespace {
+
+kiops_status fail(kiops_ctx* ctx, kiops_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return s;
+}
+
+#define KCHECK(ctx, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(ctx, KIOPS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Truncation tail sum_{k > d} theta^k / k! (terms through exp/lgamma; every term positive).
+double taylor_tail(double theta, int d) {
+  double s = 0.0;
+  for (int k = d + 1; k < d + 200; ++k) {
+    double t = std::exp(k * std::log(theta) - std::lgamma((double)k + 1.0));
+    s += t;
+    if (t < 1e-40 * s) break;
+  }
+  return s;
+}
+
+// Paterson-Stockmeyer degrees deg = r q - 1 for costs r + q - 2 = 3..10 matrix products; theta is the
+// largest ||X||_1 with a truncation tail below 2^-53 (bisection).
+void build_taylor_table(TaylorTable& tt) {
+  tt.count = 0;
+  for (int cost = 3; cost <= 10 && tt.count < kMaxDeg; ++cost) {
+    int r = (cost + 2) / 2, q = (cost + 2) - r;
+    int d = r * q - 1;
+    double lo = 1e-8, hi = 64.0;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (taylor_tail(mid, d) <= std::ldexp(1.0, -53)) lo = mid; else hi = mid;
+    }
+    tt.deg[tt.count] = d;
+    tt.r[tt.count] = r;
+    tt.q[tt.count] = q;
+    tt.theta[tt.count] = lo;
+    tt.count++;
+  }
+}
+
+int max_r(const TaylorTable& tt) {
+  int r = 1;
+  for (int i = 0; i < tt.count; ++i) r = std::max(r, tt.r[i]);
+  return r;
+}
+
+template <typename T, int KIND, bool GRID>
+void* kernel_ptr() {
+  return (void*)kiops_solve_kernel<T, KIND, GRID>;
+}
+
+void* pick_kernel(bool fp32, int kind, bool grid) {
+  if (!fp32) {
+    if (grid) {
+      if (kind == OP_CSR) return kernel_ptr<double, OP_CSR, true>();
+      if (kind == OP_ST2D) return kernel_ptr<double, OP_ST2D, true>();
+      return kernel_ptr<double, OP_ST3D, true>();
+    }
+    if (kind == OP_CSR) return kernel_ptr<double, OP_CSR, false>();
+    if (kind == OP_ST2D) return kernel_ptr<double, OP_ST2D, false>();
+    return kernel_ptr<double, OP_ST3D, false>();
+  }
+  if (grid) {
+    if (kind == OP_CSR) return kernel_ptr<float, OP_CSR, true>();
+    if (kind == OP_ST2D) return kernel_ptr<float, OP_ST2D, true>();
+    return kernel_ptr<float, OP_ST3D, true>();
+  }
+  if (kind == OP_CSR) return kernel_ptr<float, OP_CSR, false>();
+  if (kind == OP_ST2D) return kernel_ptr<float, OP_ST2D, false>();
+  return kernel_ptr<float, OP_ST3D, false>();
+}
+
+constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
+
+// Per-solve device layout (each region 256-byte aligned).
+struct Layout {
+  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, args, trace, total;
+};
+
+Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, int r_max, int64_t trace_cap,
+              int64_t* ldv_out) {
+  Layout L{};
+  const int64_t ldv = (int64_t)align_up((size_t)(N + p), 64);
+  *ldv_out = ldv;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  L.V = take((size_t)(m_max + 1) * ldv * (fp32 ? 4 : 8));
+  L.H = take((size_t)(m_max + 2) * (m_max + 2) * 8);
+  L.gram = take((size_t)(m_max + 1) * std::max(m_o, 1) * 8);
+  L.mats = take((size_t)(r_max + 2) * (m_max + 1) * (m_max + 1) * 8);
+  L.fvec = take((size_t)(m_max + 2) * 8);
+  L.partials = take((size_t)2 * std::max(grid_blocks, 1) * kMaxRed * 8);
+  L.bar = take(256);
+  L.stats = take(16 * 8);
+  L.trace_len = take(8);
+  L.args = take(sizeof(SolveArgs));
+  L.trace = take((size_t)std::max<int64_t>(trace_cap, 0) * sizeof(TraceRec));
+  L.total = off;
+  return L;
+}
+
+kiops_status ensure_workspace(kiops_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return KIOPS_OK;
+  if (!ctx->ws_owned && ctx->ws)
+    return fail(ctx, KIOPS_ENOMEM, "attached workspace has %zu bytes, the solve needs %zu", ctx->ws_bytes, bytes);
+  if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  ctx->ws_owned = false;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(ctx, KIOPS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  ctx->ws = p;
+  ctx->ws_bytes = bytes;
+  ctx->ws_owned = true;
+  return KIOPS_OK;
+}
+
+kiops_status ensure_pinned(kiops_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->host_pinned_bytes) return KIOPS_OK;
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  ctx->host_pinned = nullptr;
+  ctx->host_pinned_bytes = 0;
+  KCHECK(ctx, cudaMallocHost(&ctx->host_pinned, bytes));
+  ctx->host_pinned_bytes = bytes;
+  return KIOPS_OK;
+}
+
+int grid_size(kiops_ctx* ctx, void* fn) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kDynSmem) != cudaSuccess) return 0;
+  int g = per_sm * ctx->sms;
+  if (ctx->cfg.grid_blocks > 0) g = std::min(g, ctx->cfg.grid_blocks);
+  return g;
+}
+
+kiops_status prepare_kernel(kiops_ctx* ctx, void* fn) {
+  KCHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
+  return KIOPS_OK;
+}
+
+struct Prepared {
+  SolveArgs args;
+  Layout L;
+  char* base;
+};
+
+// Validate one request and fill its argument block.
+kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b, double tol,
+                     int m_init, int m_o, kiops_precision prec, double* w, int grid_blocks, int64_t trace_cap,
+                     Prepared& P) {
+  if (!A || !b || !w) return fail(ctx, KIOPS_EINVAL, "NULL operator, b or w");
+  if (A->ctx != ctx) return fail(ctx, KIOPS_EINVAL, "operator belongs to another context");
+  if (p < 0 || p > KIOPS_MAX_P) return fail(ctx, KIOPS_EINVAL, "p = %d outside [0, %d]", p, KIOPS_MAX_P);
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(ctx, KIOPS_EINVAL, "tau must be finite and >= 0");
+  if (!(tol > 0.0)) return fail(ctx, KIOPS_EINVAL, "tol must be > 0");
+  if (m_init < 1) return fail(ctx, KIOPS_EINVAL, "m_init must be >= 1");
+  if (m_o < 1) return fail(ctx, KIOPS_EINVAL, "m_o must be >= 1");
+  if (prec != KIOPS_FP64 && prec != KIOPS_FP32_BASIS) return fail(ctx, KIOPS_EINVAL, "unknown precision");
+  for (int k = 0; k <= p; ++k)
+    if (!b[k]) return fail(ctx, KIOPS_EINVAL, "b[%d] is NULL", k);
+  const int m_max = ctx->cfg.m_max;
+  const int m_o_eff = std::min(m_o, m_max + 1);
+  std::memset(&P.args, 0, sizeof(SolveArgs));
+  SolveArgs& a = P.args;
+  a.op = A->d;
+  a.N = A->d.n;
+  a.p = p;
+  a.T_end = tau;
+  a.tol = tol;
+  a.m_init = m_init;
+  a.m_min = ctx->cfg.m_min;
+  a.m_max = m_max;
+  a.m_o = m_o_eff;
+  a.normalize = ctx->cfg.normalize_B;
+  a.bd_tol = ctx->cfg.breakdown_tol;
+  a.max_substeps = ctx->cfg.max_substeps;
+  a.max_iters = ctx->cfg.max_iterations;
+  for (int k = 0; k <= p; ++k) a.b[k] = b[k];
+  a.w = w;
+  a.timeout_ns = (long long)(ctx->cfg.timeout_s * 1e9);
+  a.tt = ctx->tt;
+  a.trace_cap = trace_cap;
+  int64_t ldv = 0;
+  P.L = layout(a.N, p, m_max, m_o_eff, prec == KIOPS_FP32_BASIS, grid_blocks, max_r(ctx->tt), trace_cap, &ldv);
+  a.ldv = ldv;
+  return KIOPS_OK;
+}
+
+void bind(Prepared& P, char* base) {
+  SolveArgs& a = P.args;
+  const Layout& L = P.L;
+  P.base = base;
+  a.V = base + L.V;
+  a.H = (double*)(base + L.H);
+  a.gram = (double*)(base + L.gram);
+  a.mats = (double*)(base + L.mats);
+  a.fvec = (double*)(base + L.fvec);
+  a.partials = (double*)(base + L.partials);
+  a.bar = (unsigned int*)(base + L.bar);
+  a.abort_flag = (int*)(base + L.bar + 64);
+  a.stats = (int64_t*)(base + L.stats);
+  a.stats_d = (double*)(base + L.stats + 10 * 8);
+  a.trace_len = (int64_t*)(base + L.trace_len);
+  a.trace = a.trace_cap > 0 ? (TraceRec*)(base + L.trace) : nullptr;
+}
+
+void fill_stats(kiops_stats* st, const int64_t* s, const double* sd, int engine, int blocks) {
+  if (!st) return;
+  st->substeps = s[0];
+  st->rejected = s[1];
+  st->matvecs = s[2];
+  st->iterations = s[3];
+  st->expm_calls = s[4];
+  st->m_last = (int)s[5];
+  st->status = (int)s[6];
+  st->engine = engine;
+  st->grid_blocks = blocks;
+  st->err_est = sd[0];
+}
+
+// One solve on the grid engine (or a single-block CTA launch).
+kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b, double tol,
+                        int m_init, int m_o, kiops_precision prec, double* w, kiops_stats* stats,
+                        kiops_trace_rec* trace, int64_t trace_cap, int64_t* trace_len) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (trace_len) *trace_len = 0;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (tau == 0.0 && A && b && w && b[0]) {  // w = b_0, no work (Algorithm 1 lines 8-9)
+    if (w != b[0]) KCHECK(ctx, cudaMemcpyAsync(w, b[0], (size_t)A->d.n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (stats) stats->m_last = std::max(ctx->cfg.m_min, std::min(m_init, ctx->cfg.m_max));
+    return KIOPS_OK;
+  }
+  const bool fp32 = prec == KIOPS_FP32_BASIS;
+  int engine = ctx->cfg.engine == KIOPS_ENGINE_CTA ? KIOPS_ENGINE_CTA : KIOPS_ENGINE_GRID;
+  if (!A) return fail(ctx, KIOPS_EINVAL, "NULL operator");
+  void* fn = pick_kernel(fp32, A->d.kind, engine == KIOPS_ENGINE_GRID);
+  kiops_status st = prepare_kernel(ctx, fn);
+  if (st) return st;
+  int blocks = engine == KIOPS_ENGINE_GRID ? grid_size(ctx, fn) : 1;
+  if (blocks < 1) return fail(ctx, KIOPS_ECUDA, "kernel does not fit on the device");
+  Prepared P;
+  st = prepare(ctx, A, tau, p, b, tol, m_init, m_o, prec, w, blocks, trace ? trace_cap : 0, P);
+  if (st) return st;
+  st = ensure_workspace(ctx, P.L.total);
+  if (st) return st;
+  bind(P, (char*)ctx->ws);
+  const size_t tr_bytes = (size_t)(trace ? trace_cap : 0) * sizeof(TraceRec);
+  st = ensure_pinned(ctx, sizeof(SolveArgs) + 256 + tr_bytes);
+  if (st) return st;
+  char* hp = (char*)ctx->host_pinned;
+  std::memcpy(hp, &P.args, sizeof(SolveArgs));
+  KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
+  KCHECK(ctx, cudaMemsetAsync(P.base + P.L.trace_len, 0, 8, ctx->stream));
+  KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, hp, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
+  const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
+  void* kargs[] = {(void*)&dargs};
+  if (engine == KIOPS_ENGINE_GRID) {
+    KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, kDynSmem, ctx->stream));
+  } else {
+    KCHECK(ctx, cudaLaunchKernel(fn, 1, kThreads, kargs, kDynSmem, ctx->stream));
+  }
+  int64_t* hs = (int64_t*)(hp + sizeof(SolveArgs) + 0);
+  KCHECK(ctx, cudaMemcpyAsync(hs, P.base + P.L.stats, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  int64_t* htl = hs + 15;
+  KCHECK(ctx, cudaMemcpyAsync(htl, P.base + P.L.trace_len, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (trace && trace_cap > 0) {
+    int64_t n = std::min(*htl, trace_cap);
+    std::vector<TraceRec> tmp((size_t)n);
+    if (n > 0)
+      KCHECK(ctx, cudaMemcpy(tmp.data(), P.base + P.L.trace, (size_t)n * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) {
+      trace[i].substep = tmp[i].substep;
+      trace[i].j = tmp[i].j;
+      trace[i].accepted = tmp[i].accepted;
+      trace[i].breakdown = tmp[i].breakdown;
+      trace[i].m_new = tmp[i].m_new;
+      trace[i].tau = tmp[i].tau;
+      trace[i].t_now = tmp[i].t_now;
+      trace[i].eps = tmp[i].eps;
+      trace[i].omega = tmp[i].omega;
+      trace[i].tau_new = tmp[i].tau_new;
+    }
+    if (trace_len) *trace_len = n;
+  }
+  const double* hsd = (const double*)(hs + 10);
+  fill_stats(stats, hs, hsd, engine, blocks);
+  const int dst = (int)hs[6];
+  if (dst == ST_ETIMEOUT) return fail(ctx, KIOPS_ETIMEOUT, "a device-side wait exceeded %.3g s", ctx->cfg.timeout_s);
+  if (dst == ST_ENOTCONV)
+    return fail(ctx, KIOPS_ENOTCONV, "no convergence within max_substeps/max_iterations (%lld iterations)",
+                (long long)hs[3]);
+  if (dst != ST_OK) return fail(ctx, (kiops_status)dst, "device status %d", dst);
+  return KIOPS_OK;
+}
+
+template <int KIND>
+__global__ void op_apply_kernel(OpDesc op, const double* x, double* y) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < op.n; r += (int64_t)gridDim.x * blockDim.x)
+    y[r] = apply_row<double, KIND>(op, x, r);
+}
+
+}  // namespace
+
+extern "C" {
+
+kiops_status kiops_config_default(kiops_config* cfg) {
+  if (!cfg) return KIOPS_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->m_min = 10;
+  cfg->m_max = 128;
+  cfg->normalize_B = 1;
+  cfg->breakdown_tol = 1e-12;
+  cfg->max_substeps = 1000000;
+  cfg->max_iterations = 100000;
+  cfg->timeout_s = 10.0;
+  cfg->engine = KIOPS_ENGINE_AUTO;
+  cfg->grid_blocks = 0;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_constants(double out[6]) {
+  if (!out) return KIOPS_EINVAL;
+  out[0] = 1.4;  // delta, eq 39
+  out[1] = 0.9;  // gamma, eq 44
+  out[2] = 0.6;  // gamma_max, Algorithm 4
+  out[3] = 2.0;  // kappa default, section 3.6.2
+  out[4] = 5.0;  // tau clip factor, section 3.6.1
+  out[5] = 2.0;  // m_o default, Algorithm 2
+  return KIOPS_OK;
+}
+
+const char* kiops_status_string(kiops_status s) {
+  switch (s) {
+    case KIOPS_OK: return "ok";
+    case KIOPS_EINVAL: return "invalid argument";
+    case KIOPS_ENOMEM: return "out of memory";
+    case KIOPS_ENOTCONV: return "not converged";
+    case KIOPS_ETIMEOUT: return "device wait timed out";
+    case KIOPS_ECUDA: return "CUDA error";
+    case KIOPS_EBUSY: return "context busy";
+  }
+  return "unknown status";
+}
+
+kiops_status kiops_create(kiops_ctx** out, const kiops_config* cfg) {
+  if (!out) return KIOPS_EINVAL;
+  *out = nullptr;
+  kiops_ctx* ctx = new (std::nothrow) kiops_ctx();
+  if (!ctx) return KIOPS_ENOMEM;
+  if (cfg) ctx->cfg = *cfg; else kiops_config_default(&ctx->cfg);
+  const kiops_config& c = ctx->cfg;
+  if (c.m_min < 1 || c.m_max < c.m_min || c.m_max > KIOPS_MAX_M || !(c.breakdown_tol >= 0) ||
+      c.max_substeps < 1 || c.max_iterations < 1 || !(c.timeout_s > 0)) {
+    delete ctx;
+    return KIOPS_EINVAL;
+  }
+  if (cudaSetDevice(c.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) {
+    delete ctx;
+    return KIOPS_ECUDA;
+  }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.device);
+  if (!coop) {
+    delete ctx;
+    return KIOPS_ECUDA;
+  }
+  ctx->stream = (cudaStream_t)c.stream;
+  build_taylor_table(ctx->tt);
+  *out = ctx;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_destroy(kiops_ctx* ctx) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  if (ctx->stage_dev) cudaFree(ctx->stage_dev);
+  delete ctx;
+  return KIOPS_OK;
+}
+
+const char* kiops_last_error(const kiops_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+kiops_status kiops_attach_workspace(kiops_ctx* ctx, void* dptr, size_t bytes) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = dptr;
+  ctx->ws_bytes = dptr ? bytes : 0;
+  ctx->ws_owned = false;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_workspace_size(kiops_ctx* ctx, const kiops_op* A, int p, int m_o, kiops_precision prec,
+                                  size_t* bytes) {
+  if (!ctx || !A || !bytes || p < 0 || p > KIOPS_MAX_P || m_o < 1) return KIOPS_EINVAL;
+  const bool fp32 = prec == KIOPS_FP32_BASIS;
+  void* fn = pick_kernel(fp32, A->d.kind, true);
+  kiops_status st = prepare_kernel(ctx, fn);
+  if (st) return st;
+  int blocks = std::max(grid_size(ctx, fn), 1);
+  int64_t ldv;
+  Layout L = layout(A->d.n, p, ctx->cfg.m_max, std::min(m_o, ctx->cfg.m_max + 1), fp32, blocks, max_r(ctx->tt), 0, &ldv);
+  *bytes = L.total;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_op_csr(kiops_ctx* ctx, kiops_op** op, int64_t n, int64_t nnz, const int32_t* rowptr,
+                          const int32_t* colind, const double* vals) {
+  if (!ctx || !op) return KIOPS_EINVAL;
+  *op = nullptr;
+  if (n < 1 || nnz < 0 || n > INT32_MAX || !rowptr || (nnz > 0 && (!colind || !vals)))
+    return fail(ctx, KIOPS_EINVAL, "invalid CSR description");
+  kiops_op* o = new (std::nothrow) kiops_op();
+  if (!o) return KIOPS_ENOMEM;
+  o->ctx = ctx;
+  std::memset(&o->d, 0, sizeof(o->d));
+  o->d.kind = OP_CSR;
+  o->d.n = n;
+  o->d.rowptr = rowptr;
+  o->d.colind = colind;
+  o->d.vals = vals;
+  *op = o;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stencil2d_desc* d) {
+  if (!ctx || !op || !d) return KIOPS_EINVAL;
+  *op = nullptr;
+  if (d->nx < 1 || d->ny < 1 || (d->nspecies != 1 && d->nspecies != 2))
+    return fail(ctx, KIOPS_EINVAL, "invalid 2D stencil description");
+  kiops_op* o = new (std::nothrow) kiops_op();
+  if (!o) return KIOPS_ENOMEM;
+  o->ctx = ctx;
+  std::memset(&o->d, 0, sizeof(o->d));
+  o->d.kind = OP_ST2D;
+  o->d.nx = d->nx;
+  o->d.ny = d->ny;
+  o->d.nz = 1;
+  o->d.nspecies = d->nspecies;
+  o->d.periodic = d->periodic ? 1 : 0;
+  o->d.n = d->nx * d->ny * d->nspecies;
+  for (int s = 0; s < 2; ++s) {
+    for (int k = 0; k < 5; ++k) o->d.coef[s][k] = s < d->nspecies ? d->coef[s][k] : 0.0;
+    for (int r = 0; r < 2; ++r) o->d.diag[s][r] = (s < d->nspecies && r < d->nspecies) ? d->diag[s][r] : nullptr;
+  }
+  *op = o;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stencil3d_desc* d) {
+  if (!ctx || !op || !d) return KIOPS_EINVAL;
+  *op = nullptr;
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(ctx, KIOPS_EINVAL, "invalid 3D stencil description");
+  kiops_op* o = new (std::nothrow) kiops_op();
+  if (!o) return KIOPS_ENOMEM;
+  o->ctx = ctx;
+  std::memset(&o->d, 0, sizeof(o->d));
+  o->d.kind = OP_ST3D;
+  o->d.nx = d->nx;
+  o->d.ny = d->ny;
+  o->d.nz = d->nz;
+  o->d.nspecies = 1;
+  o->d.periodic = d->periodic ? 1 : 0;
+  o->d.n = d->nx * d->ny * d->nz;
+  for (int k = 0; k < 7; ++k) o->d.coef[0][k] = d->coef[k];
+  o->d.diag[0][0] = d->diag;
+  *op = o;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_op_destroy(kiops_op* op) {
+  if (!op) return KIOPS_EINVAL;
+  delete op;
+  return KIOPS_OK;
+}
+
+int64_t kiops_op_size(const kiops_op* op) { return op ? op->d.n : -1; }
+
+kiops_status kiops_op_apply(kiops_ctx* ctx, const kiops_op* A, const double* x, double* y) {
+  if (!ctx || !A || !x || !y) return KIOPS_EINVAL;
+  const int blocks = (int)std::min<int64_t>((A->d.n + 255) / 256, (int64_t)ctx->sms * 8);
+  if (A->d.kind == OP_CSR) op_apply_kernel<OP_CSR><<<blocks, 256, 0, ctx->stream>>>(A->d, x, y);
+  else if (A->d.kind == OP_ST2D) op_apply_kernel<OP_ST2D><<<blocks, 256, 0, ctx->stream>>>(A->d, x, y);
+  else op_apply_kernel<OP_ST3D><<<blocks, 256, 0, ctx->stream>>>(A->d, x, y);
+  KCHECK(ctx, cudaGetLastError());
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  return KIOPS_OK;
+}
+
+kiops_status kiops_solve(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b, double tol,
+                         int m_init, int m_o, kiops_precision prec, double* w, kiops_stats* stats) {
+  return run_single(ctx, A, tau, p, b, tol, m_init, m_o, prec, w, stats, nullptr, 0, nullptr);
+}
+
+kiops_status kiops_solve_traced(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b,
+                                double tol, int m_init, int m_o, kiops_precision prec, double* w,
+                                kiops_stats* stats, kiops_trace_rec* trace, int64_t trace_cap,
+                                int64_t* trace_len) {
+  if (!trace || trace_cap < 1) return fail(ctx, KIOPS_EINVAL, "trace buffer required");
+  return run_single(ctx, A, tau, p, b, tol, m_init, m_o, prec, w, stats, trace, trace_cap, trace_len);
+}
+
+kiops_status kiops_solve_host(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b_host,
+                              double tol, int m_init, int m_o, kiops_precision prec, double* w_host,
+                              kiops_stats* stats) {
+  if (!ctx || !A || !b_host || !w_host || p < 0 || p > KIOPS_MAX_P) return KIOPS_EINVAL;
+  for (int k = 0; k <= p; ++k)
+    if (!b_host[k]) return fail(ctx, KIOPS_EINVAL, "b_host[%d] is NULL", k);
+  const size_t n = (size_t)A->d.n;
+  const size_t need = (size_t)(p + 2) * n * sizeof(double);
+  if (need > ctx->stage_bytes) {
+    if (ctx->stage_dev) cudaFree(ctx->stage_dev);
+    ctx->stage_dev = nullptr;
+    ctx->stage_bytes = 0;
+    KCHECK(ctx, cudaMalloc(&ctx->stage_dev, need));
+    ctx->stage_bytes = need;
+  }
+  const double* bd[KIOPS_MAX_P + 1];
+  for (int k = 0; k <= p; ++k) {
+    double* dst = ctx->stage_dev + (size_t)k * n;
+    KCHECK(ctx, cudaMemcpyAsync(dst, b_host[k], n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    bd[k] = dst;
+  }
+  double* wd = ctx->stage_dev + (size_t)(p + 1) * n;
+  kiops_status st = run_single(ctx, A, tau, p, bd, tol, m_init, m_o, prec, wd, stats, nullptr, 0, nullptr);
+  if (st != KIOPS_OK) return st;
+  KCHECK(ctx, cudaMemcpyAsync(w_host, wd, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  return KIOPS_OK;
+}
+
+kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
+  if (!ctx || count < 0 || (count > 0 && !reqs)) return KIOPS_EINVAL;
+  if (count == 0) return KIOPS_OK;
+  // one kernel launch per (precision, operator kind) group; each block runs one request
+  std::vector<Prepared> prep((size_t)count);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    const kiops_request& r = reqs[i];
+    kiops_status st = prepare(ctx, r.A, r.tau, r.p, r.b, r.tol, r.m_init, r.m_o, r.prec, r.w, 1, 0, prep[i]);
+    if (st) return st;
+    total = align_up(total, 256) + prep[i].L.total;
+  }
+  const size_t args_off = align_up(total, 256);
+  total = args_off + (size_t)count * sizeof(SolveArgs);
+  kiops_status st = ensure_workspace(ctx, total + 256);
+  if (st) return st;
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    off = align_up(off, 256);
+    bind(prep[i], (char*)ctx->ws + off);
+    off += prep[i].L.total;
+  }
+  // contiguous argument array per group, staged through pinned memory
+  st = ensure_pinned(ctx, (size_t)count * (sizeof(SolveArgs) + 16 * 8) + 4096);
+  if (st) return st;
+  char* hp = (char*)ctx->host_pinned;
+  SolveArgs* hargs = (SolveArgs*)hp;
+  int64_t* hstats = (int64_t*)(hp + (size_t)count * sizeof(SolveArgs));
+  for (int i = 0; i < count; ++i) {
+    KCHECK(ctx, cudaMemsetAsync(prep[i].base + prep[i].L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
+    if (reqs[i].tau == 0.0)
+      KCHECK(ctx, cudaMemcpyAsync(reqs[i].w, reqs[i].b[0], (size_t)reqs[i].A->d.n * 8, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  }
+  // order requests by (precision, kind); tau == 0 requests are done above
+  std::vector<int> order;
+  for (int i = 0; i < count; ++i)
+    if (reqs[i].tau > 0.0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    int kx = reqs[x].prec * 4 + reqs[x].A->d.kind, ky = reqs[y].prec * 4 + reqs[y].A->d.kind;
+    return kx < ky;
+  });
+  // device argument array, grouped in launch order, at the end of the workspace
+  void* dargs_all = (char*)ctx->ws + args_off;
+  for (size_t k = 0; k < order.size(); ++k) std::memcpy(&hargs[k], &prep[order[k]].args, sizeof(SolveArgs));
+  KCHECK(ctx, cudaMemcpyAsync(dargs_all, hargs, order.size() * sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
+  size_t g0 = 0;
+  while (g0 < order.size()) {
+    size_t g1 = g0;
+    const int key = reqs[order[g0]].prec * 4 + reqs[order[g0]].A->d.kind;
+    while (g1 < order.size() && reqs[order[g1]].prec * 4 + reqs[order[g1]].A->d.kind == key) ++g1;
+    void* fn = pick_kernel(reqs[order[g0]].prec == KIOPS_FP32_BASIS, reqs[order[g0]].A->d.kind, false);
+    st = prepare_kernel(ctx, fn);
+    if (st) return st;
+    const SolveArgs* dptr = (const SolveArgs*)dargs_all + g0;
+    void* kargs[] = {(void*)&dptr};
+    cudaError_t e = cudaLaunchKernel(fn, (unsigned)(g1 - g0), kThreads, kargs, kDynSmem, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, KIOPS_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    g0 = g1;
+  }
+  for (int i = 0; i < count; ++i)
+    KCHECK(ctx, cudaMemcpyAsync(hstats + (size_t)i * 16, prep[i].base + prep[i].L.stats, 16 * 8, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  kiops_status worst = KIOPS_OK;
+  for (int i = 0; i < count; ++i) {
+    const int64_t* s = hstats + (size_t)i * 16;
+    if (reqs[i].tau == 0.0) {
+      if (stats) {
+        std::memset(&stats[i], 0, sizeof(kiops_stats));
+        stats[i].engine = KIOPS_ENGINE_CTA;
+        stats[i].grid_blocks = 1;
+      }
+      continue;
+    }
+    fill_stats(stats ? &stats[i] : nullptr, s, (const double*)(s + 10), KIOPS_ENGINE_CTA, 1);
+    if (s[6] != ST_OK && worst == KIOPS_OK) worst = (kiops_status)s[6];
+  }
+  if (worst != KIOPS_OK) return fail(ctx, worst, "at least one batch request failed (status %d)", (int)worst);
+  return KIOPS_OK;
+}
+
+kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f) {
+  if (!ctx || !a || !f || n < 1 || n > KIOPS_MAX_M + 1) return KIOPS_EINVAL;
+  void* fn = pick_kernel(false, OP_CSR, true);
+  kiops_status st = prepare_kernel(ctx, fn);
+  if (st) return st;
+  int blocks = grid_size(ctx, fn);
+  if (blocks < 1) return fail(ctx, KIOPS_ECUDA, "kernel does not fit on the device");
+  Prepared P;
+  std::memset(&P.args, 0, sizeof(SolveArgs));
+  SolveArgs& sa = P.args;
+  sa.m_max = n - 1;
+  sa.tt = ctx->tt;
+  sa.expm_only = 1;
+  sa.expm_n = n;
+  sa.expm_in = a;
+  sa.expm_out = f;
+  sa.timeout_ns = (long long)(ctx->cfg.timeout_s * 1e9);
+  int64_t ldv;
+  P.L = layout(0, 0, n - 1, 1, false, blocks, max_r(ctx->tt), 0, &ldv);
+  st = ensure_workspace(ctx, P.L.total);
+  if (st) return st;
+  bind(P, (char*)ctx->ws);
+  st = ensure_pinned(ctx, sizeof(SolveArgs) + 256);
+  if (st) return st;
+  std::memcpy(ctx->host_pinned, &P.args, sizeof(SolveArgs));
+  KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
+  KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, ctx->host_pinned, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
+  const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
+  void* kargs[] = {(void*)&dargs};
+  KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, kDynSmem, ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  int flag = 0;
+  KCHECK(ctx, cudaMemcpy(&flag, P.base + P.L.bar + 64, 4, cudaMemcpyDeviceToHost));
+  if (flag) return fail(ctx, KIOPS_ETIMEOUT, "a device-side wait exceeded the limit");
+  return KIOPS_OK;
+}
+
+}  // extern "C"

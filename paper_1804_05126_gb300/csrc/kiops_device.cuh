@@ -1,0 +1,872 @@
+// Device side of the KIOPS solver for GB300 (sm_103a).
+//
+// One kernel template runs Algorithm 1 (Task II) of Gaudreault, Rainwater & Tokman (JCP 372, 2018)
+// end to end on the device: setup (section 3.7), start vector (Algorithm 1 lines 10-15), IOP steps
+// (Algorithm 2), the small exponential of tau H~ (eqs 37-38), the estimate and acceptance (eqs 36, 39),
+// Algorithm 4 with sections 3.6.1-3.6.2, and the update w = beta V F(:,1) (Algorithm 3, Task II line).
+//
+// Two execution "teams" share that code:
+//   GridTeam  one persistent cooperative launch spreads every vector phase over all blocks of the GPU;
+//             phases are separated by a counter barrier with a deadline; every block reduces the
+//             published per-block partial sums in the same fixed order, so every block holds bitwise
+//             identical scalars and takes identical control decisions without broadcasting them.
+//   CtaTeam   one thread block owns a whole solve (batches of independent problems, small problems).
+//
+// Nothing here is a dense contraction over the large dimension, so no tensor cores are used: the vector
+// phases are bandwidth / FP64-pipe bound and the small exponential is an FP64 dense computation spread
+// over the blocks of the team.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kiops_dev {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxM = 256;                 // largest m_max
+constexpr int kMaxN = kMaxM + 1;           // largest exponential size n = j + 1
+constexpr int kMaxP = 16;                  // largest p
+constexpr int kRegK = 8;                   // accumulators per thread per reduction pass
+constexpr int kChunk = 3;                  // window vectors handled per pass (2*3 + 1 <= kRegK)
+constexpr int kMaxWin = kMaxM + 1;         // largest orthogonalisation window
+constexpr int kMaxRed = 2 * kMaxWin + 1;   // largest reduction width
+constexpr int kTile = 8;                   // dense matmul tile edge
+constexpr int kMaxDeg = 8;                 // entries of the Taylor degree table
+
+enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ENOTCONV = 3, ST_ETIMEOUT = 4, ST_ECUDA = 5 };
+enum : int { OP_CSR = 0, OP_ST2D = 1, OP_ST3D = 2 };
+
+struct OpDesc {
+  int kind;
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* vals;
+  int64_t nx, ny, nz;
+  int nspecies;
+  int periodic;
+  double coef[2][7];
+  const double* diag[2][2];
+};
+
+// Truncated Taylor degrees evaluated by Paterson-Stockmeyer: deg = r*q - 1 with r-1 matmuls for the
+// powers X^2..X^r and q-1 Horner matmuls in X^r; theta = largest ||X||_1 whose truncation tail
+// sum_{k > deg} theta^k / k! stays below the unit roundoff 2^-53.
+struct TaylorTable {
+  int count;
+  int deg[kMaxDeg];
+  int r[kMaxDeg];
+  int q[kMaxDeg];
+  double theta[kMaxDeg];
+};
+
+struct TraceRec {
+  int64_t substep;
+  int j, accepted, breakdown, m_new;
+  double tau, t_now, eps, omega, tau_new;
+};
+
+struct SolveArgs {
+  OpDesc op;
+  int64_t N;
+  int p;
+  int64_t ldv;               // stride between basis vectors (elements)
+  double T_end, tol;
+  int m_init, m_min, m_max, m_o;
+  int normalize;
+  double bd_tol;
+  int64_t max_substeps, max_iters;
+  const double* b[kMaxP + 1];
+  double* w;
+  void* V;                   // (m_max + 1) vectors of ldv elements (double or float)
+  double* H;                 // (m_max + 2)^2, row-major, 1-based H(i,k) at [(i-1)*(m_max+2) + k-1]
+  double* gram;              // (m_max + 1) * m_o : <v_i, v_{i-o}> at [(i-1)*m_o + o]
+  double* mats;              // expm work: (r_max + 2) matrices of (m_max+1)^2
+  double* fvec;              // F(:,1) in [0, m_max+1), F(j, j+1) at [m_max+1]
+  double* partials;          // 2 * grid * kMaxRed (grid engine only)
+  unsigned int* bar;         // barrier counter (grid engine only)
+  int* abort_flag;           // nonzero: a block gave up waiting (grid engine only)
+  long long timeout_ns;
+  int64_t* stats;            // substeps, rejected, matvecs, iterations, expm_calls, m_last, status
+  double* stats_d;           // err_est
+  TraceRec* trace;
+  int64_t trace_cap;
+  int64_t* trace_len;
+  TaylorTable tt;
+  int expm_only;             // 1: compute exp(a) of an n x n matrix only (kiops_expm)
+  int expm_n;
+  const double* expm_in;
+  double* expm_out;
+};
+
+// ------------------------------------------------------------------------------------------------
+// low-level helpers
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// ceil(log2(x)) for x > 0, exact (frexp gives x = f 2^e, f in [0.5, 1)).
+__device__ __forceinline__ int ceil_log2(double x) {
+  int e;
+  double f = frexp(x, &e);
+  return f == 0.5 ? e - 1 : e;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Teams
+// ------------------------------------------------------------------------------------------------
+struct GridTeam {
+  int rank, size;
+  unsigned int* ctr;
+  int* abort_flag;
+  long long timeout_ns;
+  unsigned int epoch;
+  // Counter barrier: every block adds 1 (release) and waits (acquire) until the counter reaches
+  // size * epoch.  A wait longer than timeout_ns raises the abort flag; every waiter also leaves when it
+  // sees the flag.  Returns false when the team must stop.
+  __device__ bool sync(int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      epoch += 1;
+      __threadfence();
+      red_release_add(ctr, 1u);
+      const unsigned int target = epoch * (unsigned int)size;
+      const long long t0 = global_ns();
+      int ok = 1;
+      unsigned int spins = 0;
+      while ((int)(ld_acquire(ctr) - target) < 0) {
+        if (((++spins) & 63u) == 0u) {
+          if (ld_volatile_int(abort_flag)) { ok = 0; break; }
+          if (global_ns() - t0 > timeout_ns) {
+            atomicExch(abort_flag, ST_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+  }
+};
+
+struct CtaTeam {
+  int rank = 0, size = 1;
+  __device__ bool sync(int*) {
+    __syncthreads();
+    return true;
+  }
+};
+
+// ------------------------------------------------------------------------------------------------
+// Shared control state: identical in every block of a grid team.
+// ------------------------------------------------------------------------------------------------
+struct Ctl {
+  double t_now, tau, beta, nu, mu, s, rs, eps_last, nx2_pre;
+  double kappa, qp1_est, prev_tau, prev_omega, prev_eps;
+  int m, j, i0, nwin, breakdown, recompute, accepted, done, status, have_prev, prev_j, sync_ok;
+  int64_t substeps, rejected, matvecs, iters, expm_calls;
+  // expm selection
+  int deg_i, n_exp, s_sq;
+  double xscale;
+  double hcoef[kMaxWin];        // MGS coefficients h(i0..j, j)
+  double colabs[kMaxM + 2];     // 1-based: sum_i |h(i,k)| over the window entries of column k
+  double sub[kMaxM + 2];        // 1-based: h(k+1, k)
+  double tail[kMaxP];           // tail of the vector being multiplied
+  double hc[kMaxP + 1];         // Horner epilogue coefficients
+  double red[kMaxRed];          // results of the last all-reduce
+  double blk[kMaxRed];          // this block's partial sums
+  double wred[kWarps][kRegK];
+};
+
+// Reduce acc[0..K) over the block into blk[off..off+K).  Fixed shuffle tree + fixed warp order.
+__device__ __forceinline__ void block_reduce(Ctl& c, const double (&acc)[kRegK], int K, int off) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kRegK; ++k) {
+    if (k < K) {
+      double v = warp_sum(acc[k]);
+      if (lane == 0) c.wred[warp][k] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += c.wred[w][threadIdx.x];
+    c.blk[off + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Finish an all-reduce of blk[0..K) into red[0..K).  Grid: publish, barrier, then every block sums the
+// published partials over ranks 0..size-1 in the same order.  Returns false if the team must stop.
+template <class Team>
+__device__ bool finish_reduce(Team& team, Ctl& c, double* partials, int& parity, int K);
+
+template <>
+__device__ bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, int&, int K) {
+  for (int k = threadIdx.x; k < K; k += kThreads) c.red[k] = c.blk[k];
+  __syncthreads();
+  return true;
+}
+
+template <>
+__device__ bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K) {
+  double* buf = partials + (size_t)parity * team.size * kMaxRed;
+  for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
+  if (!team.sync(&c.sync_ok)) return false;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < K; k += kWarps) {
+    double s = 0.0;
+    for (int r = lane; r < team.size; r += 32) s += buf[(size_t)r * kMaxRed + k];
+    s = warp_sum(s);
+    if (lane == 0) c.red[k] = s;
+  }
+  __syncthreads();
+  parity ^= 1;
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Operators: row r of A x (matrix-free; Algorithm 2 lines 4-6 apply A to the first N entries).
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T st_val(const OpDesc& op, const T* x, int s, int64_t ix, int64_t iy, int64_t iz,
+                                    int64_t nz) {
+  if (op.periodic) {
+    ix = ix < 0 ? ix + op.nx : (ix >= op.nx ? ix - op.nx : ix);
+    iy = iy < 0 ? iy + op.ny : (iy >= op.ny ? iy - op.ny : iy);
+    iz = iz < 0 ? iz + nz : (iz >= nz ? iz - nz : iz);
+  } else if (ix < 0 || ix >= op.nx || iy < 0 || iy >= op.ny || iz < 0 || iz >= nz) {
+    return T(0);
+  }
+  return x[(int64_t)s * op.nx * op.ny * nz + (iz * op.ny + iy) * op.nx + ix];
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ T apply_row(const OpDesc& op, const T* x, int64_t r) {
+  if (KIND == OP_CSR) {
+    T acc = T(0);
+    const int32_t k1 = __ldg(op.rowptr + r + 1);
+    for (int32_t k = __ldg(op.rowptr + r); k < k1; ++k) acc += T(__ldg(op.vals + k)) * x[__ldg(op.colind + k)];
+    return acc;
+  } else if (KIND == OP_ST2D) {
+    const int64_t npts = op.nx * op.ny;
+    const int s = (int)(r / npts);
+    const int64_t pt = r - (int64_t)s * npts;
+    const int64_t iy = pt / op.nx, ix = pt - iy * op.nx;
+    const double* c = op.coef[s];
+    T acc = T(c[0]) * x[r];
+    acc += T(c[1]) * st_val<T>(op, x, s, ix - 1, iy, 0, 1);
+    acc += T(c[2]) * st_val<T>(op, x, s, ix + 1, iy, 0, 1);
+    acc += T(c[3]) * st_val<T>(op, x, s, ix, iy - 1, 0, 1);
+    acc += T(c[4]) * st_val<T>(op, x, s, ix, iy + 1, 0, 1);
+    for (int q = 0; q < op.nspecies; ++q)
+      if (op.diag[s][q]) acc += T(__ldg(op.diag[s][q] + pt)) * x[(int64_t)q * npts + pt];
+    return acc;
+  } else {
+    const int64_t nxy = op.nx * op.ny;
+    const int64_t iz = r / nxy, rem = r - iz * nxy;
+    const int64_t iy = rem / op.nx, ix = rem - iy * op.nx;
+    const double* c = op.coef[0];
+    T acc = T(c[0]) * x[r];
+    acc += T(c[1]) * st_val<T>(op, x, 0, ix - 1, iy, iz, op.nz);
+    acc += T(c[2]) * st_val<T>(op, x, 0, ix + 1, iy, iz, op.nz);
+    acc += T(c[3]) * st_val<T>(op, x, 0, ix, iy - 1, iz, op.nz);
+    acc += T(c[4]) * st_val<T>(op, x, 0, ix, iy + 1, iz, op.nz);
+    acc += T(c[5]) * st_val<T>(op, x, 0, ix, iy, iz - 1, op.nz);
+    acc += T(c[6]) * st_val<T>(op, x, 0, ix, iy, iz + 1, op.nz);
+    if (op.diag[0][0]) acc += T(__ldg(op.diag[0][0] + r)) * x[r];
+    return acc;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Small dense exponential exp(tau H~) (section 3.3.1, eqs 37-38), spread over the team's blocks.
+//
+// Scaling and squaring with a truncated Taylor polynomial in Paterson-Stockmeyer form.  The paper uses a
+// diagonal Pade approximant; its linear solve is a chain of n dependent pivot steps, each of which would
+// need a team-wide barrier, while the Taylor form is made of matrix products only (one barrier each).
+// Both approximate exp to the unit roundoff for ||X|| <= theta.
+// ------------------------------------------------------------------------------------------------
+struct MmEpi {
+  int nterms;          // Horner epilogue: + sum_t hc[t] * P_t(i,k), P_0 = I
+  const double* pw;    // P_1 at pw, P_t at pw + (t-1) * ldm
+  size_t ldm;
+};
+
+// C = A B (+ epilogue) for n x n row-major matrices; tiles of kTile x kTile distributed over ranks.
+__device__ void mm_team(const double* A, const double* B, double* C, int n, int rank, int size, const Ctl& c,
+                        const MmEpi& epi, double* sA, double* sB) {
+  const int nt = (n + kTile - 1) / kTile;
+  const int out = threadIdx.x >> 2, part = threadIdx.x & 3;
+  const int ti_l = out / kTile, tk_l = out % kTile;
+  for (int tile = rank; tile < nt * nt; tile += size) {
+    const int ti = tile / nt, tk = tile - ti * nt;
+    for (int e = threadIdx.x; e < kTile * n; e += kThreads) {
+      const int rr = e / n, l = e - rr * n;
+      const int row = ti * kTile + rr;
+      sA[rr * kMaxN + l] = row < n ? A[(size_t)row * n + l] : 0.0;
+      const int l2 = e / kTile, cc = e - l2 * kTile;
+      const int col = tk * kTile + cc;
+      sB[l2 * kTile + cc] = col < n ? B[(size_t)l2 * n + col] : 0.0;
+    }
+    __syncthreads();
+    double s = 0.0;
+    for (int l = part; l < n; l += 4) s = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    const int row = ti * kTile + ti_l, col = tk * kTile + tk_l;
+    if (part == 0 && row < n && col < n) {
+      double e = 0.0;
+      if (epi.nterms > 0) {
+        e = row == col ? c.hc[0] : 0.0;
+        for (int t = 1; t < epi.nterms; ++t) e = fma(c.hc[t], epi.pw[(size_t)(t - 1) * epi.ldm + (size_t)row * n + col], e);
+      }
+      C[(size_t)row * n + col] = s + e;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// The solver kernel.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int KIND, class Team>
+__device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn);
+
+template <typename T, int KIND, bool GRID>
+__global__ void __launch_bounds__(kThreads) kiops_solve_kernel(const SolveArgs* __restrict__ all) {
+  extern __shared__ double smem_dyn[];
+  __shared__ Ctl c;
+  if (GRID) {
+    GridTeam team{(int)blockIdx.x, (int)gridDim.x, all[0].bar, all[0].abort_flag, all[0].timeout_ns, 0u};
+    solve_body<T, KIND, GridTeam>(all[0], team, c, smem_dyn);
+  } else {
+    CtaTeam team;
+    solve_body<T, KIND, CtaTeam>(all[blockIdx.x], team, c, smem_dyn);
+  }
+}
+
+// Builds exp(tau H~) for the current j; leaves F(:,1) in a.fvec[0..j) and F(j, j+1) in a.fvec[m_max+1].
+// With a.expm_only, exponentiates a.expm_in (n x n) into a.expm_out instead.
+template <class Team>
+__device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, double* smem_dyn) {
+  const int n = a.expm_only ? a.expm_n : c.j + 1;
+  const size_t ldm = (size_t)(a.m_max + 1) * (a.m_max + 1);
+  double* sA = smem_dyn;
+  double* sB = smem_dyn + kTile * kMaxN;
+  // ||tau H~||_1 from the running column sums (every block holds the same values)
+  if (threadIdx.x == 0) {
+    double nrm;
+    if (a.expm_only) {
+      nrm = 0.0;  // computed below from the input
+    } else {
+      nrm = 1.0;  // column j+1 of H~ is e_1
+      for (int k = 1; k <= c.j; ++k) {
+        double col = c.colabs[k] + (k < c.j ? c.sub[k] : 0.0);
+        nrm = col > nrm ? col : nrm;
+      }
+      nrm *= c.tau;
+    }
+    c.red[0] = nrm;
+  }
+  __syncthreads();
+  if (a.expm_only) {
+    // column sums of |a| by one warp per column group, same order in every block
+    if (threadIdx.x == 0) {
+      double best = 0.0;
+      for (int k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fabs(a.expm_in[(size_t)i * n + k]);
+        best = s > best ? s : best;
+      }
+      c.red[0] = best;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = c.red[0];
+    int best_i = 0, best_cost = 1 << 30, best_s = 0;
+    for (int i = 0; i < a.tt.count; ++i) {
+      int s = 0;
+      if (nrm > a.tt.theta[i]) s = ceil_log2(nrm / a.tt.theta[i]);
+      if (s < 0) s = 0;
+      const int cost = a.tt.r[i] - 1 + a.tt.q[i] - 1 + s;
+      if (cost < best_cost) { best_cost = cost; best_i = i; best_s = s; }
+    }
+    c.deg_i = best_i;
+    c.s_sq = best_s;
+    c.n_exp = n;
+    c.xscale = ldexp(a.expm_only ? 1.0 : c.tau, -best_s);
+  }
+  __syncthreads();
+  const int r = a.tt.r[c.deg_i], q = a.tt.q[c.deg_i], deg = a.tt.deg[c.deg_i];
+  double* P = a.mats;                        // P_t at P + (t-1)*ldm, t = 1..r
+  double* T0 = a.mats + (size_t)r * ldm;     // Horner / squaring ping-pong
+  double* T1 = T0 + ldm;
+  // X = xscale * H~ (band entries of H only; H~(1, j+1) = 1; last row 0), or xscale * input
+  for (int64_t e = (int64_t)team.rank * kThreads + threadIdx.x; e < (int64_t)n * n; e += (int64_t)team.size * kThreads) {
+    const int i = (int)(e / n), k = (int)(e - (int64_t)i * n);  // 0-based
+    double v = 0.0;
+    if (a.expm_only) {
+      v = a.expm_in[e];
+    } else if (k == n - 1) {
+      v = (i == 0) ? 1.0 : 0.0;
+    } else if (i < n - 1) {
+      // H(i+1, k+1) is stored if it is in the window of column k+1 or is the sub-diagonal entry
+      const int col = k + 1, row = i + 1;
+      const int lo = col - a.m_o + 1 < 1 ? 1 : col - a.m_o + 1;
+      if ((row >= lo && row <= col) || row == col + 1) v = a.H[(size_t)(row - 1) * (a.m_max + 2) + (col - 1)];
+    }
+    P[e] = c.xscale * v;
+  }
+  if (!team.sync(&c.sync_ok)) return false;
+  MmEpi none{0, nullptr, ldm};
+  for (int t = 2; t <= r; ++t) {  // powers X^2..X^r
+    mm_team(P + (size_t)(t - 2) * ldm, P, P + (size_t)(t - 1) * ldm, n, team.rank, team.size, c, none, sA, sB);
+    if (!team.sync(&c.sync_ok)) return false;
+  }
+  // Horner in X^r: T = B_{q-1}; T = T X^r + B_i, B_i = sum_{t<r} coef(i r + t) X^t, coef(k) = 1/k!
+  auto coef = [&](int k) -> double {
+    if (k > deg) return 0.0;
+    double v = 1.0;
+    for (int i = 2; i <= k; ++i) v /= (double)i;
+    return v;
+  };
+  if (threadIdx.x < r) c.hc[threadIdx.x] = coef((q - 1) * r + threadIdx.x);
+  __syncthreads();
+  for (int64_t e = (int64_t)team.rank * kThreads + threadIdx.x; e < (int64_t)n * n; e += (int64_t)team.size * kThreads) {
+    const int i = (int)(e / n), k = (int)(e - (int64_t)i * n);
+    double v = (i == k) ? c.hc[0] : 0.0;
+    for (int t = 1; t < r; ++t) v = fma(c.hc[t], P[(size_t)(t - 1) * ldm + e], v);
+    T0[e] = v;
+  }
+  if (!team.sync(&c.sync_ok)) return false;
+  double* Tc = T0;
+  double* Tn = T1;
+  for (int i = q - 2; i >= 0; --i) {
+    if (threadIdx.x < r) c.hc[threadIdx.x] = coef(i * r + threadIdx.x);
+    __syncthreads();
+    MmEpi epi{r, P, ldm};
+    mm_team(Tc, P + (size_t)(r - 1) * ldm, Tn, n, team.rank, team.size, c, epi, sA, sB);
+    if (!team.sync(&c.sync_ok)) return false;
+    double* t = Tc; Tc = Tn; Tn = t;
+  }
+  // squarings: all but the last in full
+  const int ssq = c.s_sq;
+  for (int k = 0; k + 1 < ssq || (a.expm_only && k < ssq); ++k) {
+    mm_team(Tc, Tc, Tn, n, team.rank, team.size, c, none, sA, sB);
+    if (!team.sync(&c.sync_ok)) return false;
+    double* t = Tc; Tc = Tn; Tn = t;
+  }
+  if (a.expm_only) {
+    for (int64_t e = (int64_t)team.rank * kThreads + threadIdx.x; e < (int64_t)n * n; e += (int64_t)team.size * kThreads)
+      a.expm_out[e] = Tc[e];
+    return team.sync(&c.sync_ok);
+  }
+  // last squaring (or none): only F(:,1) and F(j, j+1) are needed
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int jj = c.j;  // 1-based j: F(j, j+1) is (jj-1, jj) 0-based
+  for (int row = team.rank * kWarps + warp; row <= n; row += team.size * kWarps) {
+    // rows 0..n-1: F(row, 0); row n: F(jj-1, jj)
+    const int ri = row < n ? row : jj - 1;
+    const int ck = row < n ? 0 : jj;
+    double s = 0.0;
+    if (ssq > 0) {
+      for (int l = lane; l < n; l += 32) s = fma(Tc[(size_t)ri * n + l], Tc[(size_t)l * n + ck], s);
+      s = warp_sum(s);
+    } else {
+      s = Tc[(size_t)ri * n + ck];
+    }
+    if (lane == 0) a.fvec[row < n ? row : a.m_max + 1] = s;
+  }
+  return team.sync(&c.sync_ok);
+}
+
+template <typename T, int KIND, class Team>
+__device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn) {
+  const int tid = threadIdx.x;
+  const int64_t N = a.N;
+  const int p = a.p;
+  const int64_t M = N + p;
+  // contiguous row range of this rank
+  const int64_t chunk = (N + team.size - 1) / team.size;
+  const int64_t r0 = (int64_t)team.rank * chunk;
+  const int64_t r1 = r0 + chunk < N ? r0 + chunk : N;
+  const bool lead = team.rank == 0;
+  int parity = 0;
+  T* V = (T*)a.V;
+  const size_t ldv = (size_t)a.ldv;
+  const int ldh = a.m_max + 2;
+
+  if (tid == 0) {
+    c.status = ST_OK;
+    c.done = 0;
+    c.substeps = c.rejected = c.matvecs = c.iters = c.expm_calls = 0;
+    c.eps_last = 0.0;
+  }
+  __syncthreads();
+
+  if (a.expm_only) {
+    expm_phase<Team>(a, team, c, parity, smem_dyn);
+    return;
+  }
+
+  // ---- setup (section 3.7): ||B||_1 = max_k sum_i |b_k,i|; w = b_0 (Algorithm 1 line 8)
+  {
+    double acc[kRegK];
+    for (int base = 1; base <= p; base += kRegK) {
+      const int cnt = p - base + 1 < kRegK ? p - base + 1 : kRegK;
+#pragma unroll
+      for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+      for (int64_t r = r0 + tid; r < r1; r += kThreads)
+#pragma unroll
+        for (int k = 0; k < kRegK; ++k)
+          if (k < cnt) acc[k] += fabs(__ldg(a.b[base + k] + r));
+      block_reduce(c, acc, cnt, base - 1);
+    }
+    if (a.w != a.b[0])
+      for (int64_t r = r0 + tid; r < r1; r += kThreads) a.w[r] = __ldg(a.b[0] + r);
+    if (p > 0) {
+      if (!finish_reduce<Team>(team, c, a.partials, parity, p)) goto stop;
+    } else {
+      if (!team.sync(&c.sync_ok)) goto stop;
+    }
+    if (tid == 0) {
+      double nb = 0.0;
+      for (int k = 0; k < p; ++k) nb = c.red[k] > nb ? c.red[k] : nb;
+      c.nu = 1.0;
+      c.mu = 1.0;
+      if (p >= 1 && a.normalize && nb > 0.0) {
+        const int e = ceil_log2(nb);
+        c.nu = ldexp(1.0, -e);
+        c.mu = ldexp(1.0, e);
+      }
+      // Algorithm 1 lines 2-5
+      int m = a.m_init < a.m_max ? a.m_init : a.m_max;
+      c.m = m > a.m_min ? m : a.m_min;
+      c.tau = a.T_end;
+      c.t_now = 0.0;
+      c.j = 0;
+    }
+    __syncthreads();
+  }
+
+  while (c.t_now < a.T_end) {  // Algorithm 1 line 9
+    if (c.iters >= a.max_iters || c.substeps >= a.max_substeps) {
+      if (tid == 0) c.status = ST_ENOTCONV;
+      __syncthreads();
+      break;
+    }
+    if (c.j == 0) {
+      // ---- new substep: tail (line 13 + corrigendum, eq 47, times mu), beta = ||[w; tail]||, V_1
+      if (tid == 0) {
+        if (c.tau > a.T_end - c.t_now) c.tau = a.T_end - c.t_now;
+        for (int t = 0; t < p; ++t) {
+          const int e = p - 1 - t;
+          double v = 1.0;
+          for (int i = 1; i <= e; ++i) v *= c.t_now / (double)i;
+          c.tail[t] = c.mu * v;
+        }
+        c.have_prev = 0;
+        c.kappa = 2.0;
+        c.qp1_est = 0.0;
+      }
+      __syncthreads();
+      double acc[kRegK];
+#pragma unroll
+      for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+      for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+        const double x = a.w[r];
+        acc[0] = fma(x, x, acc[0]);
+      }
+      if (lead && tid == 0)
+        for (int t = 0; t < p; ++t) acc[0] = fma(c.tail[t], c.tail[t], acc[0]);
+      block_reduce(c, acc, 1, 0);
+      if (!finish_reduce<Team>(team, c, a.partials, parity, 1)) goto stop;
+      if (tid == 0) c.beta = sqrt(c.red[0]);
+      __syncthreads();
+      if (c.beta == 0.0) {  // v = 0 maps to 0
+        for (int64_t r = r0 + tid; r < r1; r += kThreads) a.w[r] = 0.0;
+        break;
+      }
+      {
+        const double ib = 1.0 / c.beta;  // Algorithm 1 line 14
+        for (int64_t r = r0 + tid; r < r1; r += kThreads) V[r] = (T)(a.w[r] * ib);
+        if (lead && tid < p) V[N + tid] = (T)(c.tail[tid] * ib);
+      }
+      if (!team.sync(&c.sync_ok)) goto stop;
+    }
+
+    // ---- Algorithm 2: IOP steps while j < m
+    if (tid == 0) c.breakdown = 0;
+    __syncthreads();
+    while (c.j < c.m) {
+      const int j = c.j + 1;  // step j builds v_{j+1} (slot j) from v_j (slot j-1)
+      const int i0 = j - a.m_o + 1 < 1 ? 1 : j - a.m_o + 1;
+      const int nwin = j - i0 + 1;
+      const T* vj = V + (size_t)(j - 1) * ldv;
+      T* x = V + (size_t)j * ldv;
+      if (tid < p) c.tail[tid] = (double)vj[N + tid];
+      __syncthreads();
+      // pass 0 computes x = A~ v_j, stores it raw, and reduces <v_i, x>, <x, x>, <v_j, v_i> for the
+      // first kChunk window entries; later passes reread x for further window entries (m_o > kChunk).
+      const int Ktot = 2 * nwin + 1;
+      for (int cb = 0; cb < nwin; cb += kChunk) {
+        const int cnt = nwin - cb < kChunk ? nwin - cb : kChunk;
+        double acc[kRegK];
+#pragma unroll
+        for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+        const T* vw[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) vw[u] = V + (size_t)(i0 + cb + (u < cnt ? u : 0) - 1) * ldv;
+        for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
+          // rows r1..r1+p-1 of the lead rank stand for the tail rows N..N+p-1
+          const bool tailrow = r >= r1;
+          const int64_t rr = tailrow ? N + (r - r1) : r;
+          T xv;
+          if (cb == 0) {
+            if (!tailrow) {
+              T s = apply_row<T, KIND>(a.op, vj, rr);
+              for (int t = 0; t < p; ++t) s += T(c.nu * c.tail[t]) * T(__ldg(a.b[p - t] + rr));
+              xv = s;
+            } else {
+              const int t = (int)(rr - N);
+              xv = t + 1 < p ? (T)c.tail[t + 1] : T(0);
+            }
+            x[rr] = xv;
+          } else {
+            xv = x[rr];
+          }
+          const double xd = (double)xv;
+          const double vjd = (double)vj[rr];
+#pragma unroll
+          for (int u = 0; u < kChunk; ++u) {
+            if (u < cnt) {
+              const double vi = (double)vw[u][rr];
+              acc[u] = fma(vi, xd, acc[u]);
+              acc[kChunk + u] = fma(vjd, vi, acc[kChunk + u]);
+            }
+          }
+          if (cb == 0) acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
+        }
+        // scatter into the global layout: d at [cb + u], |x|^2 at [nwin], g at [nwin + 1 + cb + u]
+        block_reduce(c, acc, 2 * kChunk + 1, 0);
+        if (tid == 0) {  // stage this pass in red (free until the all-reduce below)
+          for (int u = 0; u < cnt; ++u) {
+            c.red[cb + u] = c.blk[u];
+            c.red[nwin + 1 + cb + u] = c.blk[kChunk + u];
+          }
+          if (cb == 0) c.red[nwin] = c.blk[2 * kChunk];
+        }
+        __syncthreads();
+      }
+      for (int k = tid; k < Ktot; k += kThreads) c.blk[k] = c.red[k];
+      __syncthreads();
+      if (!finish_reduce<Team>(team, c, a.partials, parity, Ktot)) goto stop;
+      // ---- MGS coefficients from CGS dots and the Gram entries (Algorithm 2 lines 7-10):
+      // h_i = <v_i, x> - sum_{k<i} h_k <v_i, v_k>;  ||x - sum h_i v_i||^2 expanded over the window
+      if (tid == 0) {
+        const double nx2 = c.red[nwin];
+        auto G = [&](int i, int k) -> double {  // <v_i, v_k>, i, k in the window, 1-based
+          if (i < k) { int t = i; i = k; k = t; }
+          if (i == j) return c.red[nwin + 1 + (k - i0)];
+          return a.gram[(size_t)(i - 1) * a.m_o + (i - k)];
+        };
+        for (int u = 0; u < nwin; ++u) {
+          const int i = i0 + u;
+          double h = c.red[u];
+          for (int v = 0; v < u; ++v) h -= c.hcoef[v] * G(i, i0 + v);
+          c.hcoef[u] = h;
+        }
+        double s2 = nx2;
+        for (int u = 0; u < nwin; ++u) s2 -= 2.0 * c.hcoef[u] * c.red[u];
+        for (int u = 0; u < nwin; ++u)
+          for (int v = 0; v < nwin; ++v) s2 += c.hcoef[u] * c.hcoef[v] * G(i0 + u, i0 + v);
+        c.recompute = !(s2 > 1e-6 * nx2);
+        c.s = c.recompute ? 0.0 : sqrt(s2);
+        c.nx2_pre = nx2;  // ||A~ v_j||^2 for the breakdown test
+        c.i0 = i0;
+        c.nwin = nwin;
+        // record Gram row j: <v_j, v_{j-o}> for o = 0..nwin-1
+        if (lead)
+          for (int u = 0; u < nwin; ++u) a.gram[(size_t)(j - 1) * a.m_o + (j - (i0 + u))] = c.red[nwin + 1 + u];
+      }
+      __syncthreads();
+      const double nx2_pre = c.nx2_pre;
+      if (c.recompute) {
+        // explicit norm of x - sum h_i v_i (cancellation guard)
+        double acc[kRegK];
+#pragma unroll
+        for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+        for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
+          const int64_t rr = r >= r1 ? N + (r - r1) : r;
+          T xv = x[rr];
+          for (int u = 0; u < c.nwin; ++u) xv -= T(c.hcoef[u]) * V[(size_t)(c.i0 + u - 1) * ldv + rr];
+          const double xd = (double)xv;
+          acc[0] = fma(xd, xd, acc[0]);
+        }
+        block_reduce(c, acc, 1, 0);
+        if (!finish_reduce<Team>(team, c, a.partials, parity, 1)) goto stop;
+        if (tid == 0) c.s = sqrt(c.red[0]);
+        __syncthreads();
+      }
+      if (tid == 0) {
+        c.matvecs += 1;
+        double ca = 0.0;
+        for (int u = 0; u < c.nwin; ++u) ca += fabs(c.hcoef[u]);
+        c.colabs[j] = ca;
+        if (lead)
+          for (int u = 0; u < c.nwin; ++u) a.H[(size_t)(c.i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
+        c.j = j;
+        if (c.s <= a.bd_tol * sqrt(nx2_pre)) {  // happy breakdown (Algorithm 2 lines 12-15)
+          c.breakdown = 1;
+          c.sub[j] = 0.0;
+        } else {
+          c.sub[j] = c.s;
+          c.rs = 1.0 / c.s;
+          if (lead) a.H[(size_t)j * ldh + (j - 1)] = c.s;
+        }
+      }
+      __syncthreads();
+      if (c.breakdown) break;
+      // ---- v_{j+1} = (1/s) (x - sum_i h_i v_i) in MGS order (lines 9, 16-17)
+      for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
+        const int64_t rr = r >= r1 ? N + (r - r1) : r;
+        T xv = x[rr];
+        for (int u = 0; u < c.nwin; ++u) xv -= T(c.hcoef[u]) * V[(size_t)(c.i0 + u - 1) * ldv + rr];
+        x[rr] = xv * T(c.rs);
+      }
+      if (!team.sync(&c.sync_ok)) goto stop;
+    }
+
+    // ---- Algorithm 1 lines 17-18: F = exp(tau H~)
+    if (!expm_phase<Team>(a, team, c, parity, smem_dyn)) goto stop;
+
+    // ---- lines 19-22: estimate (eq 36), omega (eq 39), Algorithm 4 (sections 3.6.1, 3.6.2)
+    if (tid == 0) {
+      const double delta = 1.4, gamma = 0.9, gamma_max = 0.6;
+      const int j = c.j;
+      c.expm_calls += 1;
+      double eps = 0.0, omega = 0.0;
+      if (!c.breakdown) {
+        eps = c.beta * c.sub[j] * fabs(a.fvec[a.m_max + 1]);
+        omega = a.T_end * eps / (c.tau * a.tol);
+      }
+      c.eps_last = eps;
+      const int accepted = omega <= delta;
+      const double t_next = accepted ? c.t_now + c.tau : c.t_now;
+      const double remaining = a.T_end - t_next;
+      if (!accepted && c.have_prev) {
+        if (j != c.prev_j && c.tau == c.prev_tau) {
+          const double k = pow(omega / c.prev_omega, 1.0 / (double)(c.prev_j - j));  // eq 45
+          c.kappa = (isfinite(k) && k > 1.0) ? k : 2.0;
+        } else if (j == c.prev_j && c.tau != c.prev_tau) {
+          const double e = log(eps / c.prev_eps) / log(c.tau / c.prev_tau);  // eq 43 (order q + 1)
+          c.qp1_est = (isfinite(e) && e > 0.0) ? e : 0.0;
+        }
+      }
+      const double qp1 = c.qp1_est > 0.0 ? c.qp1_est : (double)j / 4.0;
+      double tau_new;
+      int m_new;
+      if (c.breakdown) {
+        tau_new = c.tau < remaining ? c.tau : remaining;
+        m_new = c.m;
+      } else if (j == a.m_max) {
+        if (omega > delta) {
+          m_new = j;
+          tau_new = c.tau * pow(gamma_max / omega, 1.0 / qp1);
+          if (tau_new < c.tau / 5.0) tau_new = c.tau / 5.0;
+          if (tau_new > remaining) tau_new = remaining;
+        } else {
+          m_new = c.m;
+          tau_new = c.tau * pow(gamma / omega, 1.0 / qp1);
+          if (!(tau_new <= 5.0 * c.tau)) tau_new = 5.0 * c.tau;
+          if (tau_new < c.tau / 5.0) tau_new = c.tau / 5.0;
+          if (tau_new > remaining) tau_new = remaining;
+        }
+      } else {
+        tau_new = c.tau;
+        double mn = (double)c.m + log(omega / gamma) / log(c.kappa);  // eq 46
+        const double lo = floor(0.75 * (double)c.m), hi = ceil(4.0 * (double)c.m / 3.0);
+        if (!(mn >= lo)) mn = lo;
+        if (mn > hi) mn = hi;
+        mn = ceil(mn);
+        if (mn < a.m_min) mn = a.m_min;
+        if (mn > a.m_max) mn = a.m_max;
+        m_new = (int)mn;
+      }
+      if (lead && a.trace && *a.trace_len < a.trace_cap) {
+        TraceRec& tr = a.trace[*a.trace_len];
+        tr.substep = c.substeps; tr.j = j; tr.accepted = accepted; tr.breakdown = c.breakdown; tr.m_new = m_new;
+        tr.tau = c.tau; tr.t_now = c.t_now; tr.eps = eps; tr.omega = omega; tr.tau_new = tau_new;
+        *a.trace_len += 1;
+      }
+      c.iters += 1;
+      c.accepted = accepted;
+      if (accepted) {
+        if (c.tau >= a.T_end - c.t_now || t_next >= a.T_end) c.t_now = a.T_end;
+        else c.t_now = t_next;
+        c.substeps += 1;
+      } else {
+        c.rejected += 1;
+        c.have_prev = 1; c.prev_j = j; c.prev_tau = c.tau; c.prev_omega = omega; c.prev_eps = eps;
+      }
+      c.hc[0] = c.beta;  // beta of this substep for the update
+      // a non-finite estimate, or a rejection that changes neither m nor tau, would repeat forever
+      if (!isfinite(omega) || (!accepted && m_new <= j && !(tau_new < c.tau))) {
+        c.status = ST_ENOTCONV;
+        c.done = 1;
+      }
+      c.tau = tau_new;
+      c.m = m_new;
+    }
+    __syncthreads();
+    if (c.done) break;
+    if (c.accepted) {
+      // ---- Algorithm 3 (Task II line): w = beta V(1:N, 1:j) F(1:j, 1)
+      const int j = c.j;
+      for (int k = tid; k < j; k += kThreads) c.hcoef[k] = a.fvec[k];
+      __syncthreads();
+      const double beta = c.hc[0];
+      for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+        double s = 0.0;
+        for (int k = 0; k < j; ++k) s = fma((double)V[(size_t)k * ldv + r], c.hcoef[k], s);
+        a.w[r] = beta * s;
+      }
+      if (tid == 0) c.j = 0;
+      __syncthreads();
+    }
+  }
+stop:
+  __syncthreads();
+  if (lead && tid == 0) {
+    int st = c.status;
+    if (a.abort_flag && ld_volatile_int(a.abort_flag)) st = ld_volatile_int(a.abort_flag);
+    a.stats[0] = c.substeps; a.stats[1] = c.rejected; a.stats[2] = c.matvecs; a.stats[3] = c.iters;
+    a.stats[4] = c.expm_calls; a.stats[5] = c.m; a.stats[6] = st;
+    a.stats_d[0] = c.eps_last;
+  }
+}
+
+}  // namespace kiops_dev

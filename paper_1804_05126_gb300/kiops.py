@@ -1,0 +1,378 @@
+"""Thin Python binding of the C ABI in include/kiops.h (ctypes; argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``_build/libkiops.so``; this module only converts
+arguments.  Functions with the C names (``kiops_create``, ``kiops_solve`` ...) map one to one onto the
+C entry points; :class:`Solver` and :class:`Operator` wrap them for torch CUDA tensors (PyTorch supplies
+device memory and streams).  There is no CPU fallback: :func:`lib` raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+KIOPS_MAX_P = 16
+KIOPS_MAX_M = 256
+STATUS = {0: "KIOPS_OK", 1: "KIOPS_EINVAL", 2: "KIOPS_ENOMEM", 3: "KIOPS_ENOTCONV", 4: "KIOPS_ETIMEOUT",
+          5: "KIOPS_ECUDA", 6: "KIOPS_EBUSY"}
+FP64, FP32_BASIS = 0, 1
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CTA = 0, 1, 2
+
+
+class KiopsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class kiops_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("m_min", C.c_int), ("m_max", C.c_int),
+                ("normalize_B", C.c_int), ("breakdown_tol", C.c_double), ("max_substeps", C.c_int64),
+                ("max_iterations", C.c_int64), ("timeout_s", C.c_double), ("engine", C.c_int),
+                ("grid_blocks", C.c_int)]
+
+
+class kiops_stats(C.Structure):
+    _fields_ = [("substeps", C.c_int64), ("rejected", C.c_int64), ("matvecs", C.c_int64),
+                ("iterations", C.c_int64), ("expm_calls", C.c_int64), ("m_last", C.c_int), ("engine", C.c_int),
+                ("grid_blocks", C.c_int), ("status", C.c_int), ("err_est", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class kiops_trace_rec(C.Structure):
+    _fields_ = [("substep", C.c_int64), ("j", C.c_int), ("accepted", C.c_int), ("breakdown", C.c_int),
+                ("m_new", C.c_int), ("tau", C.c_double), ("t_now", C.c_double), ("eps", C.c_double),
+                ("omega", C.c_double), ("tau_new", C.c_double)]
+
+
+class kiops_stencil2d_desc(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nspecies", C.c_int), ("periodic", C.c_int),
+                ("coef", (C.c_double * 5) * 2), ("diag", (C.c_void_p * 2) * 2)]
+
+
+class kiops_stencil3d_desc(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("periodic", C.c_int),
+                ("coef", C.c_double * 7), ("diag", C.c_void_p)]
+
+
+class kiops_request(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("tau", C.c_double), ("p", C.c_int), ("b", C.POINTER(C.c_void_p)),
+                ("tol", C.c_double), ("m_init", C.c_int), ("m_o", C.c_int), ("prec", C.c_int), ("w", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "kiops_config_default": ([C.POINTER(kiops_config)], C.c_int),
+    "kiops_constants": ([C.POINTER(C.c_double)], C.c_int),
+    "kiops_create": ([C.POINTER(C.c_void_p), C.POINTER(kiops_config)], C.c_int),
+    "kiops_destroy": ([C.c_void_p], C.c_int),
+    "kiops_last_error": ([C.c_void_p], C.c_char_p),
+    "kiops_status_string": ([C.c_int], C.c_char_p),
+    "kiops_attach_workspace": ([C.c_void_p, C.c_void_p, C.c_size_t], C.c_int),
+    "kiops_workspace_size": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+    "kiops_op_csr": ([C.c_void_p, C.POINTER(C.c_void_p), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+                     C.c_int),
+    "kiops_op_stencil2d": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(kiops_stencil2d_desc)], C.c_int),
+    "kiops_op_stencil3d": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(kiops_stencil3d_desc)], C.c_int),
+    "kiops_op_destroy": ([C.c_void_p], C.c_int),
+    "kiops_op_size": ([C.c_void_p], C.c_int64),
+    "kiops_op_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "kiops_solve": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int, C.c_int,
+                     C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
+    "kiops_solve_traced": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
+                            C.c_int, C.c_int, C.c_void_p, C.POINTER(kiops_stats), C.POINTER(kiops_trace_rec),
+                            C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "kiops_solve_host": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
+                          C.c_int, C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
+    "kiops_solve_batch": ([C.c_void_p, C.c_int, C.POINTER(kiops_request), C.POINTER(kiops_stats)], C.c_int),
+    "kiops_expm": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+}
+
+
+def lib(build_if_missing: bool = False):
+    """Load libkiops.so (raises if it is not built; never falls back to anything else)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"CUDA library not built ({_build.LIB}); run paper_1804_05126_gb300.build.build()")
+            L = C.CDLL(_build.LIB)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+# ---------------------------------------------------------------- same-name wrappers of the C ABI
+def kiops_config_default() -> kiops_config:
+    cfg = kiops_config()
+    lib().kiops_config_default(C.byref(cfg))
+    return cfg
+
+
+def kiops_constants() -> list[float]:
+    out = (C.c_double * 6)()
+    lib().kiops_constants(out)
+    return list(out)
+
+
+def kiops_create(cfg: kiops_config | None = None) -> int:
+    h = C.c_void_p()
+    st = lib().kiops_create(C.byref(h), C.byref(cfg) if cfg is not None else None)
+    if st:
+        raise KiopsError(st, "kiops_create failed")
+    return h.value
+
+
+def kiops_destroy(ctx: int) -> None:
+    lib().kiops_destroy(ctx)
+
+
+def kiops_last_error(ctx: int) -> str:
+    return lib().kiops_last_error(ctx).decode()
+
+
+def _check(ctx, st, what):
+    if st:
+        raise KiopsError(st, f"{what}: {kiops_last_error(ctx)}")
+
+
+def kiops_op_csr(ctx: int, n: int, nnz: int, rowptr: int, colind: int, vals: int) -> int:
+    h = C.c_void_p()
+    _check(ctx, lib().kiops_op_csr(ctx, C.byref(h), n, nnz, rowptr, colind, vals), "kiops_op_csr")
+    return h.value
+
+
+def kiops_op_stencil2d(ctx: int, desc: kiops_stencil2d_desc) -> int:
+    h = C.c_void_p()
+    _check(ctx, lib().kiops_op_stencil2d(ctx, C.byref(h), C.byref(desc)), "kiops_op_stencil2d")
+    return h.value
+
+
+def kiops_op_stencil3d(ctx: int, desc: kiops_stencil3d_desc) -> int:
+    h = C.c_void_p()
+    _check(ctx, lib().kiops_op_stencil3d(ctx, C.byref(h), C.byref(desc)), "kiops_op_stencil3d")
+    return h.value
+
+
+def kiops_op_destroy(op: int) -> None:
+    lib().kiops_op_destroy(op)
+
+
+def kiops_op_size(op: int) -> int:
+    return int(lib().kiops_op_size(op))
+
+
+def kiops_op_apply(ctx: int, op: int, x_ptr: int, y_ptr: int) -> None:
+    _check(ctx, lib().kiops_op_apply(ctx, op, x_ptr, y_ptr), "kiops_op_apply")
+
+
+def _ptr_array(ptrs):
+    arr = (C.c_void_p * len(ptrs))(*ptrs)
+    return arr
+
+
+def kiops_solve(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, prec, w_ptr) -> dict:
+    st = kiops_stats()
+    _check(ctx, lib().kiops_solve(ctx, op, tau, p, _ptr_array(b_ptrs), tol, m_init, m_o, prec, w_ptr, C.byref(st)),
+           "kiops_solve")
+    return st.as_dict()
+
+
+def kiops_solve_traced(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, prec, w_ptr, trace_cap=4096):
+    st = kiops_stats()
+    tr = (kiops_trace_rec * trace_cap)()
+    n = C.c_int64(0)
+    _check(ctx, lib().kiops_solve_traced(ctx, op, tau, p, _ptr_array(b_ptrs), tol, m_init, m_o, prec, w_ptr,
+                                         C.byref(st), tr, trace_cap, C.byref(n)), "kiops_solve_traced")
+    recs = [{f: getattr(r, f) for f, _ in kiops_trace_rec._fields_} for r in tr[: n.value]]
+    for r in recs:
+        r["accepted"] = bool(r["accepted"])
+        r["breakdown"] = bool(r["breakdown"])
+    return st.as_dict(), recs
+
+
+def kiops_solve_host(ctx, op, tau, p, b_host_ptrs, tol, m_init, m_o, prec, w_host_ptr) -> dict:
+    st = kiops_stats()
+    _check(ctx, lib().kiops_solve_host(ctx, op, tau, p, _ptr_array(b_host_ptrs), tol, m_init, m_o, prec, w_host_ptr,
+                                       C.byref(st)), "kiops_solve_host")
+    return st.as_dict()
+
+
+def kiops_solve_batch(ctx, reqs: list[kiops_request]) -> list[dict]:
+    n = len(reqs)
+    arr = (kiops_request * n)(*reqs)
+    stats = (kiops_stats * max(n, 1))()
+    _check(ctx, lib().kiops_solve_batch(ctx, n, arr, stats), "kiops_solve_batch")
+    return [stats[i].as_dict() for i in range(n)]
+
+
+def kiops_expm(ctx, n, a_ptr, f_ptr) -> None:
+    _check(ctx, lib().kiops_expm(ctx, n, a_ptr, f_ptr), "kiops_expm")
+
+
+def kiops_attach_workspace(ctx, ptr, nbytes) -> None:
+    _check(ctx, lib().kiops_attach_workspace(ctx, ptr, nbytes), "kiops_attach_workspace")
+
+
+def kiops_workspace_size(ctx, op, p, m_o, prec) -> int:
+    out = C.c_size_t(0)
+    _check(ctx, lib().kiops_workspace_size(ctx, op, p, m_o, prec, C.byref(out)), "kiops_workspace_size")
+    return int(out.value)
+
+
+# ---------------------------------------------------------------- torch convenience layer
+class Operator:
+    """A device operator built from a workload description (see workloads.py); owns its device arrays."""
+
+    def __init__(self, solver: "Solver", desc: dict):
+        import torch
+        self.solver = solver
+        self.desc = desc
+        self._keep = []
+        dev = solver.device
+        ctx = solver.ctx
+
+        def put(a, dtype):
+            t = torch.as_tensor(np.ascontiguousarray(a)).to(device=dev, dtype=dtype).contiguous()
+            self._keep.append(t)
+            return t.data_ptr()
+
+        k = desc["kind"]
+        if k == "csr":
+            self.handle = kiops_op_csr(ctx, int(desc["n"]), len(desc["vals"]), put(desc["rowptr"], torch.int32),
+                                       put(desc["colind"], torch.int32), put(desc["vals"], torch.float64))
+        elif k == "stencil2d":
+            d = kiops_stencil2d_desc()
+            d.nx, d.ny, d.nspecies, d.periodic = int(desc["nx"]), int(desc["ny"]), int(desc["nspecies"]), int(bool(desc["periodic"]))
+            for s in range(d.nspecies):
+                for c in range(5):
+                    d.coef[s][c] = float(desc["coef"][s][c])
+            for (r, c), arr in desc.get("diag", {}).items():
+                if arr is not None:
+                    d.diag[r][c] = put(arr, torch.float64)
+            self.handle = kiops_op_stencil2d(ctx, d)
+        elif k == "stencil3d":
+            d = kiops_stencil3d_desc()
+            d.nx, d.ny, d.nz, d.periodic = int(desc["nx"]), int(desc["ny"]), int(desc["nz"]), int(bool(desc["periodic"]))
+            for c in range(7):
+                d.coef[c] = float(desc["coef"][c])
+            d.diag = put(desc["diag"], torch.float64) if desc.get("diag") is not None else None
+            self.handle = kiops_op_stencil3d(ctx, d)
+        else:
+            raise ValueError(f"operator kind {k!r} has no device implementation")
+        self.n = kiops_op_size(self.handle)
+
+    def apply(self, x):
+        import torch
+        y = torch.empty_like(x)
+        kiops_op_apply(self.solver.ctx, self.handle, x.data_ptr(), y.data_ptr())
+        return y
+
+    def close(self):
+        if getattr(self, "handle", None):
+            kiops_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """A kiops context on a torch CUDA device/stream."""
+
+    def __init__(self, device: int = 0, stream=None, m_min: int = 10, m_max: int = 128, normalize_B: bool = True,
+                 breakdown_tol: float = 1e-12, max_substeps: int = 10**6, max_iterations: int = 10**5,
+                 timeout_s: float = 10.0, engine: int = ENGINE_AUTO, grid_blocks: int = 0):
+        import torch
+        self.device = torch.device("cuda", device)
+        cfg = kiops_config_default()
+        cfg.device = device
+        cfg.stream = stream.cuda_stream if stream is not None else None
+        cfg.m_min, cfg.m_max, cfg.normalize_B = m_min, m_max, int(normalize_B)
+        cfg.breakdown_tol, cfg.max_substeps, cfg.max_iterations = breakdown_tol, max_substeps, max_iterations
+        cfg.timeout_s, cfg.engine, cfg.grid_blocks = timeout_s, engine, grid_blocks
+        self.cfg = cfg
+        self.ctx = kiops_create(cfg)
+
+    def operator(self, desc: dict) -> Operator:
+        return Operator(self, desc)
+
+    @staticmethod
+    def _prec(precision) -> int:
+        return FP32_BASIS if precision in (FP32_BASIS, "fp32_basis", "fp32") else FP64
+
+    def solve(self, op: Operator, tau: float, b, tol: float, m_init: int = 10, m_o: int = 2, precision="fp64",
+              w=None, trace: bool = False, trace_cap: int = 4096):
+        """b: (p+1, N) float64 CUDA tensor (natural order b_0..b_p); returns (w, stats[, trace])."""
+        import torch
+        assert b.is_cuda and b.dtype == torch.float64 and b.is_contiguous()
+        p = b.shape[0] - 1
+        if w is None:
+            w = torch.empty(b.shape[1], dtype=torch.float64, device=b.device)
+        ptrs = [b[k].data_ptr() for k in range(p + 1)]
+        if trace:
+            st, tr = kiops_solve_traced(self.ctx, op.handle, tau, p, ptrs, tol, m_init, m_o, self._prec(precision),
+                                        w.data_ptr(), trace_cap)
+            return w, st, tr
+        st = kiops_solve(self.ctx, op.handle, tau, p, ptrs, tol, m_init, m_o, self._prec(precision), w.data_ptr())
+        return w, st
+
+    def solve_host(self, op: Operator, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_o: int = 2,
+                   precision="fp64", w: np.ndarray | None = None):
+        """b: (p+1, N) float64 host array (pinned or pageable); w: host output."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        p = b.shape[0] - 1
+        if w is None:
+            w = np.empty(b.shape[1], dtype=np.float64)
+        ptrs = [b[k].ctypes.data for k in range(p + 1)]
+        st = kiops_solve_host(self.ctx, op.handle, tau, p, ptrs, tol, m_init, m_o, self._prec(precision), w.ctypes.data)
+        return w, st
+
+    def solve_batch(self, items):
+        """items: list of (op, tau, b_tensor, tol, m_init, m_o, precision, w_tensor)."""
+        reqs, keep = [], []
+        for (op, tau, b, tol, m_init, m_o, precision, w) in items:
+            p = b.shape[0] - 1
+            arr = _ptr_array([b[k].data_ptr() for k in range(p + 1)])
+            keep.append(arr)
+            reqs.append(kiops_request(op.handle, tau, p, C.cast(arr, C.POINTER(C.c_void_p)), tol, m_init, m_o,
+                                      self._prec(precision), w.data_ptr()))
+        return kiops_solve_batch(self.ctx, reqs)
+
+    def expm(self, a):
+        import torch
+        a = a.contiguous()
+        f = torch.empty_like(a)
+        kiops_expm(self.ctx, a.shape[0], a.data_ptr(), f.data_ptr())
+        return f
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            kiops_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

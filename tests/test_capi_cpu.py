@@ -1,0 +1,60 @@
+"""CPU checks of the boundary: the library builds for sm_103a, loads, and exports every entry point
+declared in include/kiops.h (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "kiops.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kiops_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1804_05126_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("kiops_create", "kiops_destroy", "kiops_solve", "kiops_op_csr", "kiops_op_stencil2d",
+                 "kiops_op_stencil3d", "kiops_solve_batch", "kiops_solve_host", "kiops_expm"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    from paper_1804_05126_gb300 import kiops
+    assert set(header_functions()) <= set(kiops.exported_symbols())
+    kiops.lib()
+
+
+def test_defaults_match_the_paper(libpath):
+    from paper_1804_05126_gb300 import kiops
+    from tests.golden_util import paper_constants
+    pc = paper_constants()
+    cfg = kiops.kiops_config_default()
+    assert cfg.m_min == pc["m_min_default"] and cfg.m_max == pc["m_max_default"]
+    delta, gamma, gamma_max, kappa, clip, m_o = kiops.kiops_constants()
+    assert (delta, gamma, gamma_max, kappa, clip, m_o) == (pc["delta"], pc["gamma"], pc["gamma_max"],
+                                                           pc["kappa_default"], pc["tau_clip_high"], pc["m_o_default"])
+
+
+def test_status_strings_and_null_handling(libpath):
+    from paper_1804_05126_gb300 import kiops
+    L = kiops.lib()
+    assert L.kiops_status_string(0) == b"ok"
+    assert L.kiops_destroy(None) == 1          # EINVAL, no crash
+    assert L.kiops_last_error(None) == b"NULL context"
+    assert L.kiops_config_default(None) == 1

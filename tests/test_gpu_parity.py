@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bar: relative 2-norm difference <= 10 * tol for FP64 solves (the stated tolerance of the workloads), and
+for the FP32-basis mode <= 10 * tol with tol the request's tolerance.  Decision traces (Krylov dimension
+of every iteration, accept/reject) are compared where both sides take the decisions in FP64.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1804_05126_gb300 import kiops, workloads as W  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1804_05126_gb300 import build
+    build.build()
+    s = kiops.Solver(device=0)
+    yield s
+    s.close()
+
+
+def gpu_solve(solver, P, trace=False, **kw):
+    op = solver.operator(P.op)
+    b = torch.as_tensor(P.b, device="cuda:0")
+    out = solver.solve(op, P.tau, b, P.tol, m_init=P.m_init, m_o=kw.pop("m_o", P.m_o),
+                       precision=kw.pop("precision", P.precision), trace=trace, **kw)
+    torch.cuda.synchronize()
+    w = out[0].cpu().numpy()
+    return (w,) + tuple(out[1:])
+
+
+def oracle_solve(P, **kw):
+    return oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=kw.pop("m_o", P.m_o), **kw)
+
+
+# ---------------------------------------------------------------- building blocks
+@pytest.mark.parametrize("n", [1, 2, 7, 11, 33, 64, 113, 129])
+@pytest.mark.parametrize("scale", [1e-3, 0.5, 4.0, 60.0, 900.0])
+def test_expm_matches_oracle(solver, n, scale):
+    rng = np.random.default_rng(n * 1000 + int(scale))
+    a = rng.standard_normal((n, n)) * scale / np.sqrt(n) - scale * np.eye(n)
+    ref = oracle.expm(a)
+    f = solver.expm(torch.as_tensor(a, device="cuda:0")).cpu().numpy()
+    assert rel(f, ref) <= 1e-12 * max(1.0, scale)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.laplacian_1d_csr(37),
+    lambda: W.adr2d(13, np.random.default_rng(1)),
+    lambda: W.gray_scott2d(9, np.random.default_rng(2)),
+    lambda: W.adr3d(6, -3.0, adv=(1.0, -2.0, 4.0)),
+    lambda: dict(W.adr3d(5, -1.0), periodic=True),
+])
+def test_operator_apply_matches_oracle(solver, make):
+    op_desc = make()
+    n = W.op_size(op_desc)
+    x = np.random.default_rng(3).standard_normal(n)
+    op = solver.operator(op_desc)
+    y = op.apply(torch.as_tensor(x, device="cuda:0")).cpu().numpy()
+    assert rel(y, oracle.apply(op_desc, x)) < 1e-14
+
+
+# ---------------------------------------------------------------- solves: the measured workloads
+def test_lap1d_csr_config_parity_and_trace(solver):
+    P = W.problem_lap1d()  # N = 400, p = 2, tau = 1e-3, tol = 1e-8, m_init = 10, m_o = 2
+    w, st, tr = gpu_solve(solver, P, trace=True)
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert st["status"] == 0
+    assert rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+    assert st["matvecs"] == st_ref["matvecs"] and st["substeps"] == st_ref["substeps"]
+
+
+def test_adr2d_reduced_parity_and_trace(solver):
+    P = W.problem_adr2d(n=48, seed=11)
+    w, st, tr = gpu_solve(solver, P, trace=True)
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+
+
+def test_adr2d_full_size_parity(solver):
+    P = W.problem_adr2d()  # 512 x 512, p = 4, tau = 1e-2, tol = 1e-8 (the benchmarked workload)
+    w, st, tr = gpu_solve(solver, P, trace=True)
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert st["status"] == 0
+    assert rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32_basis", 1e-6)])
+def test_gray_scott_reduced_parity(solver, precision, tol):
+    P = W.problem_gray_scott(n=40, seed=5, precision=precision, tol=tol, tau=1.0)
+    w, st = gpu_solve(solver, P)
+    w_ref, _, _ = oracle_solve(P)
+    assert st["status"] == 0
+    assert rel(w, w_ref) <= 10 * tol
+
+
+def test_3d_batch_cta_engine_parity(solver):
+    probs = W.batch_3d(count=6, seed=77, n_range=(6, 12))
+    items, ws = [], []
+    for P in probs:
+        op = solver.operator(P.op)
+        b = torch.as_tensor(P.b, device="cuda:0")
+        w = torch.empty(P.n, dtype=torch.float64, device="cuda:0")
+        items.append((op, P.tau, b, P.tol, P.m_init, P.m_o, "fp64", w))
+        ws.append((w, op, b))
+    stats = solver.solve_batch(items)
+    torch.cuda.synchronize()
+    for P, (w, _, _), st in zip(probs, ws, stats):
+        w_ref, st_ref, _ = oracle_solve(P)
+        assert st["status"] == 0
+        assert rel(w.cpu().numpy(), w_ref) <= 10 * P.tol
+        assert st["matvecs"] == st_ref["matvecs"]
+
+
+# ---------------------------------------------------------------- edge cases
+def test_tau_zero_returns_b0(solver):
+    P = W.problem_lap1d(n=50)
+    P.tau = 0.0
+    w, st = gpu_solve(solver, P)
+    assert np.array_equal(w, P.b[0]) and st["matvecs"] == 0
+
+
+def test_p0_plain_exponential(solver):
+    P = W.problem_adr2d(n=20, seed=2, p=0)
+    w, st = gpu_solve(solver, P)
+    w_ref, _, _ = oracle_solve(P)
+    assert rel(w, w_ref) <= 10 * P.tol
+
+
+def test_zero_operator_happy_breakdown(solver):
+    n, p = 37, 4
+    op = {"kind": "csr", "n": n, "rowptr": np.zeros(n + 1, np.int32), "colind": np.zeros(0, np.int32),
+          "vals": np.zeros(0)}
+    rng = np.random.default_rng(1)
+    P = W.Problem("zero", op, rng.standard_normal((p + 1, n)), 0.8, 1e-10)
+    w, st, tr = gpu_solve(solver, P, trace=True, m_o=p + 1)
+    from math import factorial
+    want = sum(P.tau**k / factorial(k) * P.b[k] for k in range(p + 1))
+    assert rel(w, want) < 1e-13
+    assert tr[0]["breakdown"] and tr[0]["j"] == p + 1
+
+
+@pytest.mark.parametrize("m_o", [1, 3, 4, 7, 200])
+def test_orthogonalisation_lengths(solver, m_o):
+    P = W.problem_adr2d(n=16, seed=4)
+    w, st = gpu_solve(solver, P, m_o=m_o)
+    w_ref, st_ref, _ = oracle_solve(P, m_o=m_o)
+    assert rel(w, w_ref) <= 10 * P.tol
+
+
+def test_ragged_and_tiny_sizes(solver):
+    for n in (1, 2, 3, 97, 1001):
+        P = W.problem_lap1d(n=n, seed=n)
+        w, st = gpu_solve(solver, P)
+        w_ref, _, _ = oracle_solve(P)
+        assert rel(w, w_ref) <= 10 * P.tol, n
+
+
+def test_substepping_with_small_m_max():
+    s = kiops.Solver(device=0, m_min=5, m_max=20)
+    P = W.problem_lap1d(n=200)
+    w, st, tr = gpu_solve(s, P, trace=True)
+    w_ref, st_ref, tr_ref = oracle.kiops(P.op, P.tau, P.b, P.tol, m_min=5, m_max=20)
+    assert st["substeps"] > 1 and st["substeps"] == st_ref["substeps"]
+    assert rel(w, w_ref) <= 10 * P.tol
+    s.close()
+
+
+def test_host_buffer_solve_matches_device_solve(solver):
+    P = W.problem_adr2d(n=32, seed=8)
+    w_dev, _ = gpu_solve(solver, P)
+    op = solver.operator(P.op)
+    w_host, st = solver.solve_host(op, P.tau, P.b, P.tol)
+    assert np.array_equal(w_host, w_dev)
+
+
+def test_cta_engine_matches_grid_engine():
+    P = W.problem_adr2d(n=20, seed=9)
+    s = kiops.Solver(device=0, engine=kiops.ENGINE_CTA)
+    w_cta, st = gpu_solve(s, P)
+    s.close()
+    w_ref, _, _ = oracle_solve(P)
+    assert st["engine"] == kiops.ENGINE_CTA and rel(w_cta, w_ref) <= 10 * P.tol
+
+
+def test_invalid_arguments_rejected(solver):
+    P = W.problem_lap1d(n=10)
+    op = solver.operator(P.op)
+    b = torch.as_tensor(P.b, device="cuda:0")
+    with pytest.raises(kiops.KiopsError) as e:
+        solver.solve(op, P.tau, b, -1.0)
+    assert e.value.status == 1
+    with pytest.raises(kiops.KiopsError):
+        solver.solve(op, -1.0, b, 1e-8)
+    with pytest.raises(kiops.KiopsError):
+        solver.solve(op, P.tau, b, 1e-8, m_o=0)
+
+
+def test_not_converged_reports_enotconv():
+    s = kiops.Solver(device=0, m_min=2, m_max=4, max_iterations=3)
+    P = W.problem_lap1d(n=100)
+    with pytest.raises(kiops.KiopsError) as e:
+        gpu_solve(s, P)
+    assert e.value.status == 3
+    s.close()
