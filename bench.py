@@ -1,0 +1,297 @@
+"""Benchmark: adaptive KIOPS phi-solves on GB300.
+
+A step is one complete solve w = sum_k tau^k phi_k(tau A) b_k of the 512 x 512 2D advection-diffusion-
+reaction Jacobian workload (N = 262144, p = 4, tau = 1e-2, tol = 1e-8, m_init = 10, m_o = 2, FP64), with
+every input resident in HBM.  One step is one launch of the persistent solve kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (one solve stream per GPU, no
+collective on the data path): value = solves of all ranks / slowest rank's time, scaling "weak".
+``--impl reference`` times the plain FP64 CPU oracle (the reference implementation of the method) on
+the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1804_05126_gb300 import workloads as W  # noqa: E402
+
+METRIC = "phi-solves/s (adaptive KIOPS, FP64, tol 1e-8)"
+UNIT = "solves/s"
+WORKLOAD = "adr2d_512x512_dirichlet_p4_tau1e-2_tol1e-8_fp64"
+
+
+def workload():
+    return W.problem_adr2d(n=512, seed=1002, p=4, tau=1e-2, tol=1e-8)
+
+
+def config_dict(P, l2="flushed between timed solves (256 MiB write)"):
+    return {"workload": WORKLOAD, "N": P.n, "p": P.p, "tau": P.tau, "tol": P.tol, "m_init": P.m_init, "m_o": P.m_o,
+            "m_max": 128, "operator": "matrix-free 5-point ADR stencil, eps=0.01, alpha=-10, gamma=100",
+            "l2": l2}
+
+
+# ------------------------------------------------------------------ algorithmic work model
+def algorithmic_model(P, stats):
+    """Bytes and FP64 flops one solve must move/do (independent of this implementation).
+
+    Per Krylov step (Algorithm 2): read v_j, v_{j-1} and the p columns of B, write v_{j+1}, read the
+    operator's reaction field: (p+3)*8*N + 8*N bytes.  Flops per step follow the paper's IOP cost model
+    (eq 41): 2 nz(A~) + (2p-1) N + p + 8 (N+p), with nz(A~) = 5N + pN + (p-1) for the 5-point stencil.
+    Per accepted substep (Algorithm 3 / start vector): read V(1:N,1:j), write w, read w, write v_1:
+    (8j + 8 + 16) N bytes and 2 j N flops.  Once per solve: ||B||_1 reads p N values.
+    """
+    N, p = P.n, P.p
+    steps, substeps = stats["matvecs"], stats["substeps"]
+    j_avg = 128  # every substep of this workload ends at m_max (see the recorded trace)
+    bytes_step = (p + 3) * 8 * N + 8 * N
+    nz = 5 * N + p * N + (p - 1)
+    flops_step = 2 * nz + (2 * p - 1) * N + p + 8 * (N + p)
+    bytes_sub = (8 * j_avg + 8 + 16) * N
+    flops_sub = 2 * j_avg * N
+    total_bytes = steps * bytes_step + substeps * bytes_sub + p * 8 * N
+    total_flops = steps * flops_step + substeps * flops_sub
+    return {"bytes_per_solve": total_bytes, "fp64_flops_per_solve": total_flops, "bytes_per_step": bytes_step,
+            "flops_per_step": flops_step}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def cpu_baseline(P, budget_s=12.0):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} complete solves of the {WORKLOAD} workload by the serial FP64 C oracle"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    P = workload()
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+        times.append(time.perf_counter() - t0)
+    value = len(times) / sum(times)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(P, l2="n/a (CPU)"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{len(times)} complete solves, serial FP64 C oracle on the host"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_1804_05126_gb300 import build as B
+    from paper_1804_05126_gb300 import kiops
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    stream = torch.cuda.Stream(device=dev)
+    P = workload()
+    solver = kiops.Solver(device=local, stream=stream)
+    op = solver.operator(P.op)
+    b = torch.as_tensor(P.b, device=dev).contiguous()
+    w = torch.empty(P.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            _, st = solver.solve(op, P.tau, b, P.tol, m_init=P.m_init, m_o=P.m_o, w=w)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches = 0
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))          # evict L2 between timed solves (not timed)
+                ev[i][0].record(stream)
+                _, st = solver.solve(op, P.tau, b, P.tol, m_init=P.m_init, m_o=P.m_o, w=w)
+                ev[i][1].record(stream)
+                launches += 1
+            stream.synchronize()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        times_ms = [a.elapsed_time(bb) for a, bb in ev]
+    total_s = sum(times_ms) / 1e3
+    t_max = total_s
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    solves_total = args.steps * world
+    value = solves_total / t_max
+
+    # end to end through the host-buffer entry point (pinned host inputs, copies inside the timed region)
+    bh = torch.as_tensor(P.b).pin_memory().numpy()
+    wh = torch.empty(P.n, dtype=torch.float64).pin_memory().numpy()
+    solver.solve_host(op, P.tau, bh, P.tol, w=wh)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve_host(op, P.tau, bh, P.tol, w=wh)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": solves_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(bh.nbytes),
+           "d2h_bytes_per_step": int(wh.nbytes)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    model = algorithmic_model(P, st)
+    mean_s = total_s / args.steps
+    pk = peaks()
+    fp64_peak_tflops = 1.25  # nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json
+    achieved_tflops = model["fp64_flops_per_solve"] / mean_s / 1e12
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get(WORKLOAD)
+        except Exception:
+            traffic = None
+    lat = sorted(times_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * mean_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": config_dict(P),
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "matvecs_per_solve": st["matvecs"], "substeps": st["substeps"], "rejected": st["rejected"],
+        "matvecs_per_s": st["matvecs"] * value, "hbm_gbs_effective": model["bytes_per_solve"] / mean_s / 1e9,
+        "hbm_frac_effective": model["bytes_per_solve"] / mean_s / 1e9 / pk.get("hbm_gbs", 6768.1),
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp64_peak_tflops, "traffic": traffic,
+                     "kernel": "kiops_solve_kernel<double, stencil2d, grid>",
+                     "note": "FP64 flops of the eq-41 IOP cost model + update, per solve / event-timed solve; "
+                             "peak = nominal FP64 (no measured FP64 peak on file)"},
+        "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "engine": {"blocks": st["grid_blocks"], "kind": "grid (persistent cooperative)"},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(P)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.steps > 10 and "--steps" not in " ".join(sys.argv):
+            args.steps = 10
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

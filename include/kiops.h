@@ -70,6 +70,7 @@ typedef struct {
   double timeout_s;        /* limit on any single device-side wait (default 10 s) */
   int engine;              /* kiops_engine (default AUTO) */
   int grid_blocks;         /* grid engine block count; 0 = as many as are co-resident */
+  int profile;             /* 1: fill kiops_stats.phase_cycles (device cycle counters, rank-0 view) */
 } kiops_config;
 
 typedef struct {
@@ -83,6 +84,10 @@ typedef struct {
   int grid_blocks;         /* blocks of the launch */
   int status;              /* kiops_status of the device run */
   double err_est;          /* last error estimate eps_m (eq 36) */
+  /* SM cycles by phase when cfg.profile is set: 0 setup, 1 start vector, 2 step matvec+dots, 3 step
+   * all-reduce, 4 step coefficients, 5 step normalise, 6 expm powers, 7 expm Horner, 8 expm squarings,
+   * 9 control, 10 update; other entries 0. */
+  int64_t phase_cycles[16];
 } kiops_stats;
 
 /* One record per iteration (accepted or rejected) when a trace buffer is given. */

@@ -129,7 +129,7 @@ constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
 
 // Per-solve device layout (each region 256-byte aligned).
 struct Layout {
-  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, args, trace, total;
+  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, prof, args, trace, total;
 };
 
 Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, int r_max, int64_t trace_cap,
@@ -152,6 +152,7 @@ Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, 
   L.bar = take(256);
   L.stats = take(16 * 8);
   L.trace_len = take(8);
+  L.prof = take(16 * 8);
   L.args = take(sizeof(SolveArgs));
   L.trace = take((size_t)std::max<int64_t>(trace_cap, 0) * sizeof(TraceRec));
   L.total = off;
@@ -262,10 +263,12 @@ void bind(Prepared& P, char* base) {
   a.stats_d = (double*)(base + L.stats + 10 * 8);
   a.trace_len = (int64_t*)(base + L.trace_len);
   a.trace = a.trace_cap > 0 ? (TraceRec*)(base + L.trace) : nullptr;
+  a.prof = nullptr;
 }
 
 void fill_stats(kiops_stats* st, const int64_t* s, const double* sd, int engine, int blocks) {
   if (!st) return;
+  std::memset(st->phase_cycles, 0, sizeof(st->phase_cycles));
   st->substeps = s[0];
   st->rejected = s[1];
   st->matvecs = s[2];
@@ -305,13 +308,15 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   st = ensure_workspace(ctx, P.L.total);
   if (st) return st;
   bind(P, (char*)ctx->ws);
+  if (ctx->cfg.profile) P.args.prof = (long long*)(P.base + P.L.prof);
   const size_t tr_bytes = (size_t)(trace ? trace_cap : 0) * sizeof(TraceRec);
-  st = ensure_pinned(ctx, sizeof(SolveArgs) + 256 + tr_bytes);
+  st = ensure_pinned(ctx, sizeof(SolveArgs) + 512 + tr_bytes);
   if (st) return st;
   char* hp = (char*)ctx->host_pinned;
   std::memcpy(hp, &P.args, sizeof(SolveArgs));
   KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
   KCHECK(ctx, cudaMemsetAsync(P.base + P.L.trace_len, 0, 8, ctx->stream));
+  if (ctx->cfg.profile) KCHECK(ctx, cudaMemsetAsync(P.base + P.L.prof, 0, 16 * 8, ctx->stream));
   KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, hp, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
   const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
   void* kargs[] = {(void*)&dargs};
@@ -324,6 +329,9 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   KCHECK(ctx, cudaMemcpyAsync(hs, P.base + P.L.stats, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
   int64_t* htl = hs + 15;
   KCHECK(ctx, cudaMemcpyAsync(htl, P.base + P.L.trace_len, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  int64_t* hprof = hs + 16;
+  if (ctx->cfg.profile)
+    KCHECK(ctx, cudaMemcpyAsync(hprof, P.base + P.L.prof, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
   KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
   if (trace && trace_cap > 0) {
     int64_t n = std::min(*htl, trace_cap);
@@ -346,6 +354,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   }
   const double* hsd = (const double*)(hs + 10);
   fill_stats(stats, hs, hsd, engine, blocks);
+  if (stats && ctx->cfg.profile) std::memcpy(stats->phase_cycles, hprof, 16 * 8);
   const int dst = (int)hs[6];
   if (dst == ST_ETIMEOUT) return fail(ctx, KIOPS_ETIMEOUT, "a device-side wait exceeded %.3g s", ctx->cfg.timeout_s);
   if (dst == ST_ENOTCONV)
@@ -491,8 +500,8 @@ kiops_status kiops_op_csr(kiops_ctx* ctx, kiops_op** op, int64_t n, int64_t nnz,
 kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stencil2d_desc* d) {
   if (!ctx || !op || !d) return KIOPS_EINVAL;
   *op = nullptr;
-  if (d->nx < 1 || d->ny < 1 || (d->nspecies != 1 && d->nspecies != 2))
-    return fail(ctx, KIOPS_EINVAL, "invalid 2D stencil description");
+  if (d->nx < 1 || d->ny < 1 || (d->nspecies != 1 && d->nspecies != 2) || d->nx * d->ny * d->nspecies > INT32_MAX)
+    return fail(ctx, KIOPS_EINVAL, "invalid 2D stencil description (sizes, species, or more than 2^31-1 unknowns)");
   kiops_op* o = new (std::nothrow) kiops_op();
   if (!o) return KIOPS_ENOMEM;
   o->ctx = ctx;
@@ -515,7 +524,8 @@ kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
 kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stencil3d_desc* d) {
   if (!ctx || !op || !d) return KIOPS_EINVAL;
   *op = nullptr;
-  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(ctx, KIOPS_EINVAL, "invalid 3D stencil description");
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx * d->ny * d->nz > INT32_MAX)
+    return fail(ctx, KIOPS_EINVAL, "invalid 3D stencil description (sizes or more than 2^31-1 unknowns)");
   kiops_op* o = new (std::nothrow) kiops_op();
   if (!o) return KIOPS_ENOMEM;
   o->ctx = ctx;

@@ -32,6 +32,7 @@ constexpr int kMaxWin = kMaxM + 1;         // largest orthogonalisation window
 constexpr int kMaxRed = 2 * kMaxWin + 1;   // largest reduction width
 constexpr int kTile = 8;                   // dense matmul tile edge
 constexpr int kMaxDeg = 8;                 // entries of the Taylor degree table
+constexpr int kGramRing = 8;               // Gram rows kept in shared memory (m_o <= kGramRing)
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ENOTCONV = 3, ST_ETIMEOUT = 4, ST_ECUDA = 5 };
 enum : int { OP_CSR = 0, OP_ST2D = 1, OP_ST3D = 2 };
@@ -92,6 +93,7 @@ struct SolveArgs {
   TraceRec* trace;
   int64_t trace_cap;
   int64_t* trace_len;
+  long long* prof;           // non-NULL: cycles spent per phase, rank 0 view (16 counters)
   TaylorTable tt;
   int expm_only;             // 1: compute exp(a) of an n x n matrix only (kiops_expm)
   int expm_n;
@@ -144,8 +146,7 @@ struct GridTeam {
     __syncthreads();
     if (threadIdx.x == 0) {
       epoch += 1;
-      __threadfence();
-      red_release_add(ctr, 1u);
+      red_release_add(ctr, 1u);  // release: orders this block's writes (bar.sync above) before the arrival
       const unsigned int target = epoch * (unsigned int)size;
       const long long t0 = global_ns();
       int ok = 1;
@@ -160,8 +161,7 @@ struct GridTeam {
           }
         }
       }
-      __threadfence();
-      *s_flag = ok;
+      *s_flag = ok;  // the acquire load above orders the reads that follow the bar.sync below
     }
     __syncthreads();
     return *s_flag != 0;
@@ -180,7 +180,7 @@ struct CtaTeam {
 // Shared control state: identical in every block of a grid team.
 // ------------------------------------------------------------------------------------------------
 struct Ctl {
-  double t_now, tau, beta, nu, mu, s, rs, eps_last, nx2_pre;
+  double t_now, tau, beta, nu, mu, s, s2, rs, eps_last, nx2_pre;
   double kappa, qp1_est, prev_tau, prev_omega, prev_eps;
   int m, j, i0, nwin, breakdown, recompute, accepted, done, status, have_prev, prev_j, sync_ok;
   int64_t substeps, rejected, matvecs, iters, expm_calls;
@@ -191,57 +191,113 @@ struct Ctl {
   double colabs[kMaxM + 2];     // 1-based: sum_i |h(i,k)| over the window entries of column k
   double sub[kMaxM + 2];        // 1-based: h(k+1, k)
   double tail[kMaxP];           // tail of the vector being multiplied
+  double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
+  double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
   double hc[kMaxP + 1];         // Horner epilogue coefficients
   double red[kMaxRed];          // results of the last all-reduce
   double blk[kMaxRed];          // this block's partial sums
   double wred[kWarps][kRegK];
+  long long prof[16];           // cycles by phase (rank 0, thread 0) when profiling
+  long long prof_last;
 };
 
-// Reduce acc[0..K) over the block into blk[off..off+K).  Fixed shuffle tree + fixed warp order.
-__device__ __forceinline__ void block_reduce(Ctl& c, const double (&acc)[kRegK], int K, int off) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Phase profiling: thread 0 of rank 0 charges the cycles since the previous tick to a category.
+#define KIOPS_TICK(cat)                          \
+  do {                                           \
+    if (prof_on && threadIdx.x == 0) {           \
+      const long long t_ = clock64();            \
+      c.prof[(cat)] += t_ - c.prof_last;         \
+      c.prof_last = t_;                          \
+    }                                            \
+  } while (0)
+
+// Sum eight per-lane values over a warp with a transpose (butterfly) reduction: at the exchange with
+// lane ^ 16 each lane keeps half of the values and adds its partner's copy of that half, then halves
+// again at ^ 8 and ^ 4; two plain exchanges (^ 2, ^ 1) finish.  9 double adds per warp instead of the
+// 40 of eight separate shuffle trees (a warp-wide FP64 add is expensive on this GPU).  On return lane l
+// holds the sum of value index 4*b4 + 2*b3 + b2 (bits of l); the order of additions is fixed.
+__device__ __forceinline__ double warp_transpose_sum8(const double (&v)[kRegK]) {
+  const int lane = threadIdx.x & 31;
+  const bool h1 = lane & 16, h2 = lane & 8, h3 = lane & 4;
+  double a[4], b2[2];
 #pragma unroll
-  for (int k = 0; k < kRegK; ++k) {
-    if (k < K) {
-      double v = warp_sum(acc[k]);
-      if (lane == 0) c.wred[warp][k] = v;
-    }
+  for (int i = 0; i < 4; ++i) {
+    const double send = h1 ? v[i] : v[i + 4];
+    const double keep = h1 ? v[i + 4] : v[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double send = h2 ? a[i] : a[i + 2];
+    const double keep = h2 ? a[i + 2] : a[i];
+    b2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const double send = h3 ? b2[0] : b2[1];
+  const double keep = h3 ? b2[1] : b2[0];
+  double r = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+// Reduce acc[0..K) (K <= kRegK) over the first `nwarps` warps of the block into dst[0..K) (shared).
+// Fixed order: butterfly within each warp, then warps 0, 1, 2, ... in sequence.
+__device__ __forceinline__ void block_reduce_to(Ctl& c, const double (&acc)[kRegK], int K, double* dst,
+                                                int nwarps = kWarps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < nwarps) {
+    const double r = warp_transpose_sum8(acc);
+    if ((lane & 3) == 0) c.wred[warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = r;
   }
   __syncthreads();
   if (threadIdx.x < K) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += c.wred[w][threadIdx.x];
-    c.blk[off + threadIdx.x] = s;
+    double s = c.wred[0][threadIdx.x];
+    for (int w = 1; w < nwarps; ++w) s += c.wred[w][threadIdx.x];
+    dst[threadIdx.x] = s;
   }
   __syncthreads();
+}
+__device__ __forceinline__ void block_reduce(Ctl& c, const double (&acc)[kRegK], int K, int off) {
+  block_reduce_to(c, acc, K, c.blk + off);
 }
 
 // Finish an all-reduce of blk[0..K) into red[0..K).  Grid: publish, barrier, then every block sums the
 // published partials over ranks 0..size-1 in the same order.  Returns false if the team must stop.
 template <class Team>
-__device__ bool finish_reduce(Team& team, Ctl& c, double* partials, int& parity, int K);
+__device__ bool finish_reduce(Team& team, Ctl& c, double* partials, int& parity, int K, bool prof_on = false);
 
 template <>
-__device__ bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, int&, int K) {
+__device__ bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, int&, int K, bool) {
   for (int k = threadIdx.x; k < K; k += kThreads) c.red[k] = c.blk[k];
   __syncthreads();
   return true;
 }
 
 template <>
-__device__ bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K) {
+__device__ bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K,
+                                        bool prof_on) {
   double* buf = partials + (size_t)parity * team.size * kMaxRed;
   for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
   if (!team.sync(&c.sync_ok)) return false;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k < K; k += kWarps) {
-    double s = 0.0;
-    for (int r = lane; r < team.size; r += 32) s += buf[(size_t)r * kMaxRed + k];
-    s = warp_sum(s);
-    if (lane == 0) c.red[k] = s;
+  KIOPS_TICK(11);
+  // thread t loads rank t's partials (ranks t + kThreads, ... added on top), then the fixed block tree
+  // over only as many warps as hold ranks
+  const int nw = team.size >= kThreads ? kWarps : (team.size + 31) / 32;
+  for (int k0 = 0; k0 < K; k0 += kRegK) {
+    const int cnt = K - k0 < kRegK ? K - k0 : kRegK;
+    double acc[kRegK];
+    const int r = threadIdx.x;
+    const double* src = buf + (size_t)r * kMaxRed + k0;
+#pragma unroll
+    for (int k = 0; k < kRegK; ++k) acc[k] = (r < team.size && k < cnt) ? src[k] : 0.0;
+    for (int r2 = r + kThreads; r2 < team.size; r2 += kThreads) {
+      const double* src2 = buf + (size_t)r2 * kMaxRed + k0;
+#pragma unroll
+      for (int k = 0; k < kRegK; ++k)
+        if (k < cnt) acc[k] += src2[k];
+    }
+    block_reduce_to(c, acc, cnt, c.red + k0, nw);
   }
-  __syncthreads();
   parity ^= 1;
   return true;
 }
@@ -296,6 +352,71 @@ __device__ __forceinline__ T apply_row(const OpDesc& op, const T* x, int64_t r) 
     acc += T(c[5]) * st_val<T>(op, x, 0, ix, iy, iz - 1, op.nz);
     acc += T(c[6]) * st_val<T>(op, x, 0, ix, iy, iz + 1, op.nz);
     if (op.diag[0][0]) acc += T(__ldg(op.diag[0][0] + r)) * x[r];
+    return acc;
+  }
+}
+
+// Row r of A x with 32-bit index arithmetic (stencil grids hold fewer than 2^31 points).
+template <typename T, int KIND>
+__device__ __forceinline__ T apply_row_fast(const OpDesc& op, const T* __restrict__ x, uint32_t r) {
+  if (KIND == OP_CSR) {
+    return apply_row<T, KIND>(op, x, (int64_t)r);
+  } else if (KIND == OP_ST2D) {
+    const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, npts = nx * ny;
+    uint32_t sp = 0, pt = r;
+    if (op.nspecies == 2 && r >= npts) { sp = 1; pt = r - npts; }
+    const uint32_t iy = pt / nx, ix = pt - iy * nx;
+    const T* xs = x + (size_t)sp * npts;
+    T w, e, so, no;
+    if (op.periodic) {
+      w = xs[ix == 0 ? pt + nx - 1 : pt - 1];
+      e = xs[ix + 1 == nx ? pt + 1 - nx : pt + 1];
+      so = xs[iy == 0 ? pt + npts - nx : pt - nx];
+      no = xs[iy + 1 == ny ? pt + nx - npts : pt + nx];
+    } else {
+      w = ix > 0 ? xs[pt - 1] : T(0);
+      e = ix + 1 < nx ? xs[pt + 1] : T(0);
+      so = iy > 0 ? xs[pt - nx] : T(0);
+      no = iy + 1 < ny ? xs[pt + nx] : T(0);
+    }
+    const double* c = op.coef[sp];
+    T acc = T(c[0]) * xs[pt];
+    acc = fma(T(c[1]), w, acc);
+    acc = fma(T(c[2]), e, acc);
+    acc = fma(T(c[3]), so, acc);
+    acc = fma(T(c[4]), no, acc);
+    for (int q = 0; q < op.nspecies; ++q)
+      if (op.diag[sp][q]) acc = fma(T(__ldg(op.diag[sp][q] + pt)), x[(size_t)q * npts + pt], acc);
+    return acc;
+  } else {
+    const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, nz = (uint32_t)op.nz, nxy = nx * ny;
+    const uint32_t iz = r / nxy, rem = r - iz * nxy;
+    const uint32_t iy = rem / nx, ix = rem - iy * nx;
+    T xm, xp, ym, yp, zm, zp;
+    if (op.periodic) {
+      xm = x[ix == 0 ? r + nx - 1 : r - 1];
+      xp = x[ix + 1 == nx ? r + 1 - nx : r + 1];
+      ym = x[iy == 0 ? r + nxy - nx : r - nx];
+      yp = x[iy + 1 == ny ? r + nx - nxy : r + nx];
+      zm = x[iz == 0 ? r + (nz - 1) * nxy : r - nxy];
+      zp = x[iz + 1 == nz ? r - (nz - 1) * nxy : r + nxy];
+    } else {
+      xm = ix > 0 ? x[r - 1] : T(0);
+      xp = ix + 1 < nx ? x[r + 1] : T(0);
+      ym = iy > 0 ? x[r - nx] : T(0);
+      yp = iy + 1 < ny ? x[r + nx] : T(0);
+      zm = iz > 0 ? x[r - nxy] : T(0);
+      zp = iz + 1 < nz ? x[r + nxy] : T(0);
+    }
+    const double* c = op.coef[0];
+    T acc = T(c[0]) * x[r];
+    acc = fma(T(c[1]), xm, acc);
+    acc = fma(T(c[2]), xp, acc);
+    acc = fma(T(c[3]), ym, acc);
+    acc = fma(T(c[4]), yp, acc);
+    acc = fma(T(c[5]), zm, acc);
+    acc = fma(T(c[6]), zp, acc);
+    if (op.diag[0][0]) acc = fma(T(__ldg(op.diag[0][0] + r)), x[r], acc);
     return acc;
   }
 }
@@ -358,12 +479,21 @@ template <typename T, int KIND, bool GRID>
 __global__ void __launch_bounds__(kThreads) kiops_solve_kernel(const SolveArgs* __restrict__ all) {
   extern __shared__ double smem_dyn[];
   __shared__ Ctl c;
+  // The argument block is copied to shared memory: gpu-scope acquires at every barrier invalidate L1,
+  // and reading it from global memory would put chains of L2 round trips in every phase.
+  __shared__ __align__(16) SolveArgs sa;
+  {
+    const SolveArgs* src = GRID ? all : all + blockIdx.x;
+    const int words = (int)(sizeof(SolveArgs) / sizeof(int));
+    for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const int*)src)[i];
+    __syncthreads();
+  }
   if (GRID) {
-    GridTeam team{(int)blockIdx.x, (int)gridDim.x, all[0].bar, all[0].abort_flag, all[0].timeout_ns, 0u};
-    solve_body<T, KIND, GridTeam>(all[0], team, c, smem_dyn);
+    GridTeam team{(int)blockIdx.x, (int)gridDim.x, sa.bar, sa.abort_flag, sa.timeout_ns, 0u};
+    solve_body<T, KIND, GridTeam>(sa, team, c, smem_dyn);
   } else {
     CtaTeam team;
-    solve_body<T, KIND, CtaTeam>(all[blockIdx.x], team, c, smem_dyn);
+    solve_body<T, KIND, CtaTeam>(sa, team, c, smem_dyn);
   }
 }
 
@@ -371,6 +501,7 @@ __global__ void __launch_bounds__(kThreads) kiops_solve_kernel(const SolveArgs* 
 // With a.expm_only, exponentiates a.expm_in (n x n) into a.expm_out instead.
 template <class Team>
 __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, double* smem_dyn) {
+  const bool prof_on = a.prof != nullptr && team.rank == 0;
   const int n = a.expm_only ? a.expm_n : c.j + 1;
   const size_t ldm = (size_t)(a.m_max + 1) * (a.m_max + 1);
   double* sA = smem_dyn;
@@ -446,6 +577,7 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     mm_team(P + (size_t)(t - 2) * ldm, P, P + (size_t)(t - 1) * ldm, n, team.rank, team.size, c, none, sA, sB);
     if (!team.sync(&c.sync_ok)) return false;
   }
+  KIOPS_TICK(6);
   // Horner in X^r: T = B_{q-1}; T = T X^r + B_i, B_i = sum_{t<r} coef(i r + t) X^t, coef(k) = 1/k!
   auto coef = [&](int k) -> double {
     if (k > deg) return 0.0;
@@ -472,6 +604,7 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     if (!team.sync(&c.sync_ok)) return false;
     double* t = Tc; Tc = Tn; Tn = t;
   }
+  KIOPS_TICK(7);
   // squarings: all but the last in full
   const int ssq = c.s_sq;
   for (int k = 0; k + 1 < ssq || (a.expm_only && k < ssq); ++k) {
@@ -500,7 +633,9 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     }
     if (lane == 0) a.fvec[row < n ? row : a.m_max + 1] = s;
   }
-  return team.sync(&c.sync_ok);
+  const bool ok = team.sync(&c.sync_ok);
+  KIOPS_TICK(8);
+  return ok;
 }
 
 template <typename T, int KIND, class Team>
@@ -518,12 +653,15 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
   T* V = (T*)a.V;
   const size_t ldv = (size_t)a.ldv;
   const int ldh = a.m_max + 2;
+  const bool prof_on = a.prof != nullptr && lead;
 
   if (tid == 0) {
     c.status = ST_OK;
     c.done = 0;
     c.substeps = c.rejected = c.matvecs = c.iters = c.expm_calls = 0;
     c.eps_last = 0.0;
+    for (int k = 0; k < 16; ++k) c.prof[k] = 0;
+    c.prof_last = clock64();
   }
   __syncthreads();
 
@@ -572,6 +710,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     __syncthreads();
   }
 
+  KIOPS_TICK(0);
   while (c.t_now < a.T_end) {  // Algorithm 1 line 9
     if (c.iters >= a.max_iters || c.substeps >= a.max_substeps) {
       if (tid == 0) c.status = ST_ENOTCONV;
@@ -616,6 +755,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         if (lead && tid < p) V[N + tid] = (T)(c.tail[tid] * ib);
       }
       if (!team.sync(&c.sync_ok)) goto stop;
+      KIOPS_TICK(1);
     }
 
     // ---- Algorithm 2: IOP steps while j < m
@@ -627,12 +767,80 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       const int nwin = j - i0 + 1;
       const T* vj = V + (size_t)(j - 1) * ldv;
       T* x = V + (size_t)j * ldv;
-      if (tid < p) c.tail[tid] = (double)vj[N + tid];
+      if (tid < p) {
+        c.tail[tid] = (double)vj[N + tid];
+        c.ntail[tid] = c.nu * c.tail[tid];
+      }
       __syncthreads();
       // pass 0 computes x = A~ v_j, stores it raw, and reduces <v_i, x>, <x, x>, <v_j, v_i> for the
       // first kChunk window entries; later passes reread x for further window entries (m_o > kChunk).
       const int Ktot = 2 * nwin + 1;
-      for (int cb = 0; cb < nwin; cb += kChunk) {
+      if (nwin <= kChunk) {
+        // single pass: two rows per thread in flight, every load issued before the stores
+        double acc[kRegK];
+#pragma unroll
+        for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+        const T* __restrict__ vjr = vj;
+        T* __restrict__ xo = x;
+        const T* __restrict__ w0 = V + (size_t)(i0 - 1) * ldv;
+        const T* __restrict__ w1 = V + (size_t)(i0 + (nwin > 1 ? 1 : 0) - 1) * ldv;
+        const T* __restrict__ w2 = V + (size_t)(i0 + (nwin > 2 ? 2 : 0) - 1) * ldv;
+        for (int64_t rA = r0 + tid; rA < r1; rA += 2 * kThreads) {
+          const int64_t rB = rA + kThreads;
+          const bool hasB = rB < r1;
+          T xa = apply_row_fast<T, KIND>(a.op, vjr, (uint32_t)rA);
+          T xb = hasB ? apply_row_fast<T, KIND>(a.op, vjr, (uint32_t)rB) : T(0);
+          for (int t = 0; t < p; ++t) {  // B block: weights and column pointers come from shared memory
+            const double* bc = a.b[p - t];
+            const T wt = T(c.ntail[t]);
+            xa = fma(wt, T(__ldg(bc + rA)), xa);
+            if (hasB) xb = fma(wt, T(__ldg(bc + rB)), xb);
+          }
+          const double vja = (double)vjr[rA], vjb = hasB ? (double)vjr[rB] : 0.0;
+          const double wa0 = (double)w0[rA], wb0 = hasB ? (double)w0[rB] : 0.0;
+          const double wa1 = nwin > 1 ? (double)w1[rA] : 0.0, wb1 = (nwin > 1 && hasB) ? (double)w1[rB] : 0.0;
+          const double wa2 = nwin > 2 ? (double)w2[rA] : 0.0, wb2 = (nwin > 2 && hasB) ? (double)w2[rB] : 0.0;
+          xo[rA] = xa;
+          if (hasB) xo[rB] = xb;
+          const double xda = (double)xa, xdb = (double)xb;
+          acc[0] = fma(wa0, xda, fma(wb0, xdb, acc[0]));
+          acc[kChunk] = fma(vja, wa0, fma(vjb, wb0, acc[kChunk]));
+          if (nwin > 1) {
+            acc[1] = fma(wa1, xda, fma(wb1, xdb, acc[1]));
+            acc[kChunk + 1] = fma(vja, wa1, fma(vjb, wb1, acc[kChunk + 1]));
+          }
+          if (nwin > 2) {
+            acc[2] = fma(wa2, xda, fma(wb2, xdb, acc[2]));
+            acc[kChunk + 2] = fma(vja, wa2, fma(vjb, wb2, acc[kChunk + 2]));
+          }
+          acc[2 * kChunk] = fma(xda, xda, fma(xdb, xdb, acc[2 * kChunk]));
+        }
+        if (lead && tid < p) {  // tail rows N..N+p-1: the shift K of Theorem 1
+          const int64_t rr = N + tid;
+          const T xv = tid + 1 < p ? (T)c.tail[tid + 1] : T(0);
+          x[rr] = xv;
+          const double xd = (double)xv, vjd = (double)vj[rr];
+#pragma unroll
+          for (int u = 0; u < kChunk; ++u) {  // static indices keep acc[] in registers
+            if (u < nwin) {
+              const double vi = (double)V[(size_t)(i0 + u - 1) * ldv + rr];
+              acc[u] = fma(vi, xd, acc[u]);
+              acc[kChunk + u] = fma(vjd, vi, acc[kChunk + u]);
+            }
+          }
+          acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
+        }
+        block_reduce(c, acc, 2 * kChunk + 1, 0);
+        if (tid == 0) {
+          for (int u = 0; u < nwin; ++u) {
+            c.red[u] = c.blk[u];
+            c.red[nwin + 1 + u] = c.blk[kChunk + u];
+          }
+          c.red[nwin] = c.blk[2 * kChunk];
+        }
+        __syncthreads();
+      }
+      for (int cb = 0; cb < nwin && nwin > kChunk; cb += kChunk) {
         const int cnt = nwin - cb < kChunk ? nwin - cb : kChunk;
         double acc[kRegK];
 #pragma unroll
@@ -648,7 +856,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           if (cb == 0) {
             if (!tailrow) {
               T s = apply_row<T, KIND>(a.op, vj, rr);
-              for (int t = 0; t < p; ++t) s += T(c.nu * c.tail[t]) * T(__ldg(a.b[p - t] + rr));
+              for (int t = 0; t < p; ++t) s += T(c.ntail[t]) * T(__ldg(a.b[p - t] + rr));
               xv = s;
             } else {
               const int t = (int)(rr - N);
@@ -683,7 +891,9 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       }
       for (int k = tid; k < Ktot; k += kThreads) c.blk[k] = c.red[k];
       __syncthreads();
-      if (!finish_reduce<Team>(team, c, a.partials, parity, Ktot)) goto stop;
+      KIOPS_TICK(2);
+      if (!finish_reduce<Team>(team, c, a.partials, parity, Ktot, prof_on)) goto stop;
+      KIOPS_TICK(3);
       // ---- MGS coefficients from CGS dots and the Gram entries (Algorithm 2 lines 7-10):
       // h_i = <v_i, x> - sum_{k<i} h_k <v_i, v_k>;  ||x - sum h_i v_i||^2 expanded over the window
       if (tid == 0) {
@@ -691,6 +901,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         auto G = [&](int i, int k) -> double {  // <v_i, v_k>, i, k in the window, 1-based
           if (i < k) { int t = i; i = k; k = t; }
           if (i == j) return c.red[nwin + 1 + (k - i0)];
+          if (a.m_o <= kGramRing) return c.gram[i % kGramRing][i - k];
           return a.gram[(size_t)(i - 1) * a.m_o + (i - k)];
         };
         for (int u = 0; u < nwin; ++u) {
@@ -704,13 +915,32 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         for (int u = 0; u < nwin; ++u)
           for (int v = 0; v < nwin; ++v) s2 += c.hcoef[u] * c.hcoef[v] * G(i0 + u, i0 + v);
         c.recompute = !(s2 > 1e-6 * nx2);
-        c.s = c.recompute ? 0.0 : sqrt(s2);
+        c.s2 = s2;
         c.nx2_pre = nx2;  // ||A~ v_j||^2 for the breakdown test
         c.i0 = i0;
         c.nwin = nwin;
+        // common case finished here (one FP64 rsqrt gives both s and 1/s): no breakdown is possible
+        // when s^2 > 1e-6 ||x_pre||^2 > breakdown_tol^2 ||x_pre||^2
+        if (!c.recompute) {
+          const double rs = rsqrt(s2);
+          c.rs = rs;
+          c.s = s2 * rs;
+          c.sub[j] = c.s;
+          if (lead) a.H[(size_t)j * ldh + (j - 1)] = c.s;
+          double ca = 0.0;
+          for (int u = 0; u < nwin; ++u) ca += fabs(c.hcoef[u]);
+          c.colabs[j] = ca;
+          if (lead)
+            for (int u = 0; u < nwin; ++u) a.H[(size_t)(i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
+          c.matvecs += 1;
+          c.j = j;
+        }
         // record Gram row j: <v_j, v_{j-o}> for o = 0..nwin-1
-        if (lead)
+        if (a.m_o <= kGramRing) {
+          for (int u = 0; u < nwin; ++u) c.gram[j % kGramRing][j - (i0 + u)] = c.red[nwin + 1 + u];
+        } else if (lead) {
           for (int u = 0; u < nwin; ++u) a.gram[(size_t)(j - 1) * a.m_o + (j - (i0 + u))] = c.red[nwin + 1 + u];
+        }
       }
       __syncthreads();
       const double nx2_pre = c.nx2_pre;
@@ -731,7 +961,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         if (tid == 0) c.s = sqrt(c.red[0]);
         __syncthreads();
       }
-      if (tid == 0) {
+      if (tid == 0 && c.recompute) {
         c.matvecs += 1;
         double ca = 0.0;
         for (int u = 0; u < c.nwin; ++u) ca += fabs(c.hcoef[u]);
@@ -739,7 +969,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         if (lead)
           for (int u = 0; u < c.nwin; ++u) a.H[(size_t)(c.i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
         c.j = j;
-        if (c.s <= a.bd_tol * sqrt(nx2_pre)) {  // happy breakdown (Algorithm 2 lines 12-15)
+        if (c.s * c.s <= a.bd_tol * a.bd_tol * nx2_pre) {  // happy breakdown (Algorithm 2 lines 12-15)
           c.breakdown = 1;
           c.sub[j] = 0.0;
         } else {
@@ -749,15 +979,34 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         }
       }
       __syncthreads();
+      KIOPS_TICK(4);
       if (c.breakdown) break;
       // ---- v_{j+1} = (1/s) (x - sum_i h_i v_i) in MGS order (lines 9, 16-17)
-      for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
-        const int64_t rr = r >= r1 ? N + (r - r1) : r;
-        T xv = x[rr];
-        for (int u = 0; u < c.nwin; ++u) xv -= T(c.hcoef[u]) * V[(size_t)(c.i0 + u - 1) * ldv + rr];
-        x[rr] = xv * T(c.rs);
+      if (nwin <= kChunk) {
+        const T h0 = T(c.hcoef[0]), h1 = nwin > 1 ? T(c.hcoef[1]) : T(0), h2 = nwin > 2 ? T(c.hcoef[2]) : T(0);
+        const T rsT = T(c.rs);
+        T* __restrict__ xo = x;
+        const T* __restrict__ w0 = V + (size_t)(i0 - 1) * ldv;
+        const T* __restrict__ w1 = V + (size_t)(i0 + (nwin > 1 ? 1 : 0) - 1) * ldv;
+        const T* __restrict__ w2 = V + (size_t)(i0 + (nwin > 2 ? 2 : 0) - 1) * ldv;
+        for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
+          const int64_t rr = r >= r1 ? N + (r - r1) : r;
+          T xv = xo[rr];
+          xv = fma(-h0, w0[rr], xv);
+          if (nwin > 1) xv = fma(-h1, w1[rr], xv);
+          if (nwin > 2) xv = fma(-h2, w2[rr], xv);
+          xo[rr] = xv * rsT;
+        }
+      } else {
+        for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
+          const int64_t rr = r >= r1 ? N + (r - r1) : r;
+          T xv = x[rr];
+          for (int u = 0; u < c.nwin; ++u) xv -= T(c.hcoef[u]) * V[(size_t)(c.i0 + u - 1) * ldv + rr];
+          x[rr] = xv * T(c.rs);
+        }
       }
       if (!team.sync(&c.sync_ok)) goto stop;
+      KIOPS_TICK(5);
     }
 
     // ---- Algorithm 1 lines 17-18: F = exp(tau H~)
@@ -842,6 +1091,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       c.m = m_new;
     }
     __syncthreads();
+    KIOPS_TICK(9);
     if (c.done) break;
     if (c.accepted) {
       // ---- Algorithm 3 (Task II line): w = beta V(1:N, 1:j) F(1:j, 1)
@@ -856,6 +1106,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       }
       if (tid == 0) c.j = 0;
       __syncthreads();
+      KIOPS_TICK(10);
     }
   }
 stop:
@@ -866,6 +1117,8 @@ stop:
     a.stats[0] = c.substeps; a.stats[1] = c.rejected; a.stats[2] = c.matvecs; a.stats[3] = c.iters;
     a.stats[4] = c.expm_calls; a.stats[5] = c.m; a.stats[6] = st;
     a.stats_d[0] = c.eps_last;
+    if (a.prof)
+      for (int k = 0; k < 16; ++k) a.prof[k] = c.prof[k];
   }
 }
 
