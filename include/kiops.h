@@ -206,6 +206,29 @@ kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* r
  * computed by the same on-device scaling-and-squaring code the solver uses for exp(tau H~). */
 kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f);
 
+/* Size of the fixed device scratch used by kiops_solve_noalloc (bytes). */
+#define KIOPS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* kiops_solve without any memory allocation, for callers that cannot allocate: code that runs while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not allowed there), applications whose device
+ * memory is owned by their own pool or allocator and must not be fragmented by a library, and embedded or
+ * real-time hosts that forbid allocation after start-up.  (The paper has no counterpart: this is an
+ * interface property, not part of the method.)
+ *
+ * Same arguments and result as kiops_solve with prec = KIOPS_FP64; the solve runs on one thread block.
+ * Instead of the context's cudaMalloc'd workspace it uses one file-scope device array of
+ * KIOPS_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds until the process exits.
+ * The caller still passes b and w.  Requests whose workspace (Krylov basis of (m_max+1) x (N+p) FP64
+ * values, Hessenberg and exponential work matrices) does not fit are rejected with KIOPS_EINVAL and a
+ * message giving the bytes needed; with m_max = 128 roughly N + p <= 30000 fits.
+ * The first call on a device looks up the array's device address (set-up, once per device, with that
+ * device current); make that first call before any stream capture.  Every call shares the one array and
+ * it keeps the previous call's contents (the counters it needs are cleared on each call): calls whose
+ * GPU work overlaps — from several streams, threads or contexts on the same device — race and give
+ * undefined results.  The call waits for its stream before returning. */
+kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b,
+                                 double tol, int m_init, int m_o, double* w, kiops_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

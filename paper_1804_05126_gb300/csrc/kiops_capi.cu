@@ -724,3 +724,84 @@ kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free solve: the workspace is a file-scope device array.  In host code the array's name
+// is only a host-side stand-in, so its device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernel.
+// ------------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KIOPS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// The argument block travels by value (no staging buffer); one block runs the whole solve.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) kiops_solve_kernel_byval(const __grid_constant__ SolveArgs args) {
+  extern __shared__ double smem_dyn[];
+  __shared__ Ctl c;
+  __shared__ __align__(16) SolveArgs sa;
+  const int words = (int)(sizeof(SolveArgs) / sizeof(int));
+  for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const int*)&args)[i];
+  __syncthreads();
+  CtaTeam team;
+  solve_body<double, KIND, CtaTeam>(sa, team, c, smem_dyn);
+}
+
+void* noalloc_kernel(int kind) {
+  if (kind == OP_CSR) return (void*)kiops_solve_kernel_byval<OP_CSR>;
+  if (kind == OP_ST2D) return (void*)kiops_solve_kernel_byval<OP_ST2D>;
+  return (void*)kiops_solve_kernel_byval<OP_ST3D>;
+}
+
+}  // namespace
+
+extern "C" kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, double tau, int p,
+                                            const double* const* b, double tol, int m_init, int m_o, double* w,
+                                            kiops_stats* stats) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int dev = ctx->cfg.device;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(ctx, KIOPS_EINVAL, "device ordinal %d not supported", dev);
+  KCHECK(ctx, cudaSetDevice(dev));
+  if (!g_noalloc_addr[dev]) {  // set-up, once per device (make the first call before any stream capture)
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(ctx, KIOPS_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_addr[dev] = ptr;
+  }
+  if (tau == 0.0 && A && b && w && b[0]) {
+    if (w != b[0]) KCHECK(ctx, cudaMemcpyAsync(w, b[0], (size_t)A->d.n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (stats) stats->m_last = std::max(ctx->cfg.m_min, std::min(m_init, ctx->cfg.m_max));
+    return KIOPS_OK;
+  }
+  Prepared P;
+  kiops_status st = prepare(ctx, A, tau, p, b, tol, m_init, m_o, KIOPS_FP64, w, 1, 0, P);
+  if (st) return st;
+  if (P.L.total > (size_t)KIOPS_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, KIOPS_EINVAL,
+                "kiops_solve_noalloc: this solve needs %zu bytes of workspace but the fixed scratch holds %u "
+                "(N + p = %lld, m_max = %d); use kiops_solve or a smaller m_max",
+                P.L.total, (unsigned)KIOPS_NOALLOC_SCRATCH_BYTES, (long long)(A->d.n + p), ctx->cfg.m_max);
+  bind(P, (char*)g_noalloc_addr[dev]);
+  // the array keeps the previous call's contents: clear the barrier word, abort flag, stats, trace count
+  KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
+  void* fn = noalloc_kernel(A->d.kind);
+  KCHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
+  void* kargs[] = {(void*)&P.args};
+  KCHECK(ctx, cudaLaunchKernel(fn, 1, kThreads, kargs, kDynSmem, ctx->stream));
+  int64_t hs[16];
+  KCHECK(ctx, cudaMemcpyAsync(hs, P.base + P.L.stats, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  fill_stats(stats, hs, (const double*)(hs + 10), KIOPS_ENGINE_CTA, 1);
+  const int dst = (int)hs[6];
+  if (dst == ST_ENOTCONV)
+    return fail(ctx, KIOPS_ENOTCONV, "no convergence within max_substeps/max_iterations (%lld iterations)",
+                (long long)hs[3]);
+  if (dst != ST_OK) return fail(ctx, (kiops_status)dst, "device status %d", dst);
+  return KIOPS_OK;
+}

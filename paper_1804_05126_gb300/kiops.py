@@ -97,6 +97,8 @@ _SIGS = {
                           C.c_int, C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
     "kiops_solve_batch": ([C.c_void_p, C.c_int, C.POINTER(kiops_request), C.POINTER(kiops_stats)], C.c_int),
     "kiops_expm": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "kiops_solve_noalloc": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
+                             C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
 }
 
 
@@ -224,6 +226,14 @@ def kiops_solve_batch(ctx, reqs: list[kiops_request]) -> list[dict]:
     stats = (kiops_stats * max(n, 1))()
     _check(ctx, lib().kiops_solve_batch(ctx, n, arr, stats), "kiops_solve_batch")
     return [stats[i].as_dict() for i in range(n)]
+
+
+def kiops_solve_noalloc(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, w_ptr) -> dict:
+    """The allocation-free solve (FP64, one thread block, fixed device scratch); see include/kiops.h."""
+    st = kiops_stats()
+    _check(ctx, lib().kiops_solve_noalloc(ctx, op, tau, p, _ptr_array(b_ptrs), tol, m_init, m_o, w_ptr, C.byref(st)),
+           "kiops_solve_noalloc")
+    return st.as_dict()
 
 
 def kiops_expm(ctx, n, a_ptr, f_ptr) -> None:
