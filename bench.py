@@ -116,6 +116,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1804_05126_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic():
+    """DRAM bytes per launch of the solve kernel from the committed ncu capture (profiles/traffic.json),
+    or None when the kernel sources changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(WORKLOAD)
+    except Exception:
+        return None
+    if not rec or rec.get("csrc_sha256_16") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -245,13 +268,7 @@ def run_gpu(args):
     pk = peaks()
     fp64_peak_tflops = 1.25  # nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json
     achieved_tflops = model["fp64_flops_per_solve"] / mean_s / 1e12
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get(WORKLOAD)
-        except Exception:
-            traffic = None
+    traffic = dram_traffic()
     lat = sorted(times_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
