@@ -71,6 +71,8 @@ typedef struct {
   int engine;              /* kiops_engine (default AUTO) */
   int grid_blocks;         /* grid engine block count; 0 = as many as are co-resident */
   int profile;             /* 1: fill kiops_stats.phase_cycles (device cycle counters, rank-0 view) */
+  int fuse_stencil;        /* 1 (default): 2D stencils on the grid engine normalise v_{j+1} inside the next
+                              step's tiles (one grid barrier per Krylov step); 0: separate normalise pass */
 } kiops_config;
 
 typedef struct {

@@ -129,7 +129,7 @@ constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
 
 // Per-solve device layout (each region 256-byte aligned).
 struct Layout {
-  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, prof, args, trace, total;
+  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, prof, args, trace, raw, total;
 };
 
 Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, int r_max, int64_t trace_cap,
@@ -155,6 +155,7 @@ Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, 
   L.prof = take(16 * 8);
   L.args = take(sizeof(SolveArgs));
   L.trace = take((size_t)std::max<int64_t>(trace_cap, 0) * sizeof(TraceRec));
+  L.raw = take((size_t)2 * ldv * (fp32 ? 4 : 8));
   L.total = off;
   return L;
 }
@@ -197,6 +198,29 @@ int grid_size(kiops_ctx* ctx, void* fn) {
 kiops_status prepare_kernel(kiops_ctx* ctx, void* fn) {
   KCHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
   return KIOPS_OK;
+}
+
+// 2D tiling of an nx x ny grid over at most `blocks` tiles for the lagged-normalisation path: smallest
+// tile area whose halo'd tile (ns species, element size elem) fits the dynamic shared memory; ties go to
+// the wider tile (coalesced rows).  Returns false if no tiling fits.
+bool choose_tiles(int64_t nx, int64_t ny, int ns, int blocks, size_t elem, int& gx, int& gy, int& tw, int& th) {
+  int64_t best = -1;
+  for (int cx = 1; cx <= blocks && cx <= nx; ++cx) {
+    const int cy = (int)std::min<int64_t>(blocks / cx, ny);
+    if (cy < 1) continue;
+    const int w = (int)((nx + cx - 1) / cx), h = (int)((ny + cy - 1) / cy);
+    const size_t smem = (size_t)ns * (w + 2) * (h + 2) * elem;
+    if (smem > kDynSmem) continue;
+    const int64_t area = (int64_t)w * h;
+    if (best < 0 || area < best || (area == best && w > tw)) {
+      best = area;
+      tw = w;
+      th = h;
+      gx = (int)((nx + w - 1) / w);
+      gy = (int)((ny + h - 1) / h);
+    }
+  }
+  return best > 0;
 }
 
 struct Prepared {
@@ -244,6 +268,17 @@ kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const
   int64_t ldv = 0;
   P.L = layout(a.N, p, m_max, m_o_eff, prec == KIOPS_FP32_BASIS, grid_blocks, max_r(ctx->tt), trace_cap, &ldv);
   a.ldv = ldv;
+  a.fused = 0;
+  if (A->d.kind == OP_ST2D && m_o_eff <= kChunk && grid_blocks > 1 && ctx->cfg.fuse_stencil) {
+    int gx = 0, gy = 0, tw = 0, th = 0;
+    if (choose_tiles(A->d.nx, A->d.ny, A->d.nspecies, grid_blocks, prec == KIOPS_FP32_BASIS ? 4 : 8, gx, gy, tw, th)) {
+      a.fused = 1;
+      a.tile_gx = gx;
+      a.tile_gy = gy;
+      a.tile_w = tw;
+      a.tile_h = th;
+    }
+  }
   return KIOPS_OK;
 }
 
@@ -264,6 +299,7 @@ void bind(Prepared& P, char* base) {
   a.trace_len = (int64_t*)(base + L.trace_len);
   a.trace = a.trace_cap > 0 ? (TraceRec*)(base + L.trace) : nullptr;
   a.prof = nullptr;
+  a.raw = base + L.raw;
 }
 
 void fill_stats(kiops_stats* st, const int64_t* s, const double* sd, int engine, int blocks) {
@@ -388,6 +424,7 @@ kiops_status kiops_config_default(kiops_config* cfg) {
   cfg->timeout_s = 10.0;
   cfg->engine = KIOPS_ENGINE_AUTO;
   cfg->grid_blocks = 0;
+  cfg->fuse_stencil = 1;
   return KIOPS_OK;
 }
 

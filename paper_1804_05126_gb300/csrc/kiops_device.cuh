@@ -95,6 +95,10 @@ struct SolveArgs {
   int64_t* trace_len;
   long long* prof;           // non-NULL: cycles spent per phase, rank 0 view (16 counters)
   TaylorTable tt;
+  // 2D stencils: lagged normalisation on 2D tiles (one barrier per Krylov step), see fused_st2d_phase
+  int fused;                 // 1: use the tiled lagged path
+  int tile_gx, tile_gy, tile_w, tile_h;
+  void* raw;                 // two raw vectors x_{j+1} of ldv elements (ring, fused path only)
   int expm_only;             // 1: compute exp(a) of an n x n matrix only (kiops_expm)
   int expm_n;
   const double* expm_in;
@@ -191,6 +195,9 @@ struct Ctl {
   double colabs[kMaxM + 2];     // 1-based: sum_i |h(i,k)| over the window entries of column k
   double sub[kMaxM + 2];        // 1-based: h(k+1, k)
   double tail[kMaxP];           // tail of the vector being multiplied
+  double fin_h[kChunk];         // fused path: MGS coefficients and 1/s that finalise the pending raw vector
+  double fin_rs;
+  int fin_pending, fin_i0, fin_nwin;
   double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
   double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
   double hc[kMaxP + 1];         // Horner epilogue coefficients
@@ -250,10 +257,15 @@ __device__ __forceinline__ void block_reduce_to(Ctl& c, const double (&acc)[kReg
     if ((lane & 3) == 0) c.wred[warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = r;
   }
   __syncthreads();
-  if (threadIdx.x < K) {
-    double s = c.wred[0][threadIdx.x];
-    for (int w = 1; w < nwarps; ++w) s += c.wred[w][threadIdx.x];
-    dst[threadIdx.x] = s;
+  if (threadIdx.x < K) {  // pairwise tree over the warps (fixed shape for a given nwarps)
+    double v[kWarps];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) v[w] = w < nwarps ? c.wred[w][threadIdx.x] : 0.0;
+#pragma unroll
+    for (int st = 1; st < kWarps; st <<= 1)
+#pragma unroll
+      for (int w = 0; w + st < kWarps; w += 2 * st) v[w] += v[w + st];
+    dst[threadIdx.x] = v[0];
   }
   __syncthreads();
 }
@@ -435,28 +447,70 @@ struct MmEpi {
   size_t ldm;
 };
 
+// Structure of every matrix of the exponential phase: a band (lower bandwidth lo, upper bandwidth up)
+// plus a dense last column, and a last row that is zero except its diagonal entry.  tau H~ has lo = 1,
+// up = m_o - 1 (Algorithm 2 writes rows j-m_o+1..j+1 of column j) and e_1 in its last column; products
+// keep the form with bandwidths added.  Every matrix is written in full (zeros outside the structure), so
+// a product only needs the inner index range where both factors can be nonzero.
+struct Band {
+  int lo, up;
+};
+
+__device__ __forceinline__ Band band_product(Band a, Band b, int n) {
+  Band c{a.lo + b.lo, a.up + b.up};
+  if (c.lo > n - 1) c.lo = n - 1;
+  if (c.up > n - 1) c.up = n - 1;
+  return c;
+}
+
 // C = A B (+ epilogue) for n x n row-major matrices; tiles of kTile x kTile distributed over ranks.
-__device__ void mm_team(const double* A, const double* B, double* C, int n, int rank, int size, const Ctl& c,
-                        const MmEpi& epi, double* sA, double* sB) {
+// Tiles outside the band of C are written as zeros without arithmetic.
+__device__ void mm_team(const double* A, Band bA, const double* B, Band bB, double* C, int n, int rank, int size,
+                        const Ctl& c, const MmEpi& epi, double* sA, double* sB) {
+  const Band bC = band_product(bA, bB, n);
   const int nt = (n + kTile - 1) / kTile;
   const int out = threadIdx.x >> 2, part = threadIdx.x & 3;
   const int ti_l = out / kTile, tk_l = out % kTile;
   for (int tile = rank; tile < nt * nt; tile += size) {
     const int ti = tile / nt, tk = tile - ti * nt;
-    for (int e = threadIdx.x; e < kTile * n; e += kThreads) {
-      const int rr = e / n, l = e - rr * n;
-      const int row = ti * kTile + rr;
-      sA[rr * kMaxN + l] = row < n ? A[(size_t)row * n + l] : 0.0;
+    const int i0 = ti * kTile, i1 = min(n, i0 + kTile), k0 = tk * kTile, k1 = min(n, k0 + kTile);
+    const bool lastcol = k1 == n;
+    const bool inband = lastcol || (k0 - (i1 - 1) <= bC.up && i0 - (k1 - 1) <= bC.lo);
+    const int row = i0 + ti_l, col = k0 + tk_l;
+    if (!inband) {
+      if (part == 0 && row < n && col < n) C[(size_t)row * n + col] = 0.0;
+      continue;
+    }
+    // inner range: A(i, l) != 0 needs l in [i - lo, i + up] (or l = n-1, which only meets B's last row,
+    // zero outside the last column); B(l, k) != 0 needs l in [k - up, k + lo]
+    int l0 = 0, l1 = n - 1;
+    if (!lastcol) {
+      l0 = max(0, max(i0 - bA.lo, k0 - bB.up));
+      l1 = min(n - 1, min(i1 - 1 + bA.up, k1 - 1 + bB.lo));
+    }
+    const int nl = l1 - l0 + 1;
+    for (int e = threadIdx.x; e < kTile * nl; e += kThreads) {
+      const int rr = e / nl, l = l0 + (e - rr * nl);
+      const int ra = i0 + rr;
+      sA[rr * kMaxN + (l - l0)] = ra < n ? A[(size_t)ra * n + l] : 0.0;
       const int l2 = e / kTile, cc = e - l2 * kTile;
-      const int col = tk * kTile + cc;
-      sB[l2 * kTile + cc] = col < n ? B[(size_t)l2 * n + col] : 0.0;
+      const int cb = k0 + cc;
+      sB[l2 * kTile + cc] = cb < n ? B[(size_t)(l0 + l2) * n + cb] : 0.0;
     }
     __syncthreads();
-    double s = 0.0;
-    for (int l = part; l < n; l += 4) s = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s);
+    // four independent chains per thread (FP64 dependent latency is 64 cycles on this GPU)
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int l = part;
+    for (; l + 12 < nl; l += 16) {
+      s0 = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s0);
+      s1 = fma(sA[ti_l * kMaxN + l + 4], sB[(l + 4) * kTile + tk_l], s1);
+      s2 = fma(sA[ti_l * kMaxN + l + 8], sB[(l + 8) * kTile + tk_l], s2);
+      s3 = fma(sA[ti_l * kMaxN + l + 12], sB[(l + 12) * kTile + tk_l], s3);
+    }
+    for (; l < nl; l += 4) s0 = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s0);
+    double s = (s0 + s1) + (s2 + s3);
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
-    const int row = ti * kTile + ti_l, col = tk * kTile + tk_l;
     if (part == 0 && row < n && col < n) {
       double e = 0.0;
       if (epi.nterms > 0) {
@@ -466,6 +520,123 @@ __device__ void mm_team(const double* A, const double* B, double* C, int n, int 
       C[(size_t)row * n + col] = s + e;
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Lagged normalisation for 2D stencils (one barrier per Krylov step).
+//
+// Step j of Algorithm 2 needs v_j = (1/s)(x_j - sum_i h_i v_i) at this block's points and at their grid
+// neighbours.  Instead of a separate normalise pass followed by a grid barrier, each block finalises v_j on
+// its 2D tile plus a one-point halo into shared memory (halo points are recomputed by every neighbouring
+// block with the same arithmetic), writes the tile's v_j to the basis, and applies A~ from shared memory.
+// Raw vectors x_{j+1} go to a two-slot ring so that no block overwrites a value a neighbour still reads.
+// The arithmetic of every value is the same as in the unfused path.
+template <typename T>
+__device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, int i0, int nwin, bool lead,
+                                 T* V, size_t ldv, double* smem, double (&acc)[kRegK]) {
+  const OpDesc& op = a.op;
+  const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, npts = nx * ny;
+  const int ns = op.nspecies;
+  const int64_t N = a.N;
+  const int p = a.p;
+  const int tid = threadIdx.x;
+  T* raw = (T*)a.raw;
+  const bool pend = c.fin_pending != 0;
+  const T* src = pend ? raw + (size_t)((j - 1) & 1) * ldv : V + (size_t)(j - 1) * ldv;  // v_j before finalising
+  T* vj = V + (size_t)(j - 1) * ldv;
+  T* xo = raw + (size_t)(j & 1) * ldv;  // raw x_{j+1}
+  const int fnw = pend ? c.fin_nwin : 0;
+  const T fh0 = fnw > 0 ? T(c.fin_h[0]) : T(0), fh1 = fnw > 1 ? T(c.fin_h[1]) : T(0),
+          fh2 = fnw > 2 ? T(c.fin_h[2]) : T(0);
+  const T frs = pend ? T(c.fin_rs) : T(1);
+  const T* f0 = V + (size_t)((pend ? c.fin_i0 : 1) - 1) * ldv;
+  const T* f1 = V + (size_t)((pend ? c.fin_i0 : 1) + (fnw > 1 ? 1 : 0) - 1) * ldv;
+  const T* f2 = V + (size_t)((pend ? c.fin_i0 : 1) + (fnw > 2 ? 2 : 0) - 1) * ldv;
+  const T* w0 = V + (size_t)(i0 - 1) * ldv;  // dot window of step j (v_j itself comes from shared memory)
+  const T* w1 = V + (size_t)(i0 + (nwin > 1 ? 1 : 0) - 1) * ldv;
+  const T* w2 = V + (size_t)(i0 + (nwin > 2 ? 2 : 0) - 1) * ldv;
+  if (rank < a.tile_gx * a.tile_gy) {
+    const int bx = rank % a.tile_gx, by = rank / a.tile_gx;
+    const int x0 = bx * a.tile_w, y0 = by * a.tile_h;
+    const int tw = min(a.tile_w, (int)nx - x0), th = min(a.tile_h, (int)ny - y0);
+    if (tw > 0 && th > 0) {
+      const int hw = tw + 2, hh = th + 2, plane = hw * hh;
+      T* st = (T*)smem;
+      for (int e = tid; e < ns * plane; e += kThreads) {
+        const int sp = e / plane, rem = e - sp * plane, hy = rem / hw, hx = rem - hy * hw;
+        int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+        bool inside = true;
+        if (op.periodic) {
+          gx = gx < 0 ? gx + (int)nx : (gx >= (int)nx ? gx - (int)nx : gx);
+          gy = gy < 0 ? gy + (int)ny : (gy >= (int)ny ? gy - (int)ny : gy);
+        } else if (gx < 0 || gx >= (int)nx || gy < 0 || gy >= (int)ny) {
+          inside = false;
+        }
+        T v = T(0);
+        if (inside) {
+          const size_t r = (size_t)sp * npts + (size_t)gy * nx + gx;
+          v = src[r];
+          if (pend) {
+            v = fma(-fh0, f0[r], v);
+            if (fnw > 1) v = fma(-fh1, f1[r], v);
+            if (fnw > 2) v = fma(-fh2, f2[r], v);
+            v = v * frs;
+            if (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) vj[r] = v;
+          }
+        }
+        st[e] = v;
+      }
+      __syncthreads();
+      for (int e = tid; e < ns * tw * th; e += kThreads) {
+        const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
+        const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
+        const size_t r = (size_t)sp * npts + pt;
+        const int h = sp * plane + (ly + 1) * hw + (lx + 1);
+        const double* cf = op.coef[sp];
+        const T ctr = st[h];
+        T xv = T(cf[0]) * ctr;
+        xv = fma(T(cf[1]), st[h - 1], xv);
+        xv = fma(T(cf[2]), st[h + 1], xv);
+        xv = fma(T(cf[3]), st[h - hw], xv);
+        xv = fma(T(cf[4]), st[h + hw], xv);
+        for (int q = 0; q < ns; ++q)
+          if (op.diag[sp][q]) xv = fma(T(__ldg(op.diag[sp][q] + pt)), st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
+        for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), T(__ldg(a.b[p - t] + r)), xv);
+        xo[r] = xv;
+        const double xd = (double)xv, vjd = (double)ctr;
+        const double v0 = (i0 == j) ? vjd : (double)w0[r];
+        acc[0] = fma(v0, xd, acc[0]);
+        acc[kChunk] = fma(vjd, v0, acc[kChunk]);
+        if (nwin > 1) {
+          const double v1 = (i0 + 1 == j) ? vjd : (double)w1[r];
+          acc[1] = fma(v1, xd, acc[1]);
+          acc[kChunk + 1] = fma(vjd, v1, acc[kChunk + 1]);
+        }
+        if (nwin > 2) {
+          const double v2 = vjd;  // i0 + 2 == j
+          acc[2] = fma(v2, xd, acc[2]);
+          acc[kChunk + 2] = fma(vjd, v2, acc[kChunk + 2]);
+        }
+        acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
+      }
+    }
+  }
+  if (lead && tid < p) {  // tail rows: finalised tail of v_j (c.tail) and the shift K of Theorem 1
+    const int64_t rr = N + tid;
+    if (pend) vj[rr] = (T)c.tail[tid];
+    const T xv = tid + 1 < p ? (T)c.tail[tid + 1] : T(0);
+    xo[rr] = xv;
+    const double xd = (double)xv, vjd = c.tail[tid];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      if (u < nwin) {
+        const double vi = (i0 + u == j) ? vjd : (double)V[(size_t)(i0 + u - 1) * ldv + rr];
+        acc[u] = fma(vi, xd, acc[u]);
+        acc[kChunk + u] = fma(vjd, vi, acc[kChunk + u]);
+      }
+    }
+    acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
   }
 }
 
@@ -573,10 +744,18 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
   }
   if (!team.sync(&c.sync_ok)) return false;
   MmEpi none{0, nullptr, ldm};
+  const Band bX = a.expm_only ? Band{n - 1, n - 1} : Band{min(1, n - 1), min(a.m_o - 1, n - 1)};
+  Band bP = bX;  // band of X^t
   for (int t = 2; t <= r; ++t) {  // powers X^2..X^r
-    mm_team(P + (size_t)(t - 2) * ldm, P, P + (size_t)(t - 1) * ldm, n, team.rank, team.size, c, none, sA, sB);
+    mm_team(P + (size_t)(t - 2) * ldm, bP, P, bX, P + (size_t)(t - 1) * ldm, n, team.rank, team.size, c, none, sA, sB);
+    bP = band_product(bP, bX, n);
     if (!team.sync(&c.sync_ok)) return false;
   }
+  const Band bXr = bP;
+  // band of sum_{t<r} c_t X^t (the Horner chunks)
+  Band bT{0, 0};
+  for (int t = 1; t < r; ++t) bT = Band{min(n - 1, bX.lo * t), min(n - 1, bX.up * t)};
+  if (a.expm_only) bT = bX;
   KIOPS_TICK(6);
   // Horner in X^r: T = B_{q-1}; T = T X^r + B_i, B_i = sum_{t<r} coef(i r + t) X^t, coef(k) = 1/k!
   auto coef = [&](int k) -> double {
@@ -600,7 +779,8 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     if (threadIdx.x < r) c.hc[threadIdx.x] = coef(i * r + threadIdx.x);
     __syncthreads();
     MmEpi epi{r, P, ldm};
-    mm_team(Tc, P + (size_t)(r - 1) * ldm, Tn, n, team.rank, team.size, c, epi, sA, sB);
+    mm_team(Tc, bT, P + (size_t)(r - 1) * ldm, bXr, Tn, n, team.rank, team.size, c, epi, sA, sB);
+    bT = band_product(bT, bXr, n);
     if (!team.sync(&c.sync_ok)) return false;
     double* t = Tc; Tc = Tn; Tn = t;
   }
@@ -608,7 +788,8 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
   // squarings: all but the last in full
   const int ssq = c.s_sq;
   for (int k = 0; k + 1 < ssq || (a.expm_only && k < ssq); ++k) {
-    mm_team(Tc, Tc, Tn, n, team.rank, team.size, c, none, sA, sB);
+    mm_team(Tc, bT, Tc, bT, Tn, n, team.rank, team.size, c, none, sA, sB);
+    bT = band_product(bT, bT, n);
     if (!team.sync(&c.sync_ok)) return false;
     double* t = Tc; Tc = Tn; Tn = t;
   }
@@ -643,7 +824,6 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
   const int tid = threadIdx.x;
   const int64_t N = a.N;
   const int p = a.p;
-  const int64_t M = N + p;
   // contiguous row range of this rank
   const int64_t chunk = (N + team.size - 1) / team.size;
   const int64_t r0 = (int64_t)team.rank * chunk;
@@ -654,6 +834,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
   const size_t ldv = (size_t)a.ldv;
   const int ldh = a.m_max + 2;
   const bool prof_on = a.prof != nullptr && lead;
+  const bool fused = KIND == OP_ST2D && a.fused != 0;
 
   if (tid == 0) {
     c.status = ST_OK;
@@ -730,6 +911,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         c.have_prev = 0;
         c.kappa = 2.0;
         c.qp1_est = 0.0;
+        c.fin_pending = 0;
       }
       __syncthreads();
       double acc[kRegK];
@@ -768,14 +950,37 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       const T* vj = V + (size_t)(j - 1) * ldv;
       T* x = V + (size_t)j * ldv;
       if (tid < p) {
-        c.tail[tid] = (double)vj[N + tid];
+        if (fused && c.fin_pending) {  // finalise the pending tail with the arithmetic of the normalise pass
+          const size_t rr = (size_t)N + tid;
+          T xv = ((const T*)a.raw)[(size_t)((j - 1) & 1) * ldv + rr];
+          for (int u = 0; u < c.fin_nwin; ++u) xv = fma(-T(c.fin_h[u]), V[(size_t)(c.fin_i0 + u - 1) * ldv + rr], xv);
+          xv = xv * T(c.fin_rs);
+          c.tail[tid] = (double)xv;
+        } else {
+          c.tail[tid] = (double)vj[N + tid];
+        }
         c.ntail[tid] = c.nu * c.tail[tid];
       }
       __syncthreads();
       // pass 0 computes x = A~ v_j, stores it raw, and reduces <v_i, x>, <x, x>, <v_j, v_i> for the
       // first kChunk window entries; later passes reread x for further window entries (m_o > kChunk).
       const int Ktot = 2 * nwin + 1;
-      if (nwin <= kChunk) {
+      T* xraw = fused ? (T*)a.raw + (size_t)(j & 1) * ldv : x;  // where x_{j+1} lives before normalisation
+      if (fused) {
+        double acc[kRegK];
+#pragma unroll
+        for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+        fused_st2d_phase<T>(a, c, team.rank, j, i0, nwin, lead, V, ldv, smem_dyn, acc);
+        block_reduce(c, acc, 2 * kChunk + 1, 0);
+        if (tid == 0) {
+          for (int u = 0; u < nwin; ++u) {
+            c.red[u] = c.blk[u];
+            c.red[nwin + 1 + u] = c.blk[kChunk + u];
+          }
+          c.red[nwin] = c.blk[2 * kChunk];
+        }
+        __syncthreads();
+      } else if (nwin <= kChunk) {
         // single pass: two rows per thread in flight, every load issued before the stores
         double acc[kRegK];
 #pragma unroll
@@ -840,7 +1045,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         }
         __syncthreads();
       }
-      for (int cb = 0; cb < nwin && nwin > kChunk; cb += kChunk) {
+      for (int cb = 0; cb < nwin && nwin > kChunk && !fused; cb += kChunk) {
         const int cnt = nwin - cb < kChunk ? nwin - cb : kChunk;
         double acc[kRegK];
 #pragma unroll
@@ -904,16 +1109,29 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           if (a.m_o <= kGramRing) return c.gram[i % kGramRing][i - k];
           return a.gram[(size_t)(i - 1) * a.m_o + (i - k)];
         };
-        for (int u = 0; u < nwin; ++u) {
-          const int i = i0 + u;
-          double h = c.red[u];
-          for (int v = 0; v < u; ++v) h -= c.hcoef[v] * G(i, i0 + v);
-          c.hcoef[u] = h;
+        double s2;
+        if (nwin == 2 && a.m_o <= kGramRing) {
+          // straight-line form of the general expressions below (window {j-1, j})
+          const double d0 = c.red[0], d1 = c.red[1];
+          const double g10 = c.red[3], g11 = c.red[4], g00 = c.gram[(j - 1) % kGramRing][0];
+          const double h0 = d0;
+          const double h1 = fma(-h0, g10, d1);
+          c.hcoef[0] = h0;
+          c.hcoef[1] = h1;
+          const double q0 = fma(h0, g00, -2.0 * d0), q1 = fma(h1, g11, -2.0 * d1);
+          s2 = fma(h0, q0, fma(h1, q1, fma(2.0 * h0 * h1, g10, nx2)));
+        } else {
+          for (int u = 0; u < nwin; ++u) {
+            const int i = i0 + u;
+            double h = c.red[u];
+            for (int v = 0; v < u; ++v) h -= c.hcoef[v] * G(i, i0 + v);
+            c.hcoef[u] = h;
+          }
+          s2 = nx2;
+          for (int u = 0; u < nwin; ++u) s2 -= 2.0 * c.hcoef[u] * c.red[u];
+          for (int u = 0; u < nwin; ++u)
+            for (int v = 0; v < nwin; ++v) s2 += c.hcoef[u] * c.hcoef[v] * G(i0 + u, i0 + v);
         }
-        double s2 = nx2;
-        for (int u = 0; u < nwin; ++u) s2 -= 2.0 * c.hcoef[u] * c.red[u];
-        for (int u = 0; u < nwin; ++u)
-          for (int v = 0; v < nwin; ++v) s2 += c.hcoef[u] * c.hcoef[v] * G(i0 + u, i0 + v);
         c.recompute = !(s2 > 1e-6 * nx2);
         c.s2 = s2;
         c.nx2_pre = nx2;  // ||A~ v_j||^2 for the breakdown test
@@ -951,7 +1169,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
         for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
           const int64_t rr = r >= r1 ? N + (r - r1) : r;
-          T xv = x[rr];
+          T xv = xraw[rr];
           for (int u = 0; u < c.nwin; ++u) xv -= T(c.hcoef[u]) * V[(size_t)(c.i0 + u - 1) * ldv + rr];
           const double xd = (double)xv;
           acc[0] = fma(xd, xd, acc[0]);
@@ -981,6 +1199,18 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       __syncthreads();
       KIOPS_TICK(4);
       if (c.breakdown) break;
+      if (fused) {  // v_{j+1} is finalised by the next step's tiles (or stays pending)
+        if (tid == 0) {
+          for (int u = 0; u < c.nwin; ++u) c.fin_h[u] = c.hcoef[u];
+          c.fin_rs = c.rs;
+          c.fin_i0 = c.i0;
+          c.fin_nwin = c.nwin;
+          c.fin_pending = 1;
+        }
+        __syncthreads();
+        KIOPS_TICK(5);
+        continue;
+      }
       // ---- v_{j+1} = (1/s) (x - sum_i h_i v_i) in MGS order (lines 9, 16-17)
       if (nwin <= kChunk) {
         const T h0 = T(c.hcoef[0]), h1 = nwin > 1 ? T(c.hcoef[1]) : T(0), h2 = nwin > 2 ? T(c.hcoef[2]) : T(0);

@@ -33,7 +33,7 @@ class kiops_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("m_min", C.c_int), ("m_max", C.c_int),
                 ("normalize_B", C.c_int), ("breakdown_tol", C.c_double), ("max_substeps", C.c_int64),
                 ("max_iterations", C.c_int64), ("timeout_s", C.c_double), ("engine", C.c_int),
-                ("grid_blocks", C.c_int), ("profile", C.c_int)]
+                ("grid_blocks", C.c_int), ("profile", C.c_int), ("fuse_stencil", C.c_int)]
 
 
 class kiops_stats(C.Structure):
@@ -315,7 +315,8 @@ class Solver:
 
     def __init__(self, device: int = 0, stream=None, m_min: int = 10, m_max: int = 128, normalize_B: bool = True,
                  breakdown_tol: float = 1e-12, max_substeps: int = 10**6, max_iterations: int = 10**5,
-                 timeout_s: float = 10.0, engine: int = ENGINE_AUTO, grid_blocks: int = 0, profile: bool = False):
+                 timeout_s: float = 10.0, engine: int = ENGINE_AUTO, grid_blocks: int = 0, profile: bool = False,
+                 fuse_stencil: bool = True):
         import torch
         self.device = torch.device("cuda", device)
         cfg = kiops_config_default()
@@ -324,6 +325,7 @@ class Solver:
         cfg.m_min, cfg.m_max, cfg.normalize_B = m_min, m_max, int(normalize_B)
         cfg.breakdown_tol, cfg.max_substeps, cfg.max_iterations = breakdown_tol, max_substeps, max_iterations
         cfg.timeout_s, cfg.engine, cfg.grid_blocks, cfg.profile = timeout_s, engine, grid_blocks, int(profile)
+        cfg.fuse_stencil = int(fuse_stencil)
         self.cfg = cfg
         self.ctx = kiops_create(cfg)
 

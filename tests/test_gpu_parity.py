@@ -217,3 +217,17 @@ def test_not_converged_reports_enotconv():
         gpu_solve(s, P)
     assert e.value.status == 3
     s.close()
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+@pytest.mark.parametrize("make", [lambda: W.problem_adr2d(n=61, seed=21),
+                                  lambda: W.problem_gray_scott(n=37, seed=6, precision="fp64", tol=1e-8, tau=1.0)])
+def test_2d_stencil_fused_and_unfused_paths(make, fuse):
+    """The tiled lagged-normalisation path and the separate-normalise path both match the oracle."""
+    P = make()
+    s = kiops.Solver(device=0, fuse_stencil=fuse)
+    w, st, tr = gpu_solve(s, P, trace=True)
+    s.close()
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
