@@ -63,7 +63,8 @@ typedef struct {
   int device;              /* CUDA device ordinal (default 0) */
   void* stream;            /* cudaStream_t to issue work on; NULL = the legacy default stream */
   int m_min, m_max;        /* Krylov dimension bounds (Algorithm 1 defaults 10, 128); m_max <= KIOPS_MAX_M */
-  int normalize_B;         /* section 3.7 power-of-two scaling of B (default 1) */
+  int normalize_B;         /* section 3.7 power-of-two scaling of B (default 1); applied with an FP64
+                              basis only (with an FP32 basis it would make the tail dominate the basis) */
   double breakdown_tol;    /* happy breakdown when ||x|| <= breakdown_tol * ||A~ v_j|| (default 1e-12) */
   int64_t max_substeps;    /* accepted substeps before KIOPS_ENOTCONV (default 1e6) */
   int64_t max_iterations;  /* accepted + rejected iterations before KIOPS_ENOTCONV (default 1e5) */

@@ -129,11 +129,11 @@ constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
 
 // Per-solve device layout (each region 256-byte aligned).
 struct Layout {
-  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, prof, args, trace, raw, total;
+  size_t V, H, gram, mats, fvec, partials, bar, stats, trace_len, prof, args, trace, raw, bf, df, total;
 };
 
 Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, int r_max, int64_t trace_cap,
-              int64_t* ldv_out) {
+              int64_t* ldv_out, int64_t df_elems = 0) {
   Layout L{};
   const int64_t ldv = (int64_t)align_up((size_t)(N + p), 64);
   *ldv_out = ldv;
@@ -156,6 +156,8 @@ Layout layout(int64_t N, int p, int m_max, int m_o, bool fp32, int grid_blocks, 
   L.args = take(sizeof(SolveArgs));
   L.trace = take((size_t)std::max<int64_t>(trace_cap, 0) * sizeof(TraceRec));
   L.raw = take((size_t)2 * ldv * (fp32 ? 4 : 8));
+  L.bf = take(fp32 ? (size_t)std::max(p, 1) * ldv * 4 : 0);
+  L.df = take(fp32 ? (size_t)std::max<int64_t>(df_elems, 1) * 4 : 0);
   L.total = off;
   return L;
 }
@@ -266,7 +268,11 @@ kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const
   a.tt = ctx->tt;
   a.trace_cap = trace_cap;
   int64_t ldv = 0;
-  P.L = layout(a.N, p, m_max, m_o_eff, prec == KIOPS_FP32_BASIS, grid_blocks, max_r(ctx->tt), trace_cap, &ldv);
+  int64_t df_elems = 0;  // FP32 copies of the coupling fields: nspecies^2 fields of the grid's points
+  if (A->d.kind == OP_ST2D) df_elems = (int64_t)A->d.nspecies * A->d.nspecies * A->d.nx * A->d.ny;
+  if (A->d.kind == OP_ST3D) df_elems = A->d.nx * A->d.ny * A->d.nz;
+  P.L = layout(a.N, p, m_max, m_o_eff, prec == KIOPS_FP32_BASIS, grid_blocks, max_r(ctx->tt), trace_cap, &ldv,
+               df_elems);
   a.ldv = ldv;
   a.fused = 0;
   if (A->d.kind == OP_ST2D && m_o_eff <= kChunk && grid_blocks > 1 && ctx->cfg.fuse_stencil) {
@@ -300,6 +306,8 @@ void bind(Prepared& P, char* base) {
   a.trace = a.trace_cap > 0 ? (TraceRec*)(base + L.trace) : nullptr;
   a.prof = nullptr;
   a.raw = base + L.raw;
+  a.bf = (float*)(base + L.bf);
+  a.df = (float*)(base + L.df);
 }
 
 void fill_stats(kiops_stats* st, const int64_t* s, const double* sd, int engine, int blocks) {

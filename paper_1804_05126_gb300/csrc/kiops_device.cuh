@@ -99,6 +99,8 @@ struct SolveArgs {
   int fused;                 // 1: use the tiled lagged path
   int tile_gx, tile_gy, tile_w, tile_h;
   void* raw;                 // two raw vectors x_{j+1} of ldv elements (ring, fused path only)
+  float* bf;                 // FP32 basis: B columns as floats, column t = b_{p-t} at bf + t*ldv
+  float* df;                 // FP32 basis: pointwise coupling fields as floats, (s*ns + q)*npts (stencils)
   int expm_only;             // 1: compute exp(a) of an n x n matrix only (kiops_expm)
   int expm_n;
   const double* expm_in;
@@ -198,6 +200,7 @@ struct Ctl {
   double fin_h[kChunk];         // fused path: MGS coefficients and 1/s that finalise the pending raw vector
   double fin_rs;
   int fin_pending, fin_i0, fin_nwin;
+  float yhi[kMaxN], ylo[kMaxN];  // FP32 basis: update weights split into float hi + lo
   double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
   double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
   double hc[kMaxP + 1];         // Horner epilogue coefficients
@@ -368,9 +371,68 @@ __device__ __forceinline__ T apply_row(const OpDesc& op, const T* x, int64_t r) 
   }
 }
 
+// Per-thread accumulation of the step's dot products.  FP64 basis: fused multiply-adds in FP64.  FP32
+// basis: compensated float-float accumulation (TwoProduct with fmaf and TwoSum; Ogita, Rump & Oishi,
+// SIAM J. Sci. Comput. 26 (2005), algorithm Dot2), which returns the sum as if accumulated in about twice
+// the FP32 precision; the per-thread results are then reduced across threads and blocks in FP64.  On this
+// GPU an FP64 operation costs as much pipe time as ~60 FP32 operations.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double v[kRegK];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < kRegK; ++k) v[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int k, double a, double b) { v[k] = fma(a, b, v[k]); }
+  __device__ __forceinline__ void to_double(double (&out)[kRegK]) const {
+#pragma unroll
+    for (int k = 0; k < kRegK; ++k) out[k] = v[k];
+  }
+};
+template <>
+struct DotAcc<float> {
+  float hi[kRegK], lo[kRegK];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < kRegK; ++k) hi[k] = lo[k] = 0.0f;
+  }
+  __device__ __forceinline__ void add(int k, float a, float b) {
+    const float pr = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -pr);  // a*b = pr + pe exactly
+    const float t = __fadd_rn(hi[k], pr);
+    const float z = __fsub_rn(t, hi[k]);
+    const float se = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(pr, z));  // hi + pr = t + se exactly
+    hi[k] = t;
+    lo[k] = __fadd_rn(lo[k], __fadd_rn(se, pe));
+  }
+  __device__ __forceinline__ void to_double(double (&out)[kRegK]) const {
+#pragma unroll
+    for (int k = 0; k < kRegK; ++k) out[k] = (double)hi[k] + (double)lo[k];
+  }
+};
+
+// B column t (= b_{p-t}) and pointwise coupling entry in the basis precision.
+template <typename T>
+__device__ __forceinline__ T bcol(const SolveArgs& a, int t, size_t r) {
+  if constexpr (sizeof(T) == 4) return a.bf[(size_t)t * a.ldv + r];
+  else return __ldg(a.b[a.p - t] + r);
+}
+template <typename T>
+__device__ __forceinline__ T diag_val(const SolveArgs& a, int sp, int q, uint32_t pt) {
+  if constexpr (sizeof(T) == 4) {
+    const uint32_t npts = (uint32_t)(a.op.nx * a.op.ny * (a.op.kind == OP_ST3D ? a.op.nz : 1));
+    return a.df[(size_t)(sp * a.op.nspecies + q) * npts + pt];
+  } else {
+    return __ldg(a.op.diag[sp][q] + pt);
+  }
+}
+
 // Row r of A x with 32-bit index arithmetic (stencil grids hold fewer than 2^31 points).
 template <typename T, int KIND>
-__device__ __forceinline__ T apply_row_fast(const OpDesc& op, const T* __restrict__ x, uint32_t r) {
+__device__ __forceinline__ T apply_row_fast(const SolveArgs& a, const T* __restrict__ x, uint32_t r) {
+  const OpDesc& op = a.op;
   if (KIND == OP_CSR) {
     return apply_row<T, KIND>(op, x, (int64_t)r);
   } else if (KIND == OP_ST2D) {
@@ -398,7 +460,7 @@ __device__ __forceinline__ T apply_row_fast(const OpDesc& op, const T* __restric
     acc = fma(T(c[3]), so, acc);
     acc = fma(T(c[4]), no, acc);
     for (int q = 0; q < op.nspecies; ++q)
-      if (op.diag[sp][q]) acc = fma(T(__ldg(op.diag[sp][q] + pt)), x[(size_t)q * npts + pt], acc);
+      if (op.diag[sp][q]) acc = fma(diag_val<T>(a, sp, q, pt), x[(size_t)q * npts + pt], acc);
     return acc;
   } else {
     const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, nz = (uint32_t)op.nz, nxy = nx * ny;
@@ -428,7 +490,7 @@ __device__ __forceinline__ T apply_row_fast(const OpDesc& op, const T* __restric
     acc = fma(T(c[4]), yp, acc);
     acc = fma(T(c[5]), zm, acc);
     acc = fma(T(c[6]), zp, acc);
-    if (op.diag[0][0]) acc = fma(T(__ldg(op.diag[0][0] + r)), x[r], acc);
+    if (op.diag[0][0]) acc = fma(diag_val<T>(a, 0, 0, r), x[r], acc);
     return acc;
   }
 }
@@ -534,7 +596,7 @@ __device__ void mm_team(const double* A, Band bA, const double* B, Band bB, doub
 // The arithmetic of every value is the same as in the unfused path.
 template <typename T>
 __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, int i0, int nwin, bool lead,
-                                 T* V, size_t ldv, double* smem, double (&acc)[kRegK]) {
+                                 T* V, size_t ldv, double* smem, DotAcc<T>& acc, bool prof_on) {
   const OpDesc& op = a.op;
   const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, npts = nx * ny;
   const int ns = op.nspecies;
@@ -588,6 +650,7 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
         st[e] = v;
       }
       __syncthreads();
+      KIOPS_TICK(12);
       for (int e = tid; e < ns * tw * th; e += kThreads) {
         const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
         const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
@@ -601,24 +664,22 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
         xv = fma(T(cf[3]), st[h - hw], xv);
         xv = fma(T(cf[4]), st[h + hw], xv);
         for (int q = 0; q < ns; ++q)
-          if (op.diag[sp][q]) xv = fma(T(__ldg(op.diag[sp][q] + pt)), st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
-        for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), T(__ldg(a.b[p - t] + r)), xv);
+          if (op.diag[sp][q]) xv = fma(diag_val<T>(a, sp, q, pt), st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
+        for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), bcol<T>(a, t, r), xv);
         xo[r] = xv;
-        const double xd = (double)xv, vjd = (double)ctr;
-        const double v0 = (i0 == j) ? vjd : (double)w0[r];
-        acc[0] = fma(v0, xd, acc[0]);
-        acc[kChunk] = fma(vjd, v0, acc[kChunk]);
+        const T v0 = (i0 == j) ? ctr : w0[r];
+        acc.add(0, v0, xv);
+        acc.add(kChunk, ctr, v0);
         if (nwin > 1) {
-          const double v1 = (i0 + 1 == j) ? vjd : (double)w1[r];
-          acc[1] = fma(v1, xd, acc[1]);
-          acc[kChunk + 1] = fma(vjd, v1, acc[kChunk + 1]);
+          const T v1 = (i0 + 1 == j) ? ctr : w1[r];
+          acc.add(1, v1, xv);
+          acc.add(kChunk + 1, ctr, v1);
         }
-        if (nwin > 2) {
-          const double v2 = vjd;  // i0 + 2 == j
-          acc[2] = fma(v2, xd, acc[2]);
-          acc[kChunk + 2] = fma(vjd, v2, acc[kChunk + 2]);
+        if (nwin > 2) {  // i0 + 2 == j
+          acc.add(2, ctr, xv);
+          acc.add(kChunk + 2, ctr, ctr);
         }
-        acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
+        acc.add(2 * kChunk, xv, xv);
       }
     }
   }
@@ -627,16 +688,16 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
     if (pend) vj[rr] = (T)c.tail[tid];
     const T xv = tid + 1 < p ? (T)c.tail[tid + 1] : T(0);
     xo[rr] = xv;
-    const double xd = (double)xv, vjd = c.tail[tid];
+    const T vjt = (T)c.tail[tid];
 #pragma unroll
     for (int u = 0; u < kChunk; ++u) {
       if (u < nwin) {
-        const double vi = (i0 + u == j) ? vjd : (double)V[(size_t)(i0 + u - 1) * ldv + rr];
-        acc[u] = fma(vi, xd, acc[u]);
-        acc[kChunk + u] = fma(vjd, vi, acc[kChunk + u]);
+        const T vi = (i0 + u == j) ? vjt : V[(size_t)(i0 + u - 1) * ldv + rr];
+        acc.add(u, vi, xv);
+        acc.add(kChunk + u, vjt, vi);
       }
     }
-    acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
+    acc.add(2 * kChunk, xv, xv);
   }
 }
 
@@ -866,6 +927,21 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     }
     if (a.w != a.b[0])
       for (int64_t r = r0 + tid; r < r1; r += kThreads) a.w[r] = __ldg(a.b[0] + r);
+    if constexpr (sizeof(T) == 4) {  // FP32 basis: the matvec's B block and coupling fields in FP32
+      for (int t = 0; t < p; ++t)
+        for (int64_t r = r0 + tid; r < r1; r += kThreads) a.bf[(size_t)t * a.ldv + r] = (float)__ldg(a.b[p - t] + r);
+      if (KIND != OP_CSR) {
+        const int ns = KIND == OP_ST3D ? 1 : a.op.nspecies;
+        const int64_t npts = a.op.nx * a.op.ny * (KIND == OP_ST3D ? a.op.nz : 1);
+        const int64_t pchunk = (npts + team.size - 1) / team.size;
+        const int64_t q0 = (int64_t)team.rank * pchunk, q1 = q0 + pchunk < npts ? q0 + pchunk : npts;
+        for (int sp = 0; sp < ns; ++sp)
+          for (int q = 0; q < ns; ++q)
+            if (a.op.diag[sp][q])
+              for (int64_t pt = q0 + tid; pt < q1; pt += kThreads)
+                a.df[(size_t)(sp * ns + q) * npts + pt] = (float)__ldg(a.op.diag[sp][q] + pt);
+      }
+    }
     if (p > 0) {
       if (!finish_reduce<Team>(team, c, a.partials, parity, p)) goto stop;
     } else {
@@ -876,7 +952,9 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       for (int k = 0; k < p; ++k) nb = c.red[k] > nb ? c.red[k] : nb;
       c.nu = 1.0;
       c.mu = 1.0;
-      if (p >= 1 && a.normalize && nb > 0.0) {
+      // section 3.7 scaling, FP64 basis only: with an FP32 basis the tail entries (~||B||_1) would dwarf
+      // the state entries (~||b_0||_2) in every basis vector and cost about three digits of the result
+      if (p >= 1 && a.normalize && nb > 0.0 && sizeof(T) == 8) {
         const int e = ceil_log2(nb);
         c.nu = ldexp(1.0, -e);
         c.mu = ldexp(1.0, e);
@@ -967,10 +1045,13 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       const int Ktot = 2 * nwin + 1;
       T* xraw = fused ? (T*)a.raw + (size_t)(j & 1) * ldv : x;  // where x_{j+1} lives before normalisation
       if (fused) {
+        DotAcc<T> dacc;
+        dacc.zero();
+        fused_st2d_phase<T>(a, c, team.rank, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+        __syncthreads();
+        KIOPS_TICK(13);
         double acc[kRegK];
-#pragma unroll
-        for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
-        fused_st2d_phase<T>(a, c, team.rank, j, i0, nwin, lead, V, ldv, smem_dyn, acc);
+        dacc.to_double(acc);
         block_reduce(c, acc, 2 * kChunk + 1, 0);
         if (tid == 0) {
           for (int u = 0; u < nwin; ++u) {
@@ -982,9 +1063,8 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         __syncthreads();
       } else if (nwin <= kChunk) {
         // single pass: two rows per thread in flight, every load issued before the stores
-        double acc[kRegK];
-#pragma unroll
-        for (int k = 0; k < kRegK; ++k) acc[k] = 0.0;
+        DotAcc<T> dacc;
+        dacc.zero();
         const T* __restrict__ vjr = vj;
         T* __restrict__ xo = x;
         const T* __restrict__ w0 = V + (size_t)(i0 - 1) * ldv;
@@ -993,48 +1073,55 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         for (int64_t rA = r0 + tid; rA < r1; rA += 2 * kThreads) {
           const int64_t rB = rA + kThreads;
           const bool hasB = rB < r1;
-          T xa = apply_row_fast<T, KIND>(a.op, vjr, (uint32_t)rA);
-          T xb = hasB ? apply_row_fast<T, KIND>(a.op, vjr, (uint32_t)rB) : T(0);
-          for (int t = 0; t < p; ++t) {  // B block: weights and column pointers come from shared memory
-            const double* bc = a.b[p - t];
+          T xa = apply_row_fast<T, KIND>(a, vjr, (uint32_t)rA);
+          T xb = hasB ? apply_row_fast<T, KIND>(a, vjr, (uint32_t)rB) : T(0);
+          for (int t = 0; t < p; ++t) {  // B block: weights from shared memory
             const T wt = T(c.ntail[t]);
-            xa = fma(wt, T(__ldg(bc + rA)), xa);
-            if (hasB) xb = fma(wt, T(__ldg(bc + rB)), xb);
+            xa = fma(wt, bcol<T>(a, t, (size_t)rA), xa);
+            if (hasB) xb = fma(wt, bcol<T>(a, t, (size_t)rB), xb);
           }
-          const double vja = (double)vjr[rA], vjb = hasB ? (double)vjr[rB] : 0.0;
-          const double wa0 = (double)w0[rA], wb0 = hasB ? (double)w0[rB] : 0.0;
-          const double wa1 = nwin > 1 ? (double)w1[rA] : 0.0, wb1 = (nwin > 1 && hasB) ? (double)w1[rB] : 0.0;
-          const double wa2 = nwin > 2 ? (double)w2[rA] : 0.0, wb2 = (nwin > 2 && hasB) ? (double)w2[rB] : 0.0;
+          const T vja = vjr[rA], vjb = hasB ? vjr[rB] : T(0);
+          const T wa0 = w0[rA], wb0 = hasB ? w0[rB] : T(0);
+          const T wa1 = nwin > 1 ? w1[rA] : T(0), wb1 = (nwin > 1 && hasB) ? w1[rB] : T(0);
+          const T wa2 = nwin > 2 ? w2[rA] : T(0), wb2 = (nwin > 2 && hasB) ? w2[rB] : T(0);
           xo[rA] = xa;
           if (hasB) xo[rB] = xb;
-          const double xda = (double)xa, xdb = (double)xb;
-          acc[0] = fma(wa0, xda, fma(wb0, xdb, acc[0]));
-          acc[kChunk] = fma(vja, wa0, fma(vjb, wb0, acc[kChunk]));
+          dacc.add(0, wb0, xb);
+          dacc.add(0, wa0, xa);
+          dacc.add(kChunk, vjb, wb0);
+          dacc.add(kChunk, vja, wa0);
           if (nwin > 1) {
-            acc[1] = fma(wa1, xda, fma(wb1, xdb, acc[1]));
-            acc[kChunk + 1] = fma(vja, wa1, fma(vjb, wb1, acc[kChunk + 1]));
+            dacc.add(1, wb1, xb);
+            dacc.add(1, wa1, xa);
+            dacc.add(kChunk + 1, vjb, wb1);
+            dacc.add(kChunk + 1, vja, wa1);
           }
           if (nwin > 2) {
-            acc[2] = fma(wa2, xda, fma(wb2, xdb, acc[2]));
-            acc[kChunk + 2] = fma(vja, wa2, fma(vjb, wb2, acc[kChunk + 2]));
+            dacc.add(2, wb2, xb);
+            dacc.add(2, wa2, xa);
+            dacc.add(kChunk + 2, vjb, wb2);
+            dacc.add(kChunk + 2, vja, wa2);
           }
-          acc[2 * kChunk] = fma(xda, xda, fma(xdb, xdb, acc[2 * kChunk]));
+          dacc.add(2 * kChunk, xb, xb);
+          dacc.add(2 * kChunk, xa, xa);
         }
         if (lead && tid < p) {  // tail rows N..N+p-1: the shift K of Theorem 1
           const int64_t rr = N + tid;
           const T xv = tid + 1 < p ? (T)c.tail[tid + 1] : T(0);
           x[rr] = xv;
-          const double xd = (double)xv, vjd = (double)vj[rr];
+          const T vjt = vj[rr];
 #pragma unroll
-          for (int u = 0; u < kChunk; ++u) {  // static indices keep acc[] in registers
+          for (int u = 0; u < kChunk; ++u) {  // static indices keep the accumulators in registers
             if (u < nwin) {
-              const double vi = (double)V[(size_t)(i0 + u - 1) * ldv + rr];
-              acc[u] = fma(vi, xd, acc[u]);
-              acc[kChunk + u] = fma(vjd, vi, acc[kChunk + u]);
+              const T vi = V[(size_t)(i0 + u - 1) * ldv + rr];
+              dacc.add(u, vi, xv);
+              dacc.add(kChunk + u, vjt, vi);
             }
           }
-          acc[2 * kChunk] = fma(xd, xd, acc[2 * kChunk]);
+          dacc.add(2 * kChunk, xv, xv);
         }
+        double acc[kRegK];
+        dacc.to_double(acc);
         block_reduce(c, acc, 2 * kChunk + 1, 0);
         if (tid == 0) {
           for (int u = 0; u < nwin; ++u) {
@@ -1329,10 +1416,31 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       for (int k = tid; k < j; k += kThreads) c.hcoef[k] = a.fvec[k];
       __syncthreads();
       const double beta = c.hc[0];
-      for (int64_t r = r0 + tid; r < r1; r += kThreads) {
-        double s = 0.0;
-        for (int k = 0; k < j; ++k) s = fma((double)V[(size_t)k * ldv + r], c.hcoef[k], s);
-        a.w[r] = beta * s;
+      if constexpr (sizeof(T) == 4) {
+        // y = yhi + ylo in floats; v*yhi exactly (TwoProduct), v*ylo plainly, TwoSum accumulation
+        for (int k = tid; k < j; k += kThreads) {
+          const float hi = (float)c.hcoef[k];
+          c.yhi[k] = hi;
+          c.ylo[k] = (float)(c.hcoef[k] - (double)hi);
+        }
+        __syncthreads();
+        for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+          DotAcc<float> s2;
+          s2.hi[0] = 0.0f;
+          s2.lo[0] = 0.0f;
+          for (int k = 0; k < j; ++k) {
+            const float v = (float)V[(size_t)k * ldv + r];
+            s2.add(0, v, c.yhi[k]);
+            s2.lo[0] = __fmaf_rn(v, c.ylo[k], s2.lo[0]);
+          }
+          a.w[r] = beta * ((double)s2.hi[0] + (double)s2.lo[0]);
+        }
+      } else {
+        for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+          double s = 0.0;
+          for (int k = 0; k < j; ++k) s = fma((double)V[(size_t)k * ldv + r], c.hcoef[k], s);
+          a.w[r] = beta * s;
+        }
       }
       if (tid == 0) c.j = 0;
       __syncthreads();

@@ -231,3 +231,15 @@ def test_2d_stencil_fused_and_unfused_paths(make, fuse):
     w_ref, st_ref, tr_ref = oracle_solve(P)
     assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
     assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+
+
+def test_gray_scott_full_size_fp32_basis_vs_fp64_oracle(solver):
+    """Mixed precision at the full 1024 x 1024 size: FP32 basis and matvec, FP64 (compensated) dots,
+    FP64 exponential and control, against the plain FP64 oracle (tol = 1e-6, bar 10 tol)."""
+    P = W.problem_gray_scott()  # N = 2 * 1024^2, p = 3, tau = 1, tol = 1e-6, FP32 basis
+    w, st = gpu_solve(solver, P)
+    w_ref, st_ref, _ = oracle_solve(P)
+    err = rel(w, w_ref)
+    print(f"gray-scott 1024^2 fp32 basis: rel err vs FP64 oracle {err:.3e}, matvecs {st['matvecs']} "
+          f"(oracle {st_ref['matvecs']})")
+    assert st["status"] == 0 and err <= 10 * P.tol
