@@ -74,6 +74,7 @@ typedef struct {
   int profile;             /* 1: fill kiops_stats.phase_cycles (device cycle counters, rank-0 view) */
   int fuse_stencil;        /* 1 (default): 2D stencils on the grid engine normalise v_{j+1} inside the next
                               step's tiles (one grid barrier per Krylov step); 0: separate normalise pass */
+  int batch_team_blocks;   /* kiops_solve_batch: blocks per team (0 = automatic, 1 = one block per request) */
 } kiops_config;
 
 typedef struct {
@@ -201,9 +202,17 @@ kiops_status kiops_solve_host(kiops_ctx* ctx, const kiops_op* A, double tau, int
                               double tol, int m_init, int m_o, kiops_precision prec, double* w_host,
                               kiops_stats* stats);
 
-/* Independent solves in one launch, one thread block per request (single-CTA engine). stats: host array
- * of `count` entries or NULL.  Every request's operator must belong to ctx. */
+/* Independent solves in one cooperative launch per (precision, operator kind) group.  The launch is split
+ * into teams of cfg.batch_team_blocks blocks (0 = automatic); each team runs a list of requests one after
+ * another with its own barrier, partial sums and workspace.  The lists are planned on the host: requests
+ * sorted by an estimated work (N times a step count from a Gershgorin bound of ||tau A||) and each given to
+ * the least-loaded team.  With 1 block per team every request runs on its own block.  Results do not
+ * depend on the team a request lands on only up to the team size (reduction order follows the block count).
+ * stats: host array of `count` entries or NULL.  Every request's operator must belong to ctx. */
 kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats);
+
+/* Set cfg.batch_team_blocks of a live context (used by the batch autotuner). */
+kiops_status kiops_set_batch_team_blocks(kiops_ctx* ctx, int team_blocks);
 
 /* Dense exponential F = exp(A) of an n x n row-major FP64 matrix (device pointers), n <= KIOPS_MAX_M + 1,
  * computed by the same on-device scaling-and-squaring code the solver uses for exp(tau H~). */

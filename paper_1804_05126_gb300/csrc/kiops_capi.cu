@@ -125,6 +125,17 @@ void* pick_kernel(bool fp32, int kind, bool grid) {
   return kernel_ptr<float, OP_ST3D, false>();
 }
 
+void* pick_team_kernel(bool fp32, int kind) {
+  if (!fp32) {
+    if (kind == OP_CSR) return (void*)kiops_team_kernel<double, OP_CSR>;
+    if (kind == OP_ST2D) return (void*)kiops_team_kernel<double, OP_ST2D>;
+    return (void*)kiops_team_kernel<double, OP_ST3D>;
+  }
+  if (kind == OP_CSR) return (void*)kiops_team_kernel<float, OP_CSR>;
+  if (kind == OP_ST2D) return (void*)kiops_team_kernel<float, OP_ST2D>;
+  return (void*)kiops_team_kernel<float, OP_ST3D>;
+}
+
 constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
 
 // Per-solve device layout (each region 256-byte aligned).
@@ -433,6 +444,7 @@ kiops_status kiops_config_default(kiops_config* cfg) {
   cfg->engine = KIOPS_ENGINE_AUTO;
   cfg->grid_blocks = 0;
   cfg->fuse_stencil = 1;
+  cfg->batch_team_blocks = 0;
   return KIOPS_OK;
 }
 
@@ -649,7 +661,163 @@ kiops_status kiops_solve_host(kiops_ctx* ctx, const kiops_op* A, double tau, int
   return KIOPS_OK;
 }
 
-kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
+// Work estimate of one request for the batch plan: N times a step count from a Gershgorin bound of
+// ||tau A|| (Krylov dimensions grow like its square root; beyond m_max the solve substeps).
+static double estimate_work(const kiops_ctx* ctx, const kiops_request& r) {
+  const OpDesc& d = r.A->d;
+  double nrm = 0.0;
+  if (d.kind == OP_ST2D || d.kind == OP_ST3D) {
+    const int nc = d.kind == OP_ST3D ? 7 : 5;
+    for (int sp = 0; sp < (d.kind == OP_ST3D ? 1 : d.nspecies); ++sp) {
+      double rs = 0.0;
+      for (int k = 0; k < nc; ++k) rs += std::fabs(d.coef[sp][k]);
+      nrm = std::max(nrm, rs);
+    }
+  }
+  const double nu = r.tau * nrm;
+  double steps = d.kind == OP_CSR ? 30.0 : std::min((double)ctx->cfg.m_max, 10.0 + 2.0 * std::sqrt(nu));
+  steps *= std::max(1.0, nu / 400.0);
+  return (double)d.n * steps * (r.prec == KIOPS_FP32_BASIS ? 0.5 : 1.0);
+}
+
+// Team engine: requests grouped by (precision, operator kind); per group one cooperative launch of
+// floor(G / K) teams of K blocks; requests sorted by estimated work and each given to the least-loaded
+// team.  K = cfg.batch_team_blocks, or 0 = automatic (the heaviest request's share of the total work,
+// rounded down to a power of two).
+static kiops_status batch_teams(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
+  std::vector<int> order;
+  for (int i = 0; i < count; ++i)
+    if (reqs[i].tau > 0.0) order.push_back(i);
+  for (int i = 0; i < count; ++i)
+    if (reqs[i].tau == 0.0) {
+      KCHECK(ctx, cudaMemcpyAsync(reqs[i].w, reqs[i].b[0], (size_t)reqs[i].A->d.n * 8, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+      if (stats) {
+        std::memset(&stats[i], 0, sizeof(kiops_stats));
+        stats[i].engine = KIOPS_ENGINE_CTA;
+      }
+    }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return reqs[x].prec * 4 + reqs[x].A->d.kind < reqs[y].prec * 4 + reqs[y].A->d.kind;
+  });
+  kiops_status worst = KIOPS_OK;
+  size_t g0 = 0;
+  while (g0 < order.size()) {
+    size_t g1 = g0;
+    const int key = reqs[order[g0]].prec * 4 + reqs[order[g0]].A->d.kind;
+    while (g1 < order.size() && reqs[order[g1]].prec * 4 + reqs[order[g1]].A->d.kind == key) ++g1;
+    const bool fp32 = reqs[order[g0]].prec == KIOPS_FP32_BASIS;
+    void* fn = pick_team_kernel(fp32, reqs[order[g0]].A->d.kind);
+    kiops_status st = prepare_kernel(ctx, fn);
+    if (st) return st;
+    const int G = grid_size(ctx, fn);
+    if (G < 1) return fail(ctx, KIOPS_ECUDA, "team kernel does not fit on the device");
+    const int n = (int)(g1 - g0);
+    std::vector<double> work((size_t)n);
+    double total = 0.0, heaviest = 0.0;
+    for (int k = 0; k < n; ++k) {
+      work[k] = estimate_work(ctx, reqs[order[g0 + k]]);
+      total += work[k];
+      heaviest = std::max(heaviest, work[k]);
+    }
+    int K = ctx->cfg.batch_team_blocks;
+    if (K <= 0) {
+      K = 1;
+      while (2 * K <= G && (double)(2 * K) <= (double)G * heaviest / std::max(total, 1e-300)) K *= 2;
+    }
+    K = std::max(1, std::min(K, G));
+    const int T = std::max(1, G / K);
+    // LPT plan
+    std::vector<int> byw((size_t)n);
+    for (int k = 0; k < n; ++k) byw[k] = k;
+    std::stable_sort(byw.begin(), byw.end(), [&](int x, int y) { return work[x] > work[y]; });
+    std::vector<double> load((size_t)T, 0.0);
+    std::vector<std::vector<int>> lists((size_t)T);
+    for (int k : byw) {
+      int best = 0;
+      for (int t = 1; t < T; ++t)
+        if (load[t] < load[best]) best = t;
+      load[best] += work[k];
+      lists[best].push_back(k);
+    }
+    // per-request argument blocks, per-team workspace sized for the team's own requests
+    std::vector<Prepared> prep((size_t)n);
+    std::vector<size_t> team_bytes((size_t)T, 0);
+    for (int t = 0; t < T; ++t)
+      for (int k : lists[t]) {
+        const kiops_request& r = reqs[order[g0 + k]];
+        st = prepare(ctx, r.A, r.tau, r.p, r.b, r.tol, r.m_init, r.m_o, r.prec, r.w, K, 0, prep[k]);
+        if (st) return st;
+        team_bytes[t] = std::max(team_bytes[t], prep[k].L.total);
+      }
+    size_t off = 0;
+    std::vector<size_t> team_off((size_t)T);
+    for (int t = 0; t < T; ++t) {
+      team_off[t] = off;
+      off = align_up(off + team_bytes[t], 256);
+    }
+    const size_t stats_off = off;
+    off = align_up(off + (size_t)n * 16 * 8, 256);
+    const size_t ctr_off = off;
+    off = align_up(off + (size_t)T * 64 * 4 + 256, 256);
+    const size_t args_off = off;
+    off = align_up(off + (size_t)n * sizeof(SolveArgs), 256);
+    const size_t plan_off = off;
+    off = align_up(off + (size_t)(T + 1 + n) * 4, 256);
+    st = ensure_workspace(ctx, off);
+    if (st) return st;
+    char* base = (char*)ctx->ws;
+    std::vector<int> plan_ptr((size_t)T + 1, 0), plan_idx;
+    for (int t = 0; t < T; ++t) {
+      for (int k : lists[t]) {
+        bind(prep[k], base + team_off[t]);
+        prep[k].args.stats = (int64_t*)(base + stats_off + (size_t)k * 16 * 8);
+        prep[k].args.stats_d = (double*)(prep[k].args.stats + 10);
+        prep[k].args.abort_flag = (int*)(base + ctr_off + (size_t)T * 64 * 4);
+        prep[k].args.timeout_ns = (long long)(ctx->cfg.timeout_s * 1e9);
+        plan_idx.push_back(k);
+      }
+      plan_ptr[t + 1] = (int)plan_idx.size();
+    }
+    const size_t hbytes = (size_t)n * sizeof(SolveArgs) + (size_t)(T + 1 + n) * 4 + (size_t)n * 16 * 8 + 512;
+    st = ensure_pinned(ctx, hbytes);
+    if (st) return st;
+    char* hp = (char*)ctx->host_pinned;
+    for (int k = 0; k < n; ++k) std::memcpy(hp + (size_t)k * sizeof(SolveArgs), &prep[k].args, sizeof(SolveArgs));
+    int* hplan = (int*)(hp + (size_t)n * sizeof(SolveArgs));
+    std::memcpy(hplan, plan_ptr.data(), (size_t)(T + 1) * 4);
+    std::memcpy(hplan + T + 1, plan_idx.data(), (size_t)n * 4);
+    int64_t* hstats = (int64_t*)(hp + align_up((size_t)n * sizeof(SolveArgs) + (size_t)(T + 1 + n) * 4, 256));
+    KCHECK(ctx, cudaMemsetAsync(base + ctr_off, 0, (size_t)T * 64 * 4 + 256, ctx->stream));
+    KCHECK(ctx, cudaMemsetAsync(base + stats_off, 0, (size_t)n * 16 * 8, ctx->stream));
+    KCHECK(ctx, cudaMemcpyAsync(base + args_off, hp, (size_t)n * sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
+    KCHECK(ctx, cudaMemcpyAsync(base + plan_off, hplan, (size_t)(T + 1 + n) * 4, cudaMemcpyHostToDevice, ctx->stream));
+    const SolveArgs* dargs = (const SolveArgs*)(base + args_off);
+    const int* dptr = (const int*)(base + plan_off);
+    const int* didx = dptr + T + 1;
+    unsigned int* dctr = (unsigned int*)(base + ctr_off);
+    int* dabort = (int*)(base + ctr_off + (size_t)T * 64 * 4);
+    long long tns = (long long)(ctx->cfg.timeout_s * 1e9);
+    int Kv = K, Tv = T;
+    void* kargs[] = {(void*)&dargs, (void*)&dptr, (void*)&didx, (void*)&Kv, (void*)&Tv, (void*)&dctr, (void*)&dabort,
+                     (void*)&tns};
+    KCHECK(ctx, cudaLaunchCooperativeKernel(fn, T * K, kThreads, kargs, kDynSmem, ctx->stream));
+    KCHECK(ctx, cudaMemcpyAsync(hstats, base + stats_off, (size_t)n * 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < n; ++k) {
+      const int i = order[g0 + k];
+      const int64_t* sv = hstats + (size_t)k * 16;
+      fill_stats(stats ? &stats[i] : nullptr, sv, (const double*)(sv + 10), KIOPS_ENGINE_CTA, K);
+      if (sv[6] != ST_OK && worst == KIOPS_OK) worst = (kiops_status)sv[6];
+    }
+    g0 = g1;
+  }
+  if (worst != KIOPS_OK) return fail(ctx, worst, "at least one batch request failed (status %d)", (int)worst);
+  return KIOPS_OK;
+}
+
+static kiops_status batch_one_block_each(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
+
   if (!ctx || count < 0 || (count > 0 && !reqs)) return KIOPS_EINVAL;
   if (count == 0) return KIOPS_OK;
   // one kernel launch per (precision, operator kind) group; each block runs one request
@@ -728,6 +896,21 @@ kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* r
     if (s[6] != ST_OK && worst == KIOPS_OK) worst = (kiops_status)s[6];
   }
   if (worst != KIOPS_OK) return fail(ctx, worst, "at least one batch request failed (status %d)", (int)worst);
+  return KIOPS_OK;
+}
+
+kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
+  if (!ctx || count < 0 || (count > 0 && !reqs)) return KIOPS_EINVAL;
+  if (count == 0) return KIOPS_OK;
+  for (int i = 0; i < count; ++i)
+    if (!reqs[i].A || !reqs[i].b || !reqs[i].w) return fail(ctx, KIOPS_EINVAL, "request %d: NULL operator, b or w", i);
+  if (ctx->cfg.batch_team_blocks == 1) return batch_one_block_each(ctx, count, reqs, stats);
+  return batch_teams(ctx, count, reqs, stats);
+}
+
+kiops_status kiops_set_batch_team_blocks(kiops_ctx* ctx, int team_blocks) {
+  if (!ctx || team_blocks < 0) return KIOPS_EINVAL;
+  ctx->cfg.batch_team_blocks = team_blocks;
   return KIOPS_OK;
 }
 

@@ -1460,4 +1460,33 @@ stop:
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Team engine for batches: one cooperative launch is split into teams of `team_blocks` blocks.  Team t
+// runs the instances plan_idx[plan_ptr[t] .. plan_ptr[t+1]) one after another, each with the grid-team
+// code above restricted to the team (its own barrier counter, partial sums and workspace).  The host plans
+// the lists (largest estimated work first, each to the least-loaded team).
+// ------------------------------------------------------------------------------------------------
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads) kiops_team_kernel(const SolveArgs* __restrict__ all,
+                                                             const int* __restrict__ plan_ptr,
+                                                             const int* __restrict__ plan_idx, int team_blocks,
+                                                             int n_teams, unsigned int* team_ctr, int* abort_flag,
+                                                             long long timeout_ns) {
+  extern __shared__ double smem_dyn[];
+  __shared__ Ctl c;
+  __shared__ __align__(16) SolveArgs sa;
+  const int t = blockIdx.x / team_blocks;
+  if (t >= n_teams) return;  // blocks left over when the grid is not a multiple of the team size
+  GridTeam team{(int)(blockIdx.x % team_blocks), team_blocks, team_ctr + (size_t)t * 64, abort_flag, timeout_ns, 0u};
+  const int words = (int)(sizeof(SolveArgs) / sizeof(int));
+  for (int q = plan_ptr[t]; q < plan_ptr[t + 1]; ++q) {
+    const SolveArgs* src = all + plan_idx[q];
+    for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const int*)src)[i];
+    __syncthreads();
+    solve_body<T, KIND, GridTeam>(sa, team, c, smem_dyn);
+    // every block of the team leaves the instance before its workspace is reused
+    if (!team.sync(&c.sync_ok)) break;
+  }
+}
+
 }  // namespace kiops_dev

@@ -33,7 +33,8 @@ class kiops_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("m_min", C.c_int), ("m_max", C.c_int),
                 ("normalize_B", C.c_int), ("breakdown_tol", C.c_double), ("max_substeps", C.c_int64),
                 ("max_iterations", C.c_int64), ("timeout_s", C.c_double), ("engine", C.c_int),
-                ("grid_blocks", C.c_int), ("profile", C.c_int), ("fuse_stencil", C.c_int)]
+                ("grid_blocks", C.c_int), ("profile", C.c_int), ("fuse_stencil", C.c_int),
+                ("batch_team_blocks", C.c_int)]
 
 
 class kiops_stats(C.Structure):
@@ -96,6 +97,7 @@ _SIGS = {
     "kiops_solve_host": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
                           C.c_int, C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
     "kiops_solve_batch": ([C.c_void_p, C.c_int, C.POINTER(kiops_request), C.POINTER(kiops_stats)], C.c_int),
+    "kiops_set_batch_team_blocks": ([C.c_void_p, C.c_int], C.c_int),
     "kiops_expm": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "kiops_solve_noalloc": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
                              C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
@@ -236,6 +238,10 @@ def kiops_solve_noalloc(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, w_ptr) -> dic
     return st.as_dict()
 
 
+def kiops_set_batch_team_blocks(ctx, team_blocks: int) -> None:
+    _check(ctx, lib().kiops_set_batch_team_blocks(ctx, team_blocks), "kiops_set_batch_team_blocks")
+
+
 def kiops_expm(ctx, n, a_ptr, f_ptr) -> None:
     _check(ctx, lib().kiops_expm(ctx, n, a_ptr, f_ptr), "kiops_expm")
 
@@ -363,8 +369,11 @@ class Solver:
         st = kiops_solve_host(self.ctx, op.handle, tau, p, ptrs, tol, m_init, m_o, self._prec(precision), w.ctypes.data)
         return w, st
 
-    def solve_batch(self, items):
-        """items: list of (op, tau, b_tensor, tol, m_init, m_o, precision, w_tensor)."""
+    def solve_batch(self, items, team_blocks: int | None = None):
+        """items: list of (op, tau, b_tensor, tol, m_init, m_o, precision, w_tensor); team_blocks sets the
+        batch team size (None keeps the context's setting, 0 = automatic, 1 = one block per request)."""
+        if team_blocks is not None:
+            kiops_set_batch_team_blocks(self.ctx, team_blocks)
         reqs, keep = [], []
         for (op, tau, b, tol, m_init, m_o, precision, w) in items:
             p = b.shape[0] - 1
