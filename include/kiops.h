@@ -218,6 +218,40 @@ kiops_status kiops_set_batch_team_blocks(kiops_ctx* ctx, int team_blocks);
  * computed by the same on-device scaling-and-squaring code the solver uses for exp(tau H~). */
 kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f);
 
+/* ---- Serving: continuous batching of independent solves (one server per context).
+ *
+ * kiops_server_start launches a persistent cooperative kernel whose teams of blocks take requests from
+ * device-visible queues as soon as they finish the previous one; requests submitted while others run are
+ * admitted whenever a queue slot and workspace inside the HBM budget are free, and their work overlaps on
+ * the device.  Requests with an estimated work (see kiops_solve_batch) above large_work_threshold go to the
+ * "large" class (large_teams teams of large_team_blocks blocks), the others to teams of small_team_blocks
+ * blocks.  A request's result depends on its class's team size only, not on the other requests.
+ * While the server kernel runs it occupies the GPU: other solves on the device wait until it exits (it
+ * exits after idle_timeout_s without work and is relaunched by the next submit or poll).  The paper has no
+ * counterpart; this is the execution model of the build. */
+typedef struct {
+  double hbm_budget_bytes;      /* admission budget for request workspaces, allocated at start (120e9) */
+  int queue_slots;              /* request slots per class (512) */
+  int small_team_blocks;        /* blocks per small team (8) */
+  int large_team_blocks;        /* blocks per large team (0 = half of the co-resident blocks) */
+  int large_teams;              /* number of large teams (1; 0 = every request is small) */
+  double large_work_threshold;  /* estimated work above which a request is large (2e8) */
+  double idle_timeout_s;        /* the kernel exits after this long without work; must be < cfg.timeout_s (2) */
+} kiops_server_config;
+
+kiops_status kiops_server_config_default(kiops_server_config* cfg);
+kiops_status kiops_server_start(kiops_ctx* ctx, const kiops_server_config* cfg);
+/* Queue one request (same fields as kiops_solve; tau > 0).  b and w are borrowed until kiops_poll reports
+ * it done.  *ticket identifies it.  Errors: EINVAL, ENOMEM if it cannot fit the budget even alone. */
+kiops_status kiops_submit(kiops_ctx* ctx, const kiops_request* req, uint64_t* ticket);
+/* Wait up to timeout_s (0 = just check) for a ticket; *done = 1 and stats filled once it has finished. */
+kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* done, kiops_stats* stats);
+/* info[0..5] = pending (not yet admitted), in flight, reserved workspace bytes, small teams, large teams,
+ * blocks per large team. */
+kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]);
+/* Stop the server after the queued work (waits for the kernel), free its memory. */
+kiops_status kiops_server_stop(kiops_ctx* ctx);
+
 /* Size of the fixed device scratch used by kiops_solve_noalloc (bytes). */
 #define KIOPS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -11,13 +11,26 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kiops.h"
 #include "kiops_device.cuh"
+#include "kiops_kernels.h"
 
 using namespace kiops_dev;
+
+struct KiopsServer;  // serving state (kiops_server_start)
+struct kiops_ctx;
+
+extern "C" {
+static kiops_status batch_teams(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats);
+}
 
 struct kiops_ctx {
   kiops_config cfg;
@@ -33,6 +46,7 @@ struct kiops_ctx {
   size_t stage_bytes = 0;
   TaylorTable tt{};
   bool busy = false;
+  KiopsServer* server = nullptr;
 };
 
 struct kiops_op {
@@ -99,41 +113,10 @@ int max_r(const TaylorTable& tt) {
   return r;
 }
 
-template <typename T, int KIND, bool GRID>
-void* kernel_ptr() {
-  return (void*)kiops_solve_kernel<T, KIND, GRID>;
-}
-
-void* pick_kernel(bool fp32, int kind, bool grid) {
-  if (!fp32) {
-    if (grid) {
-      if (kind == OP_CSR) return kernel_ptr<double, OP_CSR, true>();
-      if (kind == OP_ST2D) return kernel_ptr<double, OP_ST2D, true>();
-      return kernel_ptr<double, OP_ST3D, true>();
-    }
-    if (kind == OP_CSR) return kernel_ptr<double, OP_CSR, false>();
-    if (kind == OP_ST2D) return kernel_ptr<double, OP_ST2D, false>();
-    return kernel_ptr<double, OP_ST3D, false>();
-  }
-  if (grid) {
-    if (kind == OP_CSR) return kernel_ptr<float, OP_CSR, true>();
-    if (kind == OP_ST2D) return kernel_ptr<float, OP_ST2D, true>();
-    return kernel_ptr<float, OP_ST3D, true>();
-  }
-  if (kind == OP_CSR) return kernel_ptr<float, OP_CSR, false>();
-  if (kind == OP_ST2D) return kernel_ptr<float, OP_ST2D, false>();
-  return kernel_ptr<float, OP_ST3D, false>();
-}
+void* pick_kernel(bool fp32, int kind) { return fp32 ? kiops_k::solve_kernel_f32(kind) : kiops_k::solve_kernel_f64(kind); }
 
 void* pick_team_kernel(bool fp32, int kind) {
-  if (!fp32) {
-    if (kind == OP_CSR) return (void*)kiops_team_kernel<double, OP_CSR>;
-    if (kind == OP_ST2D) return (void*)kiops_team_kernel<double, OP_ST2D>;
-    return (void*)kiops_team_kernel<double, OP_ST3D>;
-  }
-  if (kind == OP_CSR) return (void*)kiops_team_kernel<float, OP_CSR>;
-  if (kind == OP_ST2D) return (void*)kiops_team_kernel<float, OP_ST2D>;
-  return (void*)kiops_team_kernel<float, OP_ST3D>;
+  return fp32 ? kiops_k::team_kernel_f32(kind) : kiops_k::team_kernel_f64(kind);
 }
 
 constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
@@ -278,6 +261,7 @@ kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const
   a.timeout_ns = (long long)(ctx->cfg.timeout_s * 1e9);
   a.tt = ctx->tt;
   a.trace_cap = trace_cap;
+  a.prec = prec == KIOPS_FP32_BASIS ? 1 : 0;
   int64_t ldv = 0;
   int64_t df_elems = 0;  // FP32 copies of the coupling fields: nspecies^2 fields of the grid's points
   if (A->d.kind == OP_ST2D) df_elems = (int64_t)A->d.nspecies * A->d.nspecies * A->d.nx * A->d.ny;
@@ -352,7 +336,17 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   const bool fp32 = prec == KIOPS_FP32_BASIS;
   int engine = ctx->cfg.engine == KIOPS_ENGINE_CTA ? KIOPS_ENGINE_CTA : KIOPS_ENGINE_GRID;
   if (!A) return fail(ctx, KIOPS_EINVAL, "NULL operator");
-  void* fn = pick_kernel(fp32, A->d.kind, engine == KIOPS_ENGINE_GRID);
+  if (engine == KIOPS_ENGINE_CTA) {  // one block: a batch of one request on a one-block team
+    if (trace) return fail(ctx, KIOPS_EINVAL, "traces are recorded by the grid engine only");
+    kiops_request r{A, tau, p, b, tol, m_init, m_o, prec, w};
+    const int saved = ctx->cfg.batch_team_blocks;
+    ctx->cfg.batch_team_blocks = 1;
+    kiops_status st = batch_teams(ctx, 1, &r, stats);
+    ctx->cfg.batch_team_blocks = saved;
+    if (stats) stats->engine = KIOPS_ENGINE_CTA;
+    return st;
+  }
+  void* fn = pick_kernel(fp32, A->d.kind);
   kiops_status st = prepare_kernel(ctx, fn);
   if (st) return st;
   int blocks = engine == KIOPS_ENGINE_GRID ? grid_size(ctx, fn) : 1;
@@ -375,11 +369,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, hp, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
   const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
   void* kargs[] = {(void*)&dargs};
-  if (engine == KIOPS_ENGINE_GRID) {
-    KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, kDynSmem, ctx->stream));
-  } else {
-    KCHECK(ctx, cudaLaunchKernel(fn, 1, kThreads, kargs, kDynSmem, ctx->stream));
-  }
+  KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, kDynSmem, ctx->stream));
   int64_t* hs = (int64_t*)(hp + sizeof(SolveArgs) + 0);
   KCHECK(ctx, cudaMemcpyAsync(hs, P.base + P.L.stats, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
   int64_t* htl = hs + 15;
@@ -501,8 +491,11 @@ kiops_status kiops_create(kiops_ctx** out, const kiops_config* cfg) {
   return KIOPS_OK;
 }
 
+kiops_status kiops_server_stop(kiops_ctx* ctx);
+
 kiops_status kiops_destroy(kiops_ctx* ctx) {
   if (!ctx) return KIOPS_EINVAL;
+  if (ctx->server) kiops_server_stop(ctx);
   if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   if (ctx->stage_dev) cudaFree(ctx->stage_dev);
@@ -525,7 +518,7 @@ kiops_status kiops_workspace_size(kiops_ctx* ctx, const kiops_op* A, int p, int 
                                   size_t* bytes) {
   if (!ctx || !A || !bytes || p < 0 || p > KIOPS_MAX_P || m_o < 1) return KIOPS_EINVAL;
   const bool fp32 = prec == KIOPS_FP32_BASIS;
-  void* fn = pick_kernel(fp32, A->d.kind, true);
+  void* fn = pick_kernel(fp32, A->d.kind);
   kiops_status st = prepare_kernel(ctx, fn);
   if (st) return st;
   int blocks = std::max(grid_size(ctx, fn), 1);
@@ -816,95 +809,11 @@ static kiops_status batch_teams(kiops_ctx* ctx, int count, const kiops_request* 
   return KIOPS_OK;
 }
 
-static kiops_status batch_one_block_each(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
-
-  if (!ctx || count < 0 || (count > 0 && !reqs)) return KIOPS_EINVAL;
-  if (count == 0) return KIOPS_OK;
-  // one kernel launch per (precision, operator kind) group; each block runs one request
-  std::vector<Prepared> prep((size_t)count);
-  size_t total = 0;
-  for (int i = 0; i < count; ++i) {
-    const kiops_request& r = reqs[i];
-    kiops_status st = prepare(ctx, r.A, r.tau, r.p, r.b, r.tol, r.m_init, r.m_o, r.prec, r.w, 1, 0, prep[i]);
-    if (st) return st;
-    total = align_up(total, 256) + prep[i].L.total;
-  }
-  const size_t args_off = align_up(total, 256);
-  total = args_off + (size_t)count * sizeof(SolveArgs);
-  kiops_status st = ensure_workspace(ctx, total + 256);
-  if (st) return st;
-  size_t off = 0;
-  for (int i = 0; i < count; ++i) {
-    off = align_up(off, 256);
-    bind(prep[i], (char*)ctx->ws + off);
-    off += prep[i].L.total;
-  }
-  // contiguous argument array per group, staged through pinned memory
-  st = ensure_pinned(ctx, (size_t)count * (sizeof(SolveArgs) + 16 * 8) + 4096);
-  if (st) return st;
-  char* hp = (char*)ctx->host_pinned;
-  SolveArgs* hargs = (SolveArgs*)hp;
-  int64_t* hstats = (int64_t*)(hp + (size_t)count * sizeof(SolveArgs));
-  for (int i = 0; i < count; ++i) {
-    KCHECK(ctx, cudaMemsetAsync(prep[i].base + prep[i].L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
-    if (reqs[i].tau == 0.0)
-      KCHECK(ctx, cudaMemcpyAsync(reqs[i].w, reqs[i].b[0], (size_t)reqs[i].A->d.n * 8, cudaMemcpyDeviceToDevice,
-                                  ctx->stream));
-  }
-  // order requests by (precision, kind); tau == 0 requests are done above
-  std::vector<int> order;
-  for (int i = 0; i < count; ++i)
-    if (reqs[i].tau > 0.0) order.push_back(i);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    int kx = reqs[x].prec * 4 + reqs[x].A->d.kind, ky = reqs[y].prec * 4 + reqs[y].A->d.kind;
-    return kx < ky;
-  });
-  // device argument array, grouped in launch order, at the end of the workspace
-  void* dargs_all = (char*)ctx->ws + args_off;
-  for (size_t k = 0; k < order.size(); ++k) std::memcpy(&hargs[k], &prep[order[k]].args, sizeof(SolveArgs));
-  KCHECK(ctx, cudaMemcpyAsync(dargs_all, hargs, order.size() * sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
-  size_t g0 = 0;
-  while (g0 < order.size()) {
-    size_t g1 = g0;
-    const int key = reqs[order[g0]].prec * 4 + reqs[order[g0]].A->d.kind;
-    while (g1 < order.size() && reqs[order[g1]].prec * 4 + reqs[order[g1]].A->d.kind == key) ++g1;
-    void* fn = pick_kernel(reqs[order[g0]].prec == KIOPS_FP32_BASIS, reqs[order[g0]].A->d.kind, false);
-    st = prepare_kernel(ctx, fn);
-    if (st) return st;
-    const SolveArgs* dptr = (const SolveArgs*)dargs_all + g0;
-    void* kargs[] = {(void*)&dptr};
-    cudaError_t e = cudaLaunchKernel(fn, (unsigned)(g1 - g0), kThreads, kargs, kDynSmem, ctx->stream);
-    if (e != cudaSuccess) return fail(ctx, KIOPS_ECUDA, "batch launch: %s", cudaGetErrorString(e));
-    g0 = g1;
-  }
-  for (int i = 0; i < count; ++i)
-    KCHECK(ctx, cudaMemcpyAsync(hstats + (size_t)i * 16, prep[i].base + prep[i].L.stats, 16 * 8, cudaMemcpyDeviceToHost,
-                                ctx->stream));
-  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
-  kiops_status worst = KIOPS_OK;
-  for (int i = 0; i < count; ++i) {
-    const int64_t* s = hstats + (size_t)i * 16;
-    if (reqs[i].tau == 0.0) {
-      if (stats) {
-        std::memset(&stats[i], 0, sizeof(kiops_stats));
-        stats[i].engine = KIOPS_ENGINE_CTA;
-        stats[i].grid_blocks = 1;
-      }
-      continue;
-    }
-    fill_stats(stats ? &stats[i] : nullptr, s, (const double*)(s + 10), KIOPS_ENGINE_CTA, 1);
-    if (s[6] != ST_OK && worst == KIOPS_OK) worst = (kiops_status)s[6];
-  }
-  if (worst != KIOPS_OK) return fail(ctx, worst, "at least one batch request failed (status %d)", (int)worst);
-  return KIOPS_OK;
-}
-
 kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
   if (!ctx || count < 0 || (count > 0 && !reqs)) return KIOPS_EINVAL;
   if (count == 0) return KIOPS_OK;
   for (int i = 0; i < count; ++i)
     if (!reqs[i].A || !reqs[i].b || !reqs[i].w) return fail(ctx, KIOPS_EINVAL, "request %d: NULL operator, b or w", i);
-  if (ctx->cfg.batch_team_blocks == 1) return batch_one_block_each(ctx, count, reqs, stats);
   return batch_teams(ctx, count, reqs, stats);
 }
 
@@ -916,7 +825,7 @@ kiops_status kiops_set_batch_team_blocks(kiops_ctx* ctx, int team_blocks) {
 
 kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f) {
   if (!ctx || !a || !f || n < 1 || n > KIOPS_MAX_M + 1) return KIOPS_EINVAL;
-  void* fn = pick_kernel(false, OP_CSR, true);
+  void* fn = pick_kernel(false, OP_CSR);
   kiops_status st = prepare_kernel(ctx, fn);
   if (st) return st;
   int blocks = grid_size(ctx, fn);
@@ -965,25 +874,6 @@ namespace {
 constexpr int kNoallocMaxDevices = 64;
 void* g_noalloc_addr[kNoallocMaxDevices] = {};
 
-// The argument block travels by value (no staging buffer); one block runs the whole solve.
-template <int KIND>
-__global__ void __launch_bounds__(kThreads) kiops_solve_kernel_byval(const __grid_constant__ SolveArgs args) {
-  extern __shared__ double smem_dyn[];
-  __shared__ Ctl c;
-  __shared__ __align__(16) SolveArgs sa;
-  const int words = (int)(sizeof(SolveArgs) / sizeof(int));
-  for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const int*)&args)[i];
-  __syncthreads();
-  CtaTeam team;
-  solve_body<double, KIND, CtaTeam>(sa, team, c, smem_dyn);
-}
-
-void* noalloc_kernel(int kind) {
-  if (kind == OP_CSR) return (void*)kiops_solve_kernel_byval<OP_CSR>;
-  if (kind == OP_ST2D) return (void*)kiops_solve_kernel_byval<OP_ST2D>;
-  return (void*)kiops_solve_kernel_byval<OP_ST3D>;
-}
-
 }  // namespace
 
 extern "C" kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, double tau, int p,
@@ -1018,7 +908,7 @@ extern "C" kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, d
   bind(P, (char*)g_noalloc_addr[dev]);
   // the array keeps the previous call's contents: clear the barrier word, abort flag, stats, trace count
   KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
-  void* fn = noalloc_kernel(A->d.kind);
+  void* fn = kiops_k::noalloc_kernel(A->d.kind);
   KCHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
   void* kargs[] = {(void*)&P.args};
   KCHECK(ctx, cudaLaunchKernel(fn, 1, kThreads, kargs, kDynSmem, ctx->stream));
@@ -1033,3 +923,353 @@ extern "C" kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, d
   if (dst != ST_OK) return fail(ctx, (kiops_status)dst, "device status %d", dst);
   return KIOPS_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Serving (continuous batching): one persistent server kernel per context, request queues in mapped
+// host memory, per-request workspace from an arena of the HBM budget (first-fit free list).
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+struct Arena {
+  size_t bytes = 0;
+  std::map<size_t, size_t> free_;  // offset -> size
+  void init(size_t n) {
+    bytes = n;
+    free_.clear();
+    if (n) free_[0] = n;
+  }
+  bool alloc(size_t n, size_t& off) {
+    n = align_up(n, 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= n) {
+        off = it->first;
+        const size_t rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        return true;
+      }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = align_up(n, 256);
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+struct MappedQueues {  // lives in mapped pinned host memory
+  unsigned int tail[kServerClasses][16];
+  int stop[16];
+};
+
+struct InFlight {
+  int cls = 0, slot = -1;
+  size_t off = 0, bytes = 0;
+  int64_t* stats_dev = nullptr;
+};
+
+struct Pending {
+  uint64_t ticket;
+  int cls;
+  Prepared P;
+};
+
+}  // namespace
+
+struct KiopsServer {
+  kiops_server_config cfg{};
+  cudaStream_t kstream = nullptr, cstream = nullptr;
+  cudaEvent_t kdone = nullptr;
+  bool launched = false;
+  // mapped host memory
+  MappedQueues* q = nullptr;
+  SolveArgs* slots_h[kServerClasses] = {};
+  unsigned long long* done_h[kServerClasses] = {};
+  void* mapped_base = nullptr;
+  // device memory
+  void* dev_base = nullptr;
+  ServerDev sd{};
+  char* arena_base = nullptr;
+  Arena arena;
+  std::vector<char> slot_busy[kServerClasses];
+  unsigned int next_index[kServerClasses] = {};
+  uint64_t next_ticket = 1;
+  std::deque<Pending> pending;
+  std::unordered_map<uint64_t, InFlight> inflight;
+  std::unordered_map<uint64_t, std::vector<int64_t>> finished;  // ticket -> 16 stats words
+  int grid = 0;
+};
+
+namespace {
+
+kiops_status server_launch(kiops_ctx* ctx, KiopsServer* S) {
+  void* fn = kiops_k::server_kernel();
+  KCHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
+  // a new launch starts every team's barrier epochs at zero: clear the team counters and claim words
+  const int n_teams = S->sd.teams[0] + S->sd.teams[1];
+  KCHECK(ctx, cudaMemsetAsync(S->sd.team_ctr, 0, (size_t)n_teams * 64 * 4 * 2, S->kstream));
+  void* kargs[] = {(void*)&S->sd};
+  KCHECK(ctx, cudaLaunchCooperativeKernel(fn, S->grid, kThreads, kargs, kDynSmem, S->kstream));
+  KCHECK(ctx, cudaEventRecord(S->kdone, S->kstream));
+  S->launched = true;
+  return KIOPS_OK;
+}
+
+bool server_kernel_running(KiopsServer* S) { return S->launched && cudaEventQuery(S->kdone) == cudaErrorNotReady; }
+
+// Admit pending requests (budget and slot permitting), collect completions, relaunch an exited kernel.
+kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
+  // completions
+  std::vector<uint64_t> done_now;
+  for (auto& kv : S->inflight) {
+    const InFlight& f = kv.second;
+    const unsigned long long v = *(volatile unsigned long long*)(S->done_h[f.cls] + f.slot);
+    if (v == kv.first) done_now.push_back(kv.first);
+  }
+  for (uint64_t t : done_now) {
+    InFlight f = S->inflight[t];
+    std::vector<int64_t> st(16);
+    KCHECK(ctx, cudaMemcpyAsync(st.data(), f.stats_dev, 16 * 8, cudaMemcpyDeviceToHost, S->cstream));
+    KCHECK(ctx, cudaStreamSynchronize(S->cstream));
+    S->finished[t] = st;
+    S->arena.release(f.off, f.bytes);
+    S->slot_busy[f.cls][f.slot] = 0;
+    S->inflight.erase(t);
+  }
+  // admissions, in arrival order per class (a request that does not fit waits; later ones may pass it)
+  bool enqueued = false;
+  for (auto it = S->pending.begin(); it != S->pending.end();) {
+    Pending& pd = *it;
+    const int c = pd.cls;
+    const int slot = (int)(S->next_index[c] % (unsigned)S->cfg.queue_slots);
+    size_t off = 0;
+    if (S->slot_busy[c][slot] || !S->arena.alloc(pd.P.L.total, off)) {
+      ++it;
+      continue;
+    }
+    bind(pd.P, S->arena_base + off);
+    pd.P.args.ticket = pd.ticket;
+    pd.P.args.timeout_ns = (long long)(ctx->cfg.timeout_s * 1e9);
+    KCHECK(ctx, cudaMemsetAsync(pd.P.base + pd.P.L.bar, 0, 256 + 16 * 8 + 256, S->cstream));
+    KCHECK(ctx, cudaStreamSynchronize(S->cstream));
+    S->done_h[c][slot] = 0;
+    std::memcpy((void*)(S->slots_h[c] + slot), &pd.P.args, sizeof(SolveArgs));
+    InFlight f;
+    f.cls = c;
+    f.slot = slot;
+    f.off = off;
+    f.bytes = pd.P.L.total;
+    f.stats_dev = pd.P.args.stats;
+    S->inflight[pd.ticket] = f;
+    S->slot_busy[c][slot] = 1;
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);  // the slot is written before the tail moves
+    S->next_index[c] += 1;
+    __atomic_store_n(&S->q->tail[c][0], S->next_index[c], __ATOMIC_RELEASE);
+    enqueued = true;
+    it = S->pending.erase(it);
+  }
+  if ((enqueued || !S->inflight.empty()) && !server_kernel_running(S)) {
+    if (S->launched) {
+      cudaError_t e = cudaEventQuery(S->kdone);
+      if (e != cudaSuccess) return fail(ctx, KIOPS_ECUDA, "server kernel: %s", cudaGetErrorString(e));
+    }
+    kiops_status st = server_launch(ctx, S);
+    if (st) return st;
+  }
+  return KIOPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kiops_status kiops_server_config_default(kiops_server_config* cfg) {
+  if (!cfg) return KIOPS_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->hbm_budget_bytes = 120e9;
+  cfg->queue_slots = 512;
+  cfg->small_team_blocks = 8;
+  cfg->large_team_blocks = 0;
+  cfg->large_teams = 1;
+  cfg->large_work_threshold = 2e8;
+  cfg->idle_timeout_s = 2.0;
+  return KIOPS_OK;
+}
+
+kiops_status kiops_server_start(kiops_ctx* ctx, const kiops_server_config* cfg_in) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (ctx->server) return fail(ctx, KIOPS_EBUSY, "a server is already running on this context");
+  kiops_server_config cfg;
+  if (cfg_in) cfg = *cfg_in; else kiops_server_config_default(&cfg);
+  if (!(cfg.hbm_budget_bytes > 0) || cfg.queue_slots < 1 || cfg.small_team_blocks < 1 || cfg.large_teams < 0 ||
+      !(cfg.idle_timeout_s > 0) || cfg.idle_timeout_s >= ctx->cfg.timeout_s)
+    return fail(ctx, KIOPS_EINVAL, "invalid server configuration (the idle timeout must be below cfg.timeout_s)");
+  void* fn = kiops_k::server_kernel();
+  kiops_status st = prepare_kernel(ctx, fn);
+  if (st) return st;
+  int per_sm = 0;
+  KCHECK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kDynSmem));
+  const int G = per_sm * ctx->sms;
+  if (G < 2) return fail(ctx, KIOPS_ECUDA, "server kernel does not fit");
+  std::unique_ptr<KiopsServer> S(new KiopsServer());
+  int large_K = cfg.large_team_blocks > 0 ? cfg.large_team_blocks : G / 2;
+  int large_T = cfg.large_teams;
+  if (large_T * large_K >= G) large_T = 0;
+  const int small_K = std::min(cfg.small_team_blocks, G);
+  const int small_T = (G - large_T * large_K) / small_K;
+  if (small_T < 1) return fail(ctx, KIOPS_EINVAL, "team sizes leave no small team");
+  cfg.large_team_blocks = large_K;
+  cfg.large_teams = large_T;
+  S->cfg = cfg;
+  ServerDev& sd = S->sd;
+  sd.n_classes = kServerClasses;
+  sd.team_blocks[0] = small_K;
+  sd.teams[0] = small_T;
+  sd.first_block[0] = 0;
+  sd.team_blocks[1] = std::max(large_K, 1);
+  sd.teams[1] = large_T;
+  sd.first_block[1] = small_T * small_K;
+  S->grid = small_T * small_K + large_T * large_K;
+  sd.slots_per_class = cfg.queue_slots;
+  const int n_teams = small_T + large_T;
+  // mapped host memory: queue words, request slots, completion words
+  const size_t slots_bytes = (size_t)kServerClasses * cfg.queue_slots * sizeof(SolveArgs);
+  const size_t done_bytes = (size_t)kServerClasses * cfg.queue_slots * 8;
+  const size_t mapped = align_up(sizeof(MappedQueues), 256) + align_up(slots_bytes, 256) + done_bytes;
+  KCHECK(ctx, cudaHostAlloc(&S->mapped_base, mapped, cudaHostAllocMapped | cudaHostAllocPortable));
+  std::memset(S->mapped_base, 0, mapped);
+  char* hb = (char*)S->mapped_base;
+  S->q = (MappedQueues*)hb;
+  char* dp = nullptr;
+  KCHECK(ctx, cudaHostGetDevicePointer((void**)&dp, S->mapped_base, 0));
+  const size_t o_slots = align_up(sizeof(MappedQueues), 256), o_done = o_slots + align_up(slots_bytes, 256);
+  for (int c = 0; c < kServerClasses; ++c) {
+    S->slots_h[c] = (SolveArgs*)(hb + o_slots) + (size_t)c * cfg.queue_slots;
+    S->done_h[c] = (unsigned long long*)(hb + o_done) + (size_t)c * cfg.queue_slots;
+    sd.tail[c] = (const unsigned int*)(dp + offsetof(MappedQueues, tail) + (size_t)c * 16 * 4);
+    sd.slots[c] = (const SolveArgs*)(dp + o_slots) + (size_t)c * cfg.queue_slots;
+    sd.done[c] = (unsigned long long*)(dp + o_done) + (size_t)c * cfg.queue_slots;
+    S->slot_busy[c].assign((size_t)cfg.queue_slots, 0);
+  }
+  sd.stop = (const int*)(dp + offsetof(MappedQueues, stop));
+  // device memory: heads, team counters, claims, abort flag, team partials; then the arena
+  const size_t stride = (size_t)2 * kMaxRed * std::max(large_K, small_K);
+  const size_t dev_small = 256 * 2 + (size_t)n_teams * 64 * 4 * 2 + 256 + (size_t)n_teams * stride * 8 + 4096;
+  const size_t arena_bytes = (size_t)cfg.hbm_budget_bytes;
+  cudaError_t e = cudaMalloc(&S->dev_base, align_up(dev_small, 256) + arena_bytes);
+  if (e != cudaSuccess) {
+    cudaFreeHost(S->mapped_base);
+    return fail(ctx, KIOPS_ENOMEM, "server memory (budget %.3g bytes): %s", cfg.hbm_budget_bytes, cudaGetErrorString(e));
+  }
+  char* db = (char*)S->dev_base;
+  KCHECK(ctx, cudaMemset(db, 0, dev_small));
+  sd.head[0] = (unsigned int*)db;
+  sd.head[1] = (unsigned int*)(db + 256);
+  sd.team_ctr = (unsigned int*)(db + 512);
+  sd.team_claim = (int*)(db + 512 + (size_t)n_teams * 64 * 4);
+  sd.abort_flag = (int*)(db + 512 + (size_t)n_teams * 64 * 8);
+  sd.team_partials = (double*)(db + align_up(512 + (size_t)n_teams * 64 * 8 + 256, 256));
+  sd.team_partials_stride = stride;
+  sd.timeout_ns = (long long)(ctx->cfg.timeout_s * 1e9);
+  sd.idle_ns = (long long)(cfg.idle_timeout_s * 1e9);
+  S->arena_base = db + align_up(dev_small, 256);
+  S->arena.init(arena_bytes);
+  KCHECK(ctx, cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking));
+  KCHECK(ctx, cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking));
+  KCHECK(ctx, cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming));
+  ctx->server = S.release();
+  return KIOPS_OK;
+}
+
+kiops_status kiops_submit(kiops_ctx* ctx, const kiops_request* r, uint64_t* ticket) {
+  if (!ctx || !r || !ticket) return KIOPS_EINVAL;
+  KiopsServer* S = ctx->server;
+  if (!S) return fail(ctx, KIOPS_EINVAL, "no server: call kiops_server_start first");
+  if (!r->A || !r->b || !r->w) return fail(ctx, KIOPS_EINVAL, "NULL operator, b or w");
+  if (!(r->tau > 0.0)) return fail(ctx, KIOPS_EINVAL, "served requests need tau > 0");
+  const int cls = (S->cfg.large_teams > 0 && estimate_work(ctx, *r) > S->cfg.large_work_threshold) ? 1 : 0;
+  Pending pd;
+  pd.ticket = S->next_ticket++;
+  pd.cls = cls;
+  kiops_status st = prepare(ctx, r->A, r->tau, r->p, r->b, r->tol, r->m_init, r->m_o, r->prec, r->w,
+                            S->sd.team_blocks[cls], 0, pd.P);
+  if (st) return st;
+  if (pd.P.L.total > S->arena.bytes)
+    return fail(ctx, KIOPS_ENOMEM, "request workspace %zu bytes exceeds the HBM budget %zu", pd.P.L.total, S->arena.bytes);
+  S->pending.push_back(pd);
+  *ticket = pd.ticket;
+  return server_pump(ctx, S);
+}
+
+kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* done, kiops_stats* stats) {
+  if (!ctx || !done) return KIOPS_EINVAL;
+  KiopsServer* S = ctx->server;
+  if (!S) return fail(ctx, KIOPS_EINVAL, "no server");
+  *done = 0;
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    kiops_status st = server_pump(ctx, S);
+    if (st) return st;
+    auto it = S->finished.find(ticket);
+    if (it != S->finished.end()) {
+      const std::vector<int64_t>& sv = it->second;
+      fill_stats(stats, sv.data(), (const double*)(sv.data() + 10), KIOPS_ENGINE_GRID,
+                 (int)S->sd.team_blocks[0]);
+      const int dst = (int)sv[6];
+      S->finished.erase(it);
+      *done = 1;
+      if (dst != ST_OK) return fail(ctx, (kiops_status)dst, "served request %llu: device status %d",
+                                    (unsigned long long)ticket, dst);
+      return KIOPS_OK;
+    }
+    const bool known = S->inflight.count(ticket) ||
+                       std::any_of(S->pending.begin(), S->pending.end(), [&](const Pending& p) { return p.ticket == ticket; });
+    if (!known) return fail(ctx, KIOPS_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= timeout_s) return KIOPS_OK;
+  }
+}
+
+kiops_status kiops_server_stop(kiops_ctx* ctx) {
+  if (!ctx) return KIOPS_EINVAL;
+  KiopsServer* S = ctx->server;
+  if (!S) return KIOPS_OK;
+  __atomic_store_n(&S->q->stop[0], 1, __ATOMIC_RELEASE);
+  kiops_status rc = KIOPS_OK;
+  if (S->launched && cudaStreamSynchronize(S->kstream) != cudaSuccess) rc = fail(ctx, KIOPS_ECUDA, "server kernel failed");
+  cudaEventDestroy(S->kdone);
+  cudaStreamDestroy(S->kstream);
+  cudaStreamDestroy(S->cstream);
+  cudaFree(S->dev_base);
+  cudaFreeHost(S->mapped_base);
+  delete S;
+  ctx->server = nullptr;
+  return rc;
+}
+
+kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]) {
+  if (!ctx || !info || !ctx->server) return KIOPS_EINVAL;
+  KiopsServer* S = ctx->server;
+  size_t free_bytes = 0;
+  for (auto& kv : S->arena.free_) free_bytes += kv.second;
+  info[0] = (int64_t)S->pending.size();
+  info[1] = (int64_t)S->inflight.size();
+  info[2] = (int64_t)(S->arena.bytes - free_bytes);
+  info[3] = S->sd.teams[0];
+  info[4] = S->sd.teams[1];
+  info[5] = S->sd.team_blocks[1];
+  return KIOPS_OK;
+}
+
+}  // extern "C"

@@ -101,6 +101,8 @@ struct SolveArgs {
   void* raw;                 // two raw vectors x_{j+1} of ldv elements (ring, fused path only)
   float* bf;                 // FP32 basis: B columns as floats, column t = b_{p-t} at bf + t*ldv
   float* df;                 // FP32 basis: pointwise coupling fields as floats, (s*ns + q)*npts (stencils)
+  int prec;                  // 0 FP64 basis, 1 FP32 basis (runtime dispatch in the server kernel)
+  unsigned long long ticket; // serving: written to the completion word when the solve is done
   int expm_only;             // 1: compute exp(a) of an n x n matrix only (kiops_expm)
   int expm_n;
   const double* expm_in;
@@ -282,14 +284,14 @@ template <class Team>
 __device__ bool finish_reduce(Team& team, Ctl& c, double* partials, int& parity, int K, bool prof_on = false);
 
 template <>
-__device__ bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, int&, int K, bool) {
+__device__ inline bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, int&, int K, bool) {
   for (int k = threadIdx.x; k < K; k += kThreads) c.red[k] = c.blk[k];
   __syncthreads();
   return true;
 }
 
 template <>
-__device__ bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K,
+__device__ inline bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K,
                                         bool prof_on) {
   double* buf = partials + (size_t)parity * team.size * kMaxRed;
   for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
@@ -527,7 +529,7 @@ __device__ __forceinline__ Band band_product(Band a, Band b, int n) {
 
 // C = A B (+ epilogue) for n x n row-major matrices; tiles of kTile x kTile distributed over ranks.
 // Tiles outside the band of C are written as zeros without arithmetic.
-__device__ void mm_team(const double* A, Band bA, const double* B, Band bB, double* C, int n, int rank, int size,
+__device__ inline void mm_team(const double* A, Band bA, const double* B, Band bB, double* C, int n, int rank, int size,
                         const Ctl& c, const MmEpi& epi, double* sA, double* sB) {
   const Band bC = band_product(bA, bB, n);
   const int nt = (n + kTile - 1) / kTile;
@@ -1460,6 +1462,20 @@ stop:
   }
 }
 
+// Single-block solve with the argument block passed by value (no staging buffer): the allocation-free
+// entry point uses it.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) kiops_solve_kernel_byval(const __grid_constant__ SolveArgs args) {
+  extern __shared__ double smem_dyn[];
+  __shared__ Ctl c;
+  __shared__ __align__(16) SolveArgs sa;
+  const int words = (int)(sizeof(SolveArgs) / sizeof(int));
+  for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const int*)&args)[i];
+  __syncthreads();
+  CtaTeam team;
+  solve_body<double, KIND, CtaTeam>(sa, team, c, smem_dyn);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Team engine for batches: one cooperative launch is split into teams of `team_blocks` blocks.  Team t
 // runs the instances plan_idx[plan_ptr[t] .. plan_ptr[t+1]) one after another, each with the grid-team
@@ -1486,6 +1502,110 @@ __global__ void __launch_bounds__(kThreads) kiops_team_kernel(const SolveArgs* _
     solve_body<T, KIND, GridTeam>(sa, team, c, smem_dyn);
     // every block of the team leaves the instance before its workspace is reused
     if (!team.sync(&c.sync_ok)) break;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Serving: a persistent kernel whose teams take requests from queues as they arrive (continuous
+// batching).  Queue words and request slots live in mapped host memory: the host writes a slot and then
+// advances the class's tail with release semantics; a team leader claims index `head` with a CAS when
+// head < tail (acquire), copies the slot, runs the solve, and publishes the request's ticket in the
+// slot's completion word (system-scope release).  Teams of class c have team_blocks[c] blocks.  Every
+// wait is bounded: an idle team leaves after idle_ns without work (the host relaunches the kernel), the
+// barriers keep their own deadline.
+// ------------------------------------------------------------------------------------------------
+constexpr int kServerClasses = 2;
+
+struct ServerDev {
+  int n_classes;
+  int team_blocks[kServerClasses], teams[kServerClasses], first_block[kServerClasses];
+  int slots_per_class;
+  const unsigned int* tail[kServerClasses];  // mapped host memory
+  unsigned int* head[kServerClasses];        // device memory
+  const int* stop;                           // mapped host memory
+  const SolveArgs* slots[kServerClasses];    // mapped host memory
+  unsigned long long* done[kServerClasses];  // mapped host memory
+  unsigned int* team_ctr;                    // 64 words per team (device)
+  double* team_partials;                     // 2 * kMaxRed * team_blocks per team (device)
+  size_t team_partials_stride;               // doubles per team
+  int* team_claim;                           // one word per team, 64 apart (device)
+  int* abort_flag;
+  long long timeout_ns, idle_ns;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_sys(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_sys_int(const int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int Unused>
+__global__ void __launch_bounds__(kThreads) kiops_server_kernel(const __grid_constant__ ServerDev sd) {
+  extern __shared__ double smem_dyn[];
+  __shared__ Ctl c;
+  __shared__ __align__(16) SolveArgs sa;
+  int cls = -1;
+  for (int k = 0; k < sd.n_classes; ++k)
+    if ((int)blockIdx.x >= sd.first_block[k] && (int)blockIdx.x < sd.first_block[k] + sd.teams[k] * sd.team_blocks[k])
+      cls = k;
+  if (cls < 0) return;
+  const int local = (int)blockIdx.x - sd.first_block[cls];
+  const int K = sd.team_blocks[cls];
+  int team_id = local / K;
+  for (int k = 0; k < cls; ++k) team_id += sd.teams[k];
+  GridTeam team{local % K, K, sd.team_ctr + (size_t)team_id * 64, sd.abort_flag, sd.timeout_ns, 0u};
+  const int words = (int)(sizeof(SolveArgs) / sizeof(int));
+  while (true) {
+    if (team.rank == 0 && threadIdx.x == 0) {
+      int claimed = -1;
+      const long long t0 = global_ns();
+      while (true) {
+        const unsigned int h = *(volatile unsigned int*)sd.head[cls];
+        const unsigned int tl = ld_acquire_sys(sd.tail[cls]);
+        if ((int)(tl - h) > 0) {
+          if (atomicCAS(sd.head[cls], h, h + 1) == h) { claimed = (int)h; break; }
+          continue;
+        }
+        if (ld_acquire_sys_int(sd.stop) || ld_volatile_int(sd.abort_flag)) break;
+        if (global_ns() - t0 > sd.idle_ns) break;
+        __nanosleep(1000);
+      }
+      sd.team_claim[(size_t)team_id * 64] = claimed;
+    }
+    if (!team.sync(&c.sync_ok)) return;
+    const int claimed = *(volatile int*)(sd.team_claim + (size_t)team_id * 64);
+    if (claimed < 0) return;
+    const SolveArgs* src = sd.slots[cls] + (claimed % sd.slots_per_class);
+    for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const volatile int*)src)[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sa.partials = sd.team_partials + (size_t)team_id * sd.team_partials_stride;
+      sa.abort_flag = sd.abort_flag;
+    }
+    __syncthreads();
+    const int kind = sa.op.kind;
+    if (sa.prec == 0) {
+      if (kind == OP_CSR) solve_body<double, OP_CSR, GridTeam>(sa, team, c, smem_dyn);
+      else if (kind == OP_ST2D) solve_body<double, OP_ST2D, GridTeam>(sa, team, c, smem_dyn);
+      else solve_body<double, OP_ST3D, GridTeam>(sa, team, c, smem_dyn);
+    } else {
+      if (kind == OP_CSR) solve_body<float, OP_CSR, GridTeam>(sa, team, c, smem_dyn);
+      else if (kind == OP_ST2D) solve_body<float, OP_ST2D, GridTeam>(sa, team, c, smem_dyn);
+      else solve_body<float, OP_ST3D, GridTeam>(sa, team, c, smem_dyn);
+    }
+    if (!team.sync(&c.sync_ok)) return;
+    if (team.rank == 0 && threadIdx.x == 0) {
+      __threadfence_system();
+      st_release_sys_u64(sd.done[cls] + (claimed % sd.slots_per_class), sa.ticket);
+    }
   }
 }
 

@@ -1,0 +1,23 @@
+// FP64-basis kernel instantiations.
+#include "kiops_device.cuh"
+#include "kiops_kernels.h"
+
+using namespace kiops_dev;
+
+namespace kiops_k {
+void* solve_kernel_f64(int kind) {
+  if (kind == OP_CSR) return (void*)kiops_solve_kernel<double, OP_CSR, true>;
+  if (kind == OP_ST2D) return (void*)kiops_solve_kernel<double, OP_ST2D, true>;
+  return (void*)kiops_solve_kernel<double, OP_ST3D, true>;
+}
+void* team_kernel_f64(int kind) {
+  if (kind == OP_CSR) return (void*)kiops_team_kernel<double, OP_CSR>;
+  if (kind == OP_ST2D) return (void*)kiops_team_kernel<double, OP_ST2D>;
+  return (void*)kiops_team_kernel<double, OP_ST3D>;
+}
+void* noalloc_kernel(int kind) {
+  if (kind == OP_CSR) return (void*)kiops_solve_kernel_byval<OP_CSR>;
+  if (kind == OP_ST2D) return (void*)kiops_solve_kernel_byval<OP_ST2D>;
+  return (void*)kiops_solve_kernel_byval<OP_ST3D>;
+}
+}  // namespace kiops_k

@@ -65,6 +65,12 @@ class kiops_stencil3d_desc(C.Structure):
                 ("coef", C.c_double * 7), ("diag", C.c_void_p)]
 
 
+class kiops_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("queue_slots", C.c_int), ("small_team_blocks", C.c_int),
+                ("large_team_blocks", C.c_int), ("large_teams", C.c_int), ("large_work_threshold", C.c_double),
+                ("idle_timeout_s", C.c_double)]
+
+
 class kiops_request(C.Structure):
     _fields_ = [("A", C.c_void_p), ("tau", C.c_double), ("p", C.c_int), ("b", C.POINTER(C.c_void_p)),
                 ("tol", C.c_double), ("m_init", C.c_int), ("m_o", C.c_int), ("prec", C.c_int), ("w", C.c_void_p)]
@@ -98,6 +104,12 @@ _SIGS = {
                           C.c_int, C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
     "kiops_solve_batch": ([C.c_void_p, C.c_int, C.POINTER(kiops_request), C.POINTER(kiops_stats)], C.c_int),
     "kiops_set_batch_team_blocks": ([C.c_void_p, C.c_int], C.c_int),
+    "kiops_server_config_default": ([C.POINTER(kiops_server_config)], C.c_int),
+    "kiops_server_start": ([C.c_void_p, C.POINTER(kiops_server_config)], C.c_int),
+    "kiops_submit": ([C.c_void_p, C.POINTER(kiops_request), C.POINTER(C.c_uint64)], C.c_int),
+    "kiops_poll": ([C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_int), C.POINTER(kiops_stats)], C.c_int),
+    "kiops_server_info": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "kiops_server_stop": ([C.c_void_p], C.c_int),
     "kiops_expm": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "kiops_solve_noalloc": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
                              C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
@@ -242,6 +254,40 @@ def kiops_set_batch_team_blocks(ctx, team_blocks: int) -> None:
     _check(ctx, lib().kiops_set_batch_team_blocks(ctx, team_blocks), "kiops_set_batch_team_blocks")
 
 
+def kiops_server_config_default() -> kiops_server_config:
+    cfg = kiops_server_config()
+    lib().kiops_server_config_default(C.byref(cfg))
+    return cfg
+
+
+def kiops_server_start(ctx, cfg: kiops_server_config | None = None) -> None:
+    _check(ctx, lib().kiops_server_start(ctx, C.byref(cfg) if cfg is not None else None), "kiops_server_start")
+
+
+def kiops_submit(ctx, req: kiops_request) -> int:
+    t = C.c_uint64(0)
+    _check(ctx, lib().kiops_submit(ctx, C.byref(req), C.byref(t)), "kiops_submit")
+    return t.value
+
+
+def kiops_poll(ctx, ticket: int, timeout_s: float = 0.0):
+    done = C.c_int(0)
+    st = kiops_stats()
+    _check(ctx, lib().kiops_poll(ctx, ticket, timeout_s, C.byref(done), C.byref(st)), "kiops_poll")
+    return bool(done.value), (st.as_dict() if done.value else None)
+
+
+def kiops_server_info(ctx) -> dict:
+    v = (C.c_int64 * 6)()
+    _check(ctx, lib().kiops_server_info(ctx, v), "kiops_server_info")
+    return {"pending": v[0], "in_flight": v[1], "reserved_bytes": v[2], "small_teams": v[3], "large_teams": v[4],
+            "large_team_blocks": v[5]}
+
+
+def kiops_server_stop(ctx) -> None:
+    _check(ctx, lib().kiops_server_stop(ctx), "kiops_server_stop")
+
+
 def kiops_expm(ctx, n, a_ptr, f_ptr) -> None:
     _check(ctx, lib().kiops_expm(ctx, n, a_ptr, f_ptr), "kiops_expm")
 
@@ -382,6 +428,42 @@ class Solver:
             reqs.append(kiops_request(op.handle, tau, p, C.cast(arr, C.POINTER(C.c_void_p)), tol, m_init, m_o,
                                       self._prec(precision), w.data_ptr()))
         return kiops_solve_batch(self.ctx, reqs)
+
+    # ---- serving (continuous batching)
+    def server_start(self, hbm_budget_bytes: float | None = None, **kw) -> None:
+        cfg = kiops_server_config_default()
+        if hbm_budget_bytes is not None:
+            cfg.hbm_budget_bytes = float(hbm_budget_bytes)
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        kiops_server_start(self.ctx, cfg)
+        self._served = {}
+
+    def submit(self, op: Operator, tau: float, b, tol: float, m_init: int = 10, m_o: int = 2, precision="fp64",
+               w=None):
+        """Queue one request; returns (ticket, w).  b and w stay borrowed until poll reports done."""
+        import torch
+        p = b.shape[0] - 1
+        if w is None:
+            w = torch.empty(b.shape[1], dtype=torch.float64, device=b.device)
+        arr = _ptr_array([b[k].data_ptr() for k in range(p + 1)])
+        req = kiops_request(op.handle, tau, p, C.cast(arr, C.POINTER(C.c_void_p)), tol, m_init, m_o,
+                            self._prec(precision), w.data_ptr())
+        t = kiops_submit(self.ctx, req)
+        self._served[t] = (op, b, w)
+        return t, w
+
+    def poll(self, ticket: int, timeout_s: float = 0.0):
+        done, st = kiops_poll(self.ctx, ticket, timeout_s)
+        if done:
+            self._served.pop(ticket, None)
+        return done, st
+
+    def server_info(self) -> dict:
+        return kiops_server_info(self.ctx)
+
+    def server_stop(self) -> None:
+        kiops_server_stop(self.ctx)
 
     def expm(self, a):
         import torch

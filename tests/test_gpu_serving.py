@@ -1,0 +1,78 @@
+"""Continuous-batching server on the GPU: results alone and in the mix, admission under a budget, a
+served stream checked against the oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1804_05126_gb300 import kiops, serve, workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1804_05126_gb300 import build
+    build.build()
+    s = kiops.Solver(device=0)
+    s.server_start(hbm_budget_bytes=4e9, small_team_blocks=8, large_teams=1, large_team_blocks=64,
+                   large_work_threshold=5e7)
+    yield s
+    s.server_stop()
+    s.close()
+
+
+def small_stream(count=24, seed=1005, n_range=(16, 32), rate=2000.0, tau_max=0.02):
+    """The serving workload's request mix on small grids (tau capped so that the oracle stays fast)."""
+    out = W.request_stream(count, seed=seed, rate=rate, n_range=n_range)
+    for _, P in out:
+        P.tau = min(P.tau, tau_max)
+    return out
+
+
+def test_served_stream_matches_oracle(solver):
+    stream = small_stream(count=12)
+    res = serve.run_stream(solver, stream)
+    for (t, P), w, st in zip(stream, res["w"], res["stats"]):
+        ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+        err = np.linalg.norm(w.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert st["status"] == 0
+        assert err <= 10 * P.tol, (P.name, P.precision, err)
+    assert res["p99_ms"] >= res["p50_ms"] > 0
+
+
+def test_result_alone_equals_result_in_the_mix(solver):
+    stream = small_stream(count=30, seed=77)
+    mix = serve.run_stream(solver, stream)
+    for k in (0, 11, 29):
+        t, P = stream[k]
+        alone = serve.run_stream(solver, [(0.0, P)])
+        assert torch.equal(alone["w"][0], mix["w"][k]), k
+
+
+def test_admission_waits_for_budget():
+    """A budget that holds about one request at a time still completes a burst (requests queue on the
+    host and are admitted as workspaces free up)."""
+    s = kiops.Solver(device=0)
+    stream = small_stream(count=6, seed=5, n_range=(28, 28))
+    P0 = stream[0][1]
+    need = (128 + 1) * (P0.n + 64) * 8 * 1.5
+    s.server_start(hbm_budget_bytes=need, small_team_blocks=8, large_teams=0)
+    res = serve.run_stream(s, [(0.0, P) for _, P in stream])
+    for (_, P), w in zip(stream, res["w"]):
+        ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+        assert np.linalg.norm(w.cpu().numpy() - ref) <= 10 * P.tol * np.linalg.norm(ref)
+    s.server_stop()
+    s.close()
+
+
+def test_large_class_request(solver):
+    """A request above the large-work threshold runs on the large team."""
+    P = W.request_stream(1, seed=9, n_range=(64, 64))[0][1]
+    P.tau = 0.01
+    res = serve.run_stream(solver, [(0.0, P)])
+    ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+    assert np.linalg.norm(res["w"][0].cpu().numpy() - ref) <= 10 * P.tol * np.linalg.norm(ref)
