@@ -139,6 +139,20 @@ def dram_traffic():
     return rec["dram_bytes_per_launch"]
 
 
+def max_over_ranks(local_s: float, dist=None, device=None) -> float:
+    """Slowest rank's time (replicas: value = all ranks' solves / this time)."""
+    if dist is None:
+        return local_s
+    import torch
+    t = torch.tensor([local_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps: int, world: int, t_max: float) -> float:
+    return steps * world / t_max
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -188,6 +202,75 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ growth patterns (extra keys)
+def measure_patterns(dev):
+    """Batched, mixed-precision and served forms against plain single-instance FP64 on the same GPU."""
+    import torch
+
+    from paper_1804_05126_gb300 import kiops, serve
+
+    out = {}
+    s = kiops.Solver(device=dev.index)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, r
+
+    # batched: 256 independent 3D diffusion-reaction instances (n in 10..40, FP64, tol 1e-8)
+    probs = W.batch_3d()
+    items = []
+    for P in probs:
+        op = s.operator(P.op)
+        b = torch.as_tensor(P.b, device=dev)
+        items.append((op, P.tau, b, P.tol, P.m_init, P.m_o, "fp64", torch.empty(P.n, dtype=torch.float64, device=dev)))
+    s.solve_batch(items, team_blocks=0)
+    t_batch, st = timed(lambda: s.solve_batch(items, team_blocks=0))
+    wb = [it[7].clone() for it in items]
+    t_seq, _ = timed(lambda: [s.solve(it[0], it[1], it[2], it[3], w=it[7]) for it in items])
+    diff = max(float((wb[i] - items[i][7]).norm() / items[i][7].norm()) for i in range(len(items)))
+    out["batched_3d_256"] = {"solves_per_s": len(items) / t_batch, "ms": 1e3 * t_batch,
+                             "team_blocks": st[0]["grid_blocks"],
+                             "single_instance_fp64_solves_per_s": len(items) / t_seq,
+                             "speedup_vs_single_instance": t_seq / t_batch, "max_rel_diff_vs_single": diff}
+    del items
+    # mixed precision: 1024^2 Gray-Scott, FP32 basis vs FP64
+    P = W.problem_gray_scott()
+    op = s.operator(P.op)
+    b = torch.as_tensor(P.b, device=dev)
+    res = {}
+    for prec in ("fp32_basis", "fp64"):
+        s.solve(op, P.tau, b, P.tol, precision=prec)
+        dt, (w, st) = timed(lambda: s.solve(op, P.tau, b, P.tol, precision=prec))
+        res[prec] = (dt, w.clone(), st)
+    rel = float((res["fp32_basis"][1] - res["fp64"][1]).norm() / res["fp64"][1].norm())
+    out["mixed_precision_gray_scott_1024"] = {
+        "fp32_basis_ms": 1e3 * res["fp32_basis"][0], "fp64_ms": 1e3 * res["fp64"][0],
+        "speedup": res["fp64"][0] / res["fp32_basis"][0], "rel_err_vs_fp64": rel, "tol": P.tol,
+        "matvecs_fp32": res["fp32_basis"][2]["matvecs"], "matvecs_fp64": res["fp64"][2]["matvecs"]}
+    s.close()
+    # served: Poisson stream (2000/s) of the 3D ADR request mix with n in 16..64
+    srv = kiops.Solver(device=dev.index)
+    srv.server_start(hbm_budget_bytes=120e9)
+    stream = W.request_stream(200, seed=1005, n_range=(16, 64))
+    r = serve.run_stream(srv, stream)
+    srv.server_stop()
+    seq = kiops.Solver(device=dev.index)
+    ops = [seq.operator(P.op) for _, P in stream]
+    bs = [torch.as_tensor(P.b, device=dev) for _, P in stream]
+    t_seq, _ = timed(lambda: [seq.solve(ops[i], P.tau, bs[i], P.tol, precision="fp64") for i, (_, P) in enumerate(stream)])
+    out["served_3d_adr_poisson"] = {
+        "requests": len(stream), "arrival_rate_per_s": 2000.0, "n_range": [16, 64],
+        "solves_per_s": r["solves_per_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+        "single_instance_fp64_solves_per_s": len(stream) / t_seq,
+        "note": "half the requests FP32 basis (tol 1e-6), half FP64 (tol 1e-10); latency = completion - arrival"}
+    srv.close()
+    seq.close()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -235,13 +318,9 @@ def run_gpu(args):
             dist.barrier()
         times_ms = [a.elapsed_time(bb) for a, bb in ev]
     total_s = sum(times_ms) / 1e3
-    t_max = total_s
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_s, dist, dev)
     solves_total = args.steps * world
-    value = solves_total / t_max
+    value = replica_value(args.steps, world, t_max)
 
     # end to end through the host-buffer entry point (pinned host inputs, copies inside the timed region)
     bh = torch.as_tensor(P.b).pin_memory().numpy()
@@ -251,11 +330,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         solver.solve_host(op, P.tau, bh, P.tol, w=wh)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e = {"value": solves_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(bh.nbytes),
            "d2h_bytes_per_step": int(wh.nbytes)}
 
@@ -287,6 +362,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "engine": {"blocks": st["grid_blocks"], "kind": "grid (persistent cooperative)"},
     }
+    if world == 1 and not args.no_patterns:
+        out["patterns"] = measure_patterns(dev)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(P)
     print(json.dumps(out), flush=True)
@@ -301,6 +378,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the batched / mixed / served measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps > 10 and "--steps" not in " ".join(sys.argv):
