@@ -82,6 +82,10 @@ def _load():
                                          C.POINTER(_Opts), C.c_void_p, C.c_void_p, C.POINTER(_Trace), C.c_int64,
                                          C.POINTER(C.c_int64)]
             lib.oracle_kiops.restype = C.c_int
+            lib.oracle_kiops_task1.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double,
+                                               C.c_int, C.POINTER(_Opts), C.c_void_p, C.c_void_p, C.POINTER(_Trace),
+                                               C.c_int64, C.POINTER(C.c_int64)]
+            lib.oracle_kiops_task1.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -205,3 +209,26 @@ def kiops(op: dict, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_m
                   accepted=bool(t.accepted), breakdown=bool(t.breakdown), m_new=t.m_new, tau_new=t.tau_new)
              for t in tr[: tl.value]]
     return w, stats, trace
+
+
+def kiops_task1(op: dict, T, b: np.ndarray, tol: float, m_init: int = 10, m_min: int = 10, m_max: int = 128,
+                m_o: int = 2, normalize: bool = True, breakdown_tol: float = 1e-12, max_substeps: int = 10**6,
+                max_iterations: int = 10**7):
+    """Task I (Algorithm 1 with Algorithm 3's intermediate outputs): returns (W, stats) with W[l] =
+    (1/T[l])^p * (top N entries of e^{T[l] A~} v), T increasing and positive."""
+    lib = _load()
+    s, keep = _make_op(op)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    p = b.shape[0] - 1
+    n = b.shape[1]
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    o = _Opts(m_min, m_max, m_o, int(normalize), breakdown_tol, max_substeps, max_iterations, 0)
+    W = np.empty((len(T), n))
+    st = np.zeros(5, dtype=np.int64)
+    tr = (_Trace * 1)()
+    tl = C.c_int64(0)
+    rc = lib.oracle_kiops_task1(C.byref(s), T.ctypes.data, len(T), p, b.ctypes.data, float(tol), int(m_init),
+                                C.byref(o), W.ctypes.data, st.ctypes.data, tr, 0, C.byref(tl))
+    stats = dict(substeps=int(st[0]), rejected=int(st[1]), matvecs=int(st[2]), m_last=int(st[3]),
+                 iterations=int(st[4]), status=int(rc))
+    return W, stats

@@ -30,6 +30,7 @@
  *       rejected one; a new substep starts with tau = min(tau, T_end - T_now).
  *   R6  happy breakdown when ||x|| <= breakdown_tol * ||A~ v_j|| (Algorithm 2 line 12).
  *   R7  ||B||_1 is the matrix 1-norm (largest column sum); nu = mu = 1 when it is 0 or p = 0.
+ *   R8  Task I: the intermediate outputs of Algorithm 3 line 15 use beta (line 14) as their scale.
  */
 #include <math.h>
 #include <stdint.h>
@@ -326,26 +327,33 @@ int oracle_iop(const oracle_op* A, int p, const double* b_flat, const double* v_
 }
 
 /* ------------------------------------------------------------------------------------------------
- * Algorithm 1 (Task II) with Algorithms 2-4.
- *   T_end     the single output time (tau of eq 12)
- *   b_flat    (p+1) vectors b_0..b_p of length N, contiguous, natural order
- *   w_out     N entries: sum_k T_end^k phi_k(T_end A) b_k
- *   stats     [substeps, rejected, matvecs, m_last, iterations]
+ * Algorithm 1 with Algorithms 2-4.
+ *   T, n_steps  output times T(1) < ... < T(end) (Task II: one time)
+ *   task1       Task I: outputs at every T(l), scaled by (1/T(l))^p (Algorithm 1 lines 31-35)
+ *   b_flat      (p+1) vectors b_0..b_p of length N, contiguous, natural order
+ *   W           n_steps columns of N entries (column l: the result at T(l))
+ *   stats       [substeps, rejected, matvecs, m_last, iterations]
+ * Reading R8: the intermediate outputs of Algorithm 3 line 15 are scaled by beta, the norm of the
+ * substep's start vector (line 14); the printed ||w(:,l)|| would read a column line 15 has overwritten.
  * ---------------------------------------------------------------------------------------------- */
-int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, double tol, int m_init,
-                 const oracle_opts* o, double* w_out, int64_t* stats, oracle_trace* trace,
-                 int64_t trace_cap, int64_t* trace_len) {
+static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task1, int p, const double* b_flat,
+                      double tol, int m_init, const oracle_opts* o, double* W, int64_t* stats,
+                      oracle_trace* trace, int64_t trace_cap, int64_t* trace_len) {
+  const double T_end = T[n_steps - 1];
+  int ell = 0;  /* current output column (Algorithm 1 line 6) */
   const double delta = 1.4, gamma = 0.9, gamma_max = 0.6; /* section 3.5, Algorithm 4 line 2 */
   int64_t N = A->n, M = N + p;
   int m_min = o->m_min, m_max = o->m_max, m_o = o->m_o;
   const double* b[8];
   if (p < 0 || p > 7 || N < 1 || !(tol > 0) || m_init < 1 || m_min < 1 || m_max < m_min || m_o < 1 ||
-      T_end < 0 || !isfinite(T_end))
+      T_end < 0 || !isfinite(T_end) || n_steps < 1)
     return ORACLE_EINVAL;
+  for (int l = 0; l + 1 < n_steps; ++l)
+    if (!(T[l] > 0.0) || !(T[l] < T[l + 1])) return ORACLE_EINVAL;
   for (int k = 0; k <= p; ++k) b[k] = b_flat + (size_t)k * N;
   if (trace_len) *trace_len = 0;
   for (int k = 0; k < 5; ++k) stats[k] = 0;
-  memcpy(w_out, b[0], (size_t)N * sizeof(double)); /* Algorithm 1 line 8 */
+  memcpy(W, b[0], (size_t)N * sizeof(double)); /* Algorithm 1 line 8 */
   if (T_end == 0.0) { stats[3] = m_init; return ORACLE_OK; }
 
   /* section 3.7, eqs 48-49 */
@@ -384,7 +392,7 @@ int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, 
     if (iters >= o->max_iterations || substeps >= o->max_substeps) { rc = ORACLE_ENOTCONV; break; }
     if (j == 0) { /* lines 10-15 */
       if (tau > T_end - t_now) tau = T_end - t_now; /* R5 */
-      memcpy(V, w_out, (size_t)N * sizeof(double));
+      memcpy(V, W + (size_t)ell * N, (size_t)N * sizeof(double));
       for (int t = 0; t < p; ++t) { /* line 13 (corrigendum), eq 47, times mu */
         int e = p - 1 - t;
         double v = 1.0;
@@ -393,7 +401,7 @@ int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, 
       }
       beta = sqrt(dot(V, V, M));
       if (beta == 0.0) { /* v = 0: the exponential maps it to 0 */
-        memset(w_out, 0, (size_t)N * sizeof(double));
+        memset(W + (size_t)ell * N, 0, (size_t)(n_steps - ell) * N * sizeof(double));
         break;
       }
       double inv = 1.0 / beta;
@@ -475,11 +483,39 @@ int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, 
     }
     iters++;
 
-    if (accepted) { /* lines 22-25, Algorithm 3 (Task II): w = beta V(1:N,1:j) F(1:j,1) */
+    if (accepted) { /* lines 22-25, Algorithm 3 */
+      if (task1) { /* Algorithm 3 lines 4-19: outputs strictly inside this substep */
+        int n_tau = 0;
+        for (int k = ell; k < n_steps; ++k)
+          if (fabs(T[k]) < fabs(t_now + tau)) n_tau++;
+        if (n_tau > 0) {
+          memcpy(W + (size_t)(ell + n_tau) * N, W + (size_t)ell * N, (size_t)N * sizeof(double)); /* line 11 */
+          double* h2 = (double*)malloc((size_t)j * j * sizeof(double));
+          double* F2 = (double*)malloc((size_t)j * j * sizeof(double));
+          if (!h2 || !F2) { free(h2); free(F2); rc = ORACLE_ENOMEM; break; }
+          for (int k = 0; k < n_tau; ++k) {
+            const double tt = T[ell + k] - t_now; /* line 13 */
+            for (int r = 0; r < j; ++r)
+              for (int cc = 0; cc < j; ++cc) h2[r * j + cc] = tt * h[r * ldh + cc];
+            if (oracle_expm(j, h2, F2) != ORACLE_OK) { rc = ORACLE_ENOTCONV; break; } /* line 14 */
+            double* wk = W + (size_t)(ell + k) * N;
+            for (int64_t r = 0; r < N; ++r) { /* line 15 */
+              double sacc = 0.0;
+              for (int cc = 0; cc < j; ++cc) sacc += V[(size_t)cc * M + r] * F2[cc * j + 0];
+              wk[r] = beta * sacc;
+            }
+          }
+          free(h2);
+          free(F2);
+          if (rc != ORACLE_OK) break;
+          ell += n_tau; /* line 17 */
+        }
+      }
+      double* wl = W + (size_t)ell * N; /* the last line of Algorithm 3: w = beta V(1:N,1:j) F(1:j,1) */
       for (int64_t r = 0; r < N; ++r) {
         double s = 0.0;
         for (int c = 0; c < j; ++c) s += V[(size_t)c * M + r] * F[c * n + 0];
-        w_out[r] = beta * s;
+        wl[r] = beta * s;
       }
       if (tau >= T_end - t_now || t_next >= T_end) t_now = T_end;
       else t_now = t_next;
@@ -492,7 +528,27 @@ int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, 
     tau = tau_new;
     m = m_new;
   }
+  if (task1 && rc == ORACLE_OK) /* Algorithm 1 lines 31-35 */
+    for (int l = 0; l < n_steps; ++l) {
+      double sc = 1.0;
+      for (int k = 0; k < p; ++k) sc *= 1.0 / T[l];
+      for (int64_t r = 0; r < N; ++r) W[(size_t)l * N + r] *= sc;
+    }
   stats[0] = substeps; stats[1] = rejected; stats[2] = matvecs; stats[3] = m; stats[4] = iters;
   free(V); free(h); free(x); free(ht); free(F);
   return rc;
+}
+
+/* Task II (one output time T_end): sum_k T_end^k phi_k(T_end A) b_k. */
+int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, double tol, int m_init,
+                 const oracle_opts* o, double* w_out, int64_t* stats, oracle_trace* trace,
+                 int64_t trace_cap, int64_t* trace_len) {
+  return kiops_core(A, &T_end, 1, 0, p, b_flat, tol, m_init, o, w_out, stats, trace, trace_cap, trace_len);
+}
+
+/* Task I: W(:, l) = (1/T(l))^p e^{T(l) A~} v (top N entries), l = 1..n_steps (Algorithm 1 lines 31-36). */
+int oracle_kiops_task1(const oracle_op* A, const double* T, int n_steps, int p, const double* b_flat, double tol,
+                       int m_init, const oracle_opts* o, double* W, int64_t* stats, oracle_trace* trace,
+                       int64_t trace_cap, int64_t* trace_len) {
+  return kiops_core(A, T, n_steps, 1, p, b_flat, tol, m_init, o, W, stats, trace, trace_cap, trace_len);
 }

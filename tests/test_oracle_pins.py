@@ -311,3 +311,40 @@ def test_matvec_count_equals_basis_growth():
     for t in tr:
         last_j[t["substep"]] = t["j"]
     assert st["matvecs"] == sum(last_j.values())
+
+
+# ---------------------------------------------------------------- Task I (Algorithm 1 lines 31-35, Algorithm 3)
+def test_task1_single_phi_at_several_times_vs_dst():
+    """Task I with b = [0, 0, b_2]: W[l] = phi_2(T_l A) b_2, checked against the DST-I closed form."""
+    n, tol = 120, 1e-10
+    op = W.laplacian_1d_csr(n)
+    rng = np.random.default_rng(31)
+    b = np.zeros((3, n))
+    b[2] = rng.standard_normal(n)
+    T = [2e-4, 5e-4, 1e-3, 2.5e-3]
+    Wt, st = oracle.kiops_task1(op, T, b, tol, m_max=30, m_min=5)
+    assert st["status"] == 0 and st["substeps"] > 1
+    for l, t in enumerate(T):
+        want = exact_dst_1d(n, 1.0, b, t) / t**2
+        assert err_ok(Wt[l], want, tol / t**2), l
+
+
+def test_task1_general_combination_vs_dense_expm():
+    """W[l] = T_l^{-p} sum_k T_l^k phi_k(T_l A) b_k = T_l^{-p} (top of e^{T_l A~} v)."""
+    rng = np.random.default_rng(32)
+    n, p, tol = 40, 3, 1e-10
+    a = -np.diag(rng.uniform(0, 300, n)) + 3.0 * rng.standard_normal((n, n))
+    b = rng.standard_normal((p + 1, n))
+    T = [0.003, 0.007, 0.0071, 0.02]
+    Wt, st = oracle.kiops_task1({"kind": "dense", "n": n, "a": a}, T, b, tol, m_max=16, m_min=5)
+    assert st["status"] == 0  # one substep: the first three outputs come from Algorithm 3 lines 4-18
+    for l, t in enumerate(T):
+        assert err_ok(Wt[l], exact_dense(a, b, t) / t**p, tol / t**p), l
+
+
+def test_task1_last_time_equals_task2_scaled():
+    P = W.problem_adr2d(n=14, seed=33, p=2)
+    T = [0.25 * P.tau, P.tau]
+    Wt, _ = oracle.kiops_task1(P.op, T, P.b, P.tol)
+    w2, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+    assert rel(Wt[-1], w2 / P.tau**2) < 1e-12
