@@ -37,6 +37,7 @@ extern "C" {
 
 #define KIOPS_MAX_P 16   /* largest p (number of phi terms beyond phi_0) */
 #define KIOPS_MAX_M 256  /* largest m_max (Krylov dimension cap) */
+#define KIOPS_MAX_TIMES 32  /* largest number of Task I output times */
 
 typedef enum {
   KIOPS_OK = 0,
@@ -195,6 +196,17 @@ kiops_status kiops_solve_traced(kiops_ctx* ctx, const kiops_op* A, double tau, i
                                 double tol, int m_init, int m_o, kiops_precision prec, double* w,
                                 kiops_stats* stats, kiops_trace_rec* trace, int64_t trace_cap,
                                 int64_t* trace_len);
+
+/* Task I (Algorithm 1 lines 31-36 with Algorithm 3): one adaptive run to T[n_times-1] that also returns
+ *   w[l] = (1/T[l])^p * sum_k T[l]^k phi_k(T[l] A) b_k,   l = 0..n_times-1,
+ * i.e. phi_p(T[l] A) b_p for every l when b_0..b_{p-1} are zero (the use the paper makes of it in
+ * exponential integrators).  T: host array of increasing positive times (n_times <= KIOPS_MAX_TIMES);
+ * w: host array of n_times DEVICE output pointers (N FP64 values each).  Outputs strictly inside an
+ * accepted substep come from exp((T[l] - T_now) H_j) on that substep's basis (Algorithm 3 line 14);
+ * the substep sizes are not shortened to hit them. */
+kiops_status kiops_solve_task1(kiops_ctx* ctx, const kiops_op* A, const double* T, int n_times, int p,
+                               const double* const* b, double tol, int m_init, int m_o, kiops_precision prec,
+                               double* const* w, kiops_stats* stats);
 
 /* Same as kiops_solve but b (p+1 pointers to N values each) and w are HOST buffers; the host-device
  * copies happen inside the call (pinned staging owned by the context). */

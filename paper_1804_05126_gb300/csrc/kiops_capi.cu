@@ -323,7 +323,8 @@ void fill_stats(kiops_stats* st, const int64_t* s, const double* sd, int engine,
 // One solve on the grid engine (or a single-block CTA launch).
 kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b, double tol,
                         int m_init, int m_o, kiops_precision prec, double* w, kiops_stats* stats,
-                        kiops_trace_rec* trace, int64_t trace_cap, int64_t* trace_len) {
+                        kiops_trace_rec* trace, int64_t trace_cap, int64_t* trace_len, const double* times = nullptr,
+                        int n_times = 0, double* const* wout = nullptr) {
   if (!ctx) return KIOPS_EINVAL;
   if (trace_len) *trace_len = 0;
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -354,6 +355,13 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   Prepared P;
   st = prepare(ctx, A, tau, p, b, tol, m_init, m_o, prec, w, blocks, trace ? trace_cap : 0, P);
   if (st) return st;
+  if (n_times > 0) {  // Task I: the running state lives in the last output
+    P.args.n_times = n_times;
+    for (int l = 0; l < n_times; ++l) {
+      P.args.times[l] = times[l];
+      P.args.wout[l] = wout[l];
+    }
+  }
   st = ensure_workspace(ctx, P.L.total);
   if (st) return st;
   bind(P, (char*)ctx->ws);
@@ -623,6 +631,21 @@ kiops_status kiops_solve_traced(kiops_ctx* ctx, const kiops_op* A, double tau, i
                                 int64_t* trace_len) {
   if (!trace || trace_cap < 1) return fail(ctx, KIOPS_EINVAL, "trace buffer required");
   return run_single(ctx, A, tau, p, b, tol, m_init, m_o, prec, w, stats, trace, trace_cap, trace_len);
+}
+
+kiops_status kiops_solve_task1(kiops_ctx* ctx, const kiops_op* A, const double* T, int n_times, int p,
+                               const double* const* b, double tol, int m_init, int m_o, kiops_precision prec,
+                               double* const* w, kiops_stats* stats) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (!T || !w || n_times < 1 || n_times > KIOPS_MAX_TIMES)
+    return fail(ctx, KIOPS_EINVAL, "Task I needs 1..%d output times and as many outputs", KIOPS_MAX_TIMES);
+  for (int l = 0; l < n_times; ++l) {
+    if (!w[l]) return fail(ctx, KIOPS_EINVAL, "w[%d] is NULL", l);
+    if (!(T[l] > 0.0) || !std::isfinite(T[l]) || (l > 0 && !(T[l] > T[l - 1])))
+      return fail(ctx, KIOPS_EINVAL, "output times must be positive and increasing");
+  }
+  return run_single(ctx, A, T[n_times - 1], p, b, tol, m_init, m_o, prec, w[n_times - 1], stats, nullptr, 0, nullptr,
+                    T, n_times, w);
 }
 
 kiops_status kiops_solve_host(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b_host,

@@ -33,6 +33,7 @@ constexpr int kMaxRed = 2 * kMaxWin + 1;   // largest reduction width
 constexpr int kTile = 8;                   // dense matmul tile edge
 constexpr int kMaxDeg = 8;                 // entries of the Taylor degree table
 constexpr int kGramRing = 8;               // Gram rows kept in shared memory (m_o <= kGramRing)
+constexpr int kMaxTimes = 32;              // Task I: largest number of output times
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ENOTCONV = 3, ST_ETIMEOUT = 4, ST_ECUDA = 5 };
 enum : int { OP_CSR = 0, OP_ST2D = 1, OP_ST3D = 2 };
@@ -102,6 +103,9 @@ struct SolveArgs {
   float* bf;                 // FP32 basis: B columns as floats, column t = b_{p-t} at bf + t*ldv
   float* df;                 // FP32 basis: pointwise coupling fields as floats, (s*ns + q)*npts (stencils)
   int prec;                  // 0 FP64 basis, 1 FP32 basis (runtime dispatch in the server kernel)
+  int n_times;               // Task I: output times (0 = Task II, the single result in w)
+  double times[kMaxTimes];   // Task I: T(1) < ... < T(end) = T_end
+  double* wout[kMaxTimes];   // Task I: outputs (wout[n_times-1] == w holds the running state)
   unsigned long long ticket; // serving: written to the completion word when the solve is done
   int expm_only;             // 1: compute exp(a) of an n x n matrix only (kiops_expm)
   int expm_n;
@@ -203,6 +207,9 @@ struct Ctl {
   double fin_rs;
   int fin_pending, fin_i0, fin_nwin;
   float yhi[kMaxN], ylo[kMaxN];  // FP32 basis: update weights split into float hi + lo
+  double yint[kMaxN];           // Task I: first column of exp(tau~ H_j) for an intermediate output
+  double t_sub, tau_sub;        // start time and step of the substep that was just accepted
+  int ell;                      // Task I: next output index (Algorithm 1 line 6)
   double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
   double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
   double hc[kMaxP + 1];         // Horner epilogue coefficients
@@ -529,7 +536,7 @@ __device__ __forceinline__ Band band_product(Band a, Band b, int n) {
 
 // C = A B (+ epilogue) for n x n row-major matrices; tiles of kTile x kTile distributed over ranks.
 // Tiles outside the band of C are written as zeros without arithmetic.
-__device__ inline void mm_team(const double* A, Band bA, const double* B, Band bB, double* C, int n, int rank, int size,
+static __device__ __noinline__ void mm_team(const double* A, Band bA, const double* B, Band bB, double* C, int n, int rank, int size,
                         const Ctl& c, const MmEpi& epi, double* sA, double* sB) {
   const Band bC = band_product(bA, bB, n);
   const int nt = (n + kTile - 1) / kTile;
@@ -734,9 +741,12 @@ __global__ void __launch_bounds__(kThreads) kiops_solve_kernel(const SolveArgs* 
 // Builds exp(tau H~) for the current j; leaves F(:,1) in a.fvec[0..j) and F(j, j+1) in a.fvec[m_max+1].
 // With a.expm_only, exponentiates a.expm_in (n x n) into a.expm_out instead.
 template <class Team>
-__device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, double* smem_dyn) {
+__device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, double* smem_dyn,
+                                        bool aug = true, double scale = 0.0) {
+  // aug: exp(tau H~) of size j+1 (eqs 37-38), F(:,1) and F(j, j+1) into fvec.  !aug: exp(scale H_j) of
+  // size j (Algorithm 3 line 14), its first column into fvec.
   const bool prof_on = a.prof != nullptr && team.rank == 0;
-  const int n = a.expm_only ? a.expm_n : c.j + 1;
+  const int n = a.expm_only ? a.expm_n : (aug ? c.j + 1 : c.j);
   const size_t ldm = (size_t)(a.m_max + 1) * (a.m_max + 1);
   double* sA = smem_dyn;
   double* sB = smem_dyn + kTile * kMaxN;
@@ -746,12 +756,12 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     if (a.expm_only) {
       nrm = 0.0;  // computed below from the input
     } else {
-      nrm = 1.0;  // column j+1 of H~ is e_1
+      nrm = aug ? 1.0 : 0.0;  // column j+1 of H~ is e_1
       for (int k = 1; k <= c.j; ++k) {
         double col = c.colabs[k] + (k < c.j ? c.sub[k] : 0.0);
         nrm = col > nrm ? col : nrm;
       }
-      nrm *= c.tau;
+      nrm *= aug ? c.tau : scale;
     }
     c.red[0] = nrm;
   }
@@ -782,7 +792,7 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     c.deg_i = best_i;
     c.s_sq = best_s;
     c.n_exp = n;
-    c.xscale = ldexp(a.expm_only ? 1.0 : c.tau, -best_s);
+    c.xscale = ldexp(a.expm_only ? 1.0 : (aug ? c.tau : scale), -best_s);
   }
   __syncthreads();
   const int r = a.tt.r[c.deg_i], q = a.tt.q[c.deg_i], deg = a.tt.deg[c.deg_i];
@@ -795,9 +805,9 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
     double v = 0.0;
     if (a.expm_only) {
       v = a.expm_in[e];
-    } else if (k == n - 1) {
+    } else if (aug && k == n - 1) {
       v = (i == 0) ? 1.0 : 0.0;
-    } else if (i < n - 1) {
+    } else if (!aug || i < n - 1) {
       // H(i+1, k+1) is stored if it is in the window of column k+1 or is the sub-diagonal entry
       const int col = k + 1, row = i + 1;
       const int lo = col - a.m_o + 1 < 1 ? 1 : col - a.m_o + 1;
@@ -864,7 +874,8 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
   // last squaring (or none): only F(:,1) and F(j, j+1) are needed
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int jj = c.j;  // 1-based j: F(j, j+1) is (jj-1, jj) 0-based
-  for (int row = team.rank * kWarps + warp; row <= n; row += team.size * kWarps) {
+  const int nrows = aug ? n : n - 1;  // F(j, j+1) only for H~
+  for (int row = team.rank * kWarps + warp; row <= nrows; row += team.size * kWarps) {
     // rows 0..n-1: F(row, 0); row n: F(jj-1, jj)
     const int ri = row < n ? row : jj - 1;
     const int ck = row < n ? 0 : jj;
@@ -880,6 +891,39 @@ __device__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, 
   const bool ok = team.sync(&c.sync_ok);
   KIOPS_TICK(8);
   return ok;
+}
+
+// out[r] = beta * sum_k V(r, k) y_k for this rank's rows (Algorithm 3, eq 33).  FP32 basis: y is split into
+// float hi + lo, v*yhi is formed exactly (TwoProduct) and the sum is accumulated with TwoSum.
+template <typename T>
+__device__ void combine_rows(Ctl& c, const T* V, size_t ldv, int j, const double* y, double beta, double* out,
+                             int64_t r0, int64_t r1) {
+  const int tid = threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    for (int k = tid; k < j; k += kThreads) {
+      const float hi = (float)y[k];
+      c.yhi[k] = hi;
+      c.ylo[k] = (float)(y[k] - (double)hi);
+    }
+    __syncthreads();
+    for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+      DotAcc<float> s2;
+      s2.hi[0] = 0.0f;
+      s2.lo[0] = 0.0f;
+      for (int k = 0; k < j; ++k) {
+        const float v = (float)V[(size_t)k * ldv + r];
+        s2.add(0, v, c.yhi[k]);
+        s2.lo[0] = __fmaf_rn(v, c.ylo[k], s2.lo[0]);
+      }
+      out[r] = beta * ((double)s2.hi[0] + (double)s2.lo[0]);
+    }
+  } else {
+    for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+      double s = 0.0;
+      for (int k = 0; k < j; ++k) s = fma((double)V[(size_t)k * ldv + r], y[k], s);
+      out[r] = beta * s;
+    }
+  }
 }
 
 template <typename T, int KIND, class Team>
@@ -906,6 +950,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     c.eps_last = 0.0;
     for (int k = 0; k < 16; ++k) c.prof[k] = 0;
     c.prof_last = clock64();
+    c.ell = 0;
   }
   __syncthreads();
 
@@ -1392,6 +1437,8 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       }
       c.iters += 1;
       c.accepted = accepted;
+      c.t_sub = c.t_now;
+      c.tau_sub = c.tau;
       if (accepted) {
         if (c.tau >= a.T_end - c.t_now || t_next >= a.T_end) c.t_now = a.T_end;
         else c.t_now = t_next;
@@ -1413,40 +1460,33 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     KIOPS_TICK(9);
     if (c.done) break;
     if (c.accepted) {
-      // ---- Algorithm 3 (Task II line): w = beta V(1:N, 1:j) F(1:j, 1)
+      // ---- Algorithm 3: w = beta V(1:N, 1:j) F(1:j, 1), after the Task I outputs inside the substep
       const int j = c.j;
       for (int k = tid; k < j; k += kThreads) c.hcoef[k] = a.fvec[k];
       __syncthreads();
-      const double beta = c.hc[0];
-      if constexpr (sizeof(T) == 4) {
-        // y = yhi + ylo in floats; v*yhi exactly (TwoProduct), v*ylo plainly, TwoSum accumulation
-        for (int k = tid; k < j; k += kThreads) {
-          const float hi = (float)c.hcoef[k];
-          c.yhi[k] = hi;
-          c.ylo[k] = (float)(c.hcoef[k] - (double)hi);
-        }
-        __syncthreads();
-        for (int64_t r = r0 + tid; r < r1; r += kThreads) {
-          DotAcc<float> s2;
-          s2.hi[0] = 0.0f;
-          s2.lo[0] = 0.0f;
-          for (int k = 0; k < j; ++k) {
-            const float v = (float)V[(size_t)k * ldv + r];
-            s2.add(0, v, c.yhi[k]);
-            s2.lo[0] = __fmaf_rn(v, c.ylo[k], s2.lo[0]);
-          }
-          a.w[r] = beta * ((double)s2.hi[0] + (double)s2.lo[0]);
-        }
-      } else {
-        for (int64_t r = r0 + tid; r < r1; r += kThreads) {
-          double s = 0.0;
-          for (int k = 0; k < j; ++k) s = fma((double)V[(size_t)k * ldv + r], c.hcoef[k], s);
-          a.w[r] = beta * s;
+      const double beta = c.beta;
+      if (a.n_times > 0) {  // Task I: outputs T(k) < T_now + tau (Algorithm 3 lines 4-18)
+        while (c.ell < a.n_times - 1 && fabs(a.times[c.ell]) < fabs(c.t_sub + c.tau_sub)) {
+          if (!expm_phase<Team>(a, team, c, parity, smem_dyn, false, a.times[c.ell] - c.t_sub)) goto stop;
+          for (int k = tid; k < j; k += kThreads) c.yint[k] = a.fvec[k];
+          __syncthreads();
+          combine_rows<T>(c, V, ldv, j, c.yint, beta, a.wout[c.ell], r0, r1);
+          __syncthreads();
+          if (tid == 0) c.ell += 1;
+          __syncthreads();
         }
       }
+      combine_rows<T>(c, V, ldv, j, c.hcoef, beta, a.w, r0, r1);
       if (tid == 0) c.j = 0;
       __syncthreads();
       KIOPS_TICK(10);
+    }
+  }
+  if (a.n_times > 0 && c.status == ST_OK) {  // Task I: w(:, l) *= (1/T(l))^p (Algorithm 1 lines 31-35)
+    for (int l = 0; l < a.n_times; ++l) {
+      double sc = 1.0;
+      for (int k = 0; k < p; ++k) sc *= 1.0 / a.times[l];
+      for (int64_t r = r0 + tid; r < r1; r += kThreads) a.wout[l][r] *= sc;
     }
   }
 stop:

@@ -111,6 +111,8 @@ _SIGS = {
     "kiops_server_info": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "kiops_server_stop": ([C.c_void_p], C.c_int),
     "kiops_expm": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "kiops_solve_task1": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                           C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p), C.POINTER(kiops_stats)], C.c_int),
     "kiops_solve_noalloc": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
                              C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
 }
@@ -225,6 +227,14 @@ def kiops_solve_traced(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, prec, w_ptr, t
         r["accepted"] = bool(r["accepted"])
         r["breakdown"] = bool(r["breakdown"])
     return st.as_dict(), recs
+
+
+def kiops_solve_task1(ctx, op, T, p, b_ptrs, tol, m_init, m_o, prec, w_ptrs) -> dict:
+    st = kiops_stats()
+    Ta = (C.c_double * len(T))(*T)
+    _check(ctx, lib().kiops_solve_task1(ctx, op, Ta, len(T), p, _ptr_array(b_ptrs), tol, m_init, m_o, prec,
+                                        _ptr_array(w_ptrs), C.byref(st)), "kiops_solve_task1")
+    return st.as_dict()
 
 
 def kiops_solve_host(ctx, op, tau, p, b_host_ptrs, tol, m_init, m_o, prec, w_host_ptr) -> dict:
@@ -403,6 +413,15 @@ class Solver:
             return w, st, tr
         st = kiops_solve(self.ctx, op.handle, tau, p, ptrs, tol, m_init, m_o, self._prec(precision), w.data_ptr())
         return w, st
+
+    def solve_task1(self, op: Operator, T, b, tol: float, m_init: int = 10, m_o: int = 2, precision="fp64"):
+        """Task I: returns ([w_l], stats) with w_l = (1/T_l)^p sum_k T_l^k phi_k(T_l A) b_k."""
+        import torch
+        p = b.shape[0] - 1
+        ws = [torch.empty(b.shape[1], dtype=torch.float64, device=b.device) for _ in T]
+        st = kiops_solve_task1(self.ctx, op.handle, [float(t) for t in T], p, [b[k].data_ptr() for k in range(p + 1)],
+                               tol, m_init, m_o, self._prec(precision), [w.data_ptr() for w in ws])
+        return ws, st
 
     def solve_host(self, op: Operator, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_o: int = 2,
                    precision="fp64", w: np.ndarray | None = None):

@@ -243,3 +243,22 @@ def test_gray_scott_full_size_fp32_basis_vs_fp64_oracle(solver):
     print(f"gray-scott 1024^2 fp32 basis: rel err vs FP64 oracle {err:.3e}, matvecs {st['matvecs']} "
           f"(oracle {st_ref['matvecs']})")
     assert st["status"] == 0 and err <= 10 * P.tol
+
+
+@pytest.mark.parametrize("make,T,m_max", [
+    (lambda: W.problem_lap1d(n=300, seed=41), [2e-4, 5e-4, 7.5e-4, 1e-3], 30),
+    (lambda: W.problem_adr2d(n=40, seed=42, p=3), [1e-3, 4e-3, 1e-2], 128),
+])
+def test_task1_outputs_match_oracle(make, T, m_max):
+    """Task I: several output times in one run (Algorithm 3's intermediate outputs, 1/T^p scaling)."""
+    P = make()
+    s = kiops.Solver(device=0, m_min=5 if m_max < 128 else 10, m_max=m_max)
+    op = s.operator(P.op)
+    b = torch.as_tensor(P.b, device="cuda:0")
+    ws, st = s.solve_task1(op, T, b, P.tol)
+    torch.cuda.synchronize()
+    s.close()
+    Wr, st_ref = oracle.kiops_task1(P.op, T, P.b, P.tol, m_min=5 if m_max < 128 else 10, m_max=m_max)
+    assert st["status"] == 0 and st["substeps"] == st_ref["substeps"]
+    for l in range(len(T)):
+        assert rel(ws[l].cpu().numpy(), Wr[l]) <= 10 * P.tol, l
