@@ -76,6 +76,11 @@ typedef struct {
   int fuse_stencil;        /* 1 (default): 2D stencils on the grid engine normalise v_{j+1} inside the next
                               step's tiles (one grid barrier per Krylov step); 0: separate normalise pass */
   int batch_team_blocks;   /* kiops_solve_batch: blocks per team (0 = automatic, 1 = one block per request) */
+  int fused_smem;          /* tiled 2D path: shared-memory extras, a bitmask of 1 = the finalised tiles of the
+                              last m_o + 1 basis vectors, 2 = the next raw tile prefetched (cp.async) during
+                              the cross-block sum, 4 = the tile's B columns and coupling fields; -1 (default) =
+                              automatic.  A combination that would lower the co-resident block count is
+                              dropped.  Results are bit-identical for every value. */
 } kiops_config;
 
 typedef struct {

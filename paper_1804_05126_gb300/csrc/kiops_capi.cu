@@ -223,7 +223,55 @@ struct Prepared {
   SolveArgs args;
   Layout L;
   char* base;
+  size_t dyn_smem = kDynSmem;  // dynamic shared memory of the launch
 };
+
+// Grid engine, tiled path: shared-memory extras of the fused phase, all placed over the exponential's
+// region (which invalidates them).  Ring: finalised tiles of the last m_o + 1 basis vectors; stage: the
+// next raw tile prefetched during the cross-block sum; cache: the tile's B columns and coupling fields.
+// The first combination that still leaves `blocks` co-resident blocks is taken.
+void enable_fused_smem(kiops_ctx* ctx, void* fn, int blocks, Prepared& P) {
+  SolveArgs& a = P.args;
+  if (!a.fused) return;
+  const size_t elem = a.prec ? 4 : 8;
+  const int ns = a.op.nspecies;
+  const size_t halo_pts = (size_t)ns * (a.tile_w + 2) * (a.tile_h + 2);
+  const size_t tile = halo_pts * elem;
+  const size_t cache = (size_t)(a.p + ns) * ns * a.tile_w * a.tile_h * elem;
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device) != cudaSuccess) return;
+  // automatic: preferred combinations (1 ring, 2 stage, 4 cache), measured on the 512^2 ADR (all three
+  // best) and 1024^2 Gray-Scott FP32 (only the ring fits with two blocks per SM, and beats the stage)
+  const int order[7] = {7, 3, 5, 1, 6, 2, 4};
+  const int forced = ctx->cfg.fused_smem;
+  for (int ci = 0; ci < (forced >= 0 ? 1 : 7); ++ci) {
+    const int mask = forced >= 0 ? (forced & 7) : order[ci];
+    if (mask == 0) break;
+    const int cb[3] = {mask & 1, (mask >> 1) & 1, (mask >> 2) & 1};
+    const int nr = cb[0] ? a.m_o + 1 : 0;
+    const size_t ring_b = up((size_t)(nr > 0 ? nr : 1) * tile);
+    const size_t stage_b = cb[1] ? up(tile) : 0;
+    const size_t tbl_b = cb[1] ? up(halo_pts * 4) : 0;
+    const size_t cache_b = cb[2] ? up(cache) : 0;
+    const size_t dyn = std::max(kDynSmem, ring_b + stage_b + tbl_b + cache_b);
+    if (dyn > (size_t)optin) continue;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) continue;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, dyn) != cudaSuccess) continue;
+    if ((int64_t)per_sm * ctx->sms < blocks) continue;
+    a.ring_n = nr;
+    a.stage_on = cb[1];
+    a.cache_on = cb[2];
+    a.sm_stage = (int)(ring_b / 8);
+    a.sm_tbl = (int)((ring_b + stage_b) / 8);
+    a.sm_cache = (int)((ring_b + stage_b + tbl_b) / 8);
+    P.dyn_smem = dyn;
+    return;
+  }
+  cudaGetLastError();
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+}
 
 // Validate one request and fill its argument block.
 kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b, double tol,
@@ -270,7 +318,9 @@ kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const
                df_elems);
   a.ldv = ldv;
   a.fused = 0;
-  if (A->d.kind == OP_ST2D && m_o_eff <= kChunk && grid_blocks > 1 && ctx->cfg.fuse_stencil) {
+  // (the tiled path codes a grid index r as 2 r + 1 in 32 bits)
+  if (A->d.kind == OP_ST2D && m_o_eff <= kChunk && grid_blocks > 1 && ctx->cfg.fuse_stencil &&
+      (int64_t)A->d.nspecies * A->d.nx * A->d.ny < ((int64_t)1 << 31)) {
     int gx = 0, gy = 0, tw = 0, th = 0;
     if (choose_tiles(A->d.nx, A->d.ny, A->d.nspecies, grid_blocks, prec == KIOPS_FP32_BASIS ? 4 : 8, gx, gy, tw, th)) {
       a.fused = 1;
@@ -362,6 +412,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
       P.args.wout[l] = wout[l];
     }
   }
+  if (engine == KIOPS_ENGINE_GRID) enable_fused_smem(ctx, fn, blocks, P);
   st = ensure_workspace(ctx, P.L.total);
   if (st) return st;
   bind(P, (char*)ctx->ws);
@@ -377,7 +428,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, hp, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
   const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
   void* kargs[] = {(void*)&dargs};
-  KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, kDynSmem, ctx->stream));
+  KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, P.dyn_smem, ctx->stream));
   int64_t* hs = (int64_t*)(hp + sizeof(SolveArgs) + 0);
   KCHECK(ctx, cudaMemcpyAsync(hs, P.base + P.L.stats, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
   int64_t* htl = hs + 15;
@@ -443,6 +494,7 @@ kiops_status kiops_config_default(kiops_config* cfg) {
   cfg->grid_blocks = 0;
   cfg->fuse_stencil = 1;
   cfg->batch_team_blocks = 0;
+  cfg->fused_smem = -1;
   return KIOPS_OK;
 }
 

@@ -17,6 +17,7 @@
 // over the blocks of the team.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace kiops_dev {
@@ -99,6 +100,13 @@ struct SolveArgs {
   // 2D stencils: lagged normalisation on 2D tiles (one barrier per Krylov step), see fused_st2d_phase
   int fused;                 // 1: use the tiled lagged path
   int tile_gx, tile_gy, tile_w, tile_h;
+  // fused path, dynamic shared memory (all of it reused by the exponential, which invalidates it):
+  //   [ring: max(ring_n, 1) halo'd tiles][stage: one halo'd tile][table: one code per halo'd tile point]
+  //   [cache: (p + ns) values per tile point]
+  int ring_n;                // finalised tiles of the last ring_n basis vectors (0: only v_j's tile is kept)
+  int stage_on;              // prefetch the raw x_{j+1} tile + halo with cp.async (needs the table)
+  int cache_on;              // keep the tile's B columns and coupling fields in shared memory
+  int sm_stage, sm_tbl, sm_cache;  // offsets (doubles) in dynamic shared memory
   void* raw;                 // two raw vectors x_{j+1} of ldv elements (ring, fused path only)
   float* bf;                 // FP32 basis: B columns as floats, column t = b_{p-t} at bf + t*ldv
   float* df;                 // FP32 basis: pointwise coupling fields as floats, (s*ns + q)*npts (stencils)
@@ -209,6 +217,11 @@ struct Ctl {
   float yhi[kMaxN], ylo[kMaxN];  // FP32 basis: update weights split into float hi + lo
   double yint[kMaxN];           // Task I: first column of exp(tau~ H_j) for an intermediate output
   double t_sub, tau_sub;        // start time and step of the substep that was just accepted
+  int ring_lo;                  // fused path: v_ring_lo .. v_j are in the shared-memory ring
+  int pre_j;                    // fused path: the stage holds raw x_{pre_j} (0: nothing staged)
+  int cache_ok;                 // fused path: the B / coupling cache is filled
+  int tbl_ok;                   // fused path: the halo index table is filled
+  double vtail[kGramRing][kMaxP];  // fused path: tail of v_k (basis precision) in row k % kGramRing
   int ell;                      // Task I: next output index (Algorithm 1 line 6)
   double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
   double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
@@ -297,15 +310,9 @@ __device__ inline bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, in
   return true;
 }
 
-template <>
-__device__ inline bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K,
-                                        bool prof_on) {
-  double* buf = partials + (size_t)parity * team.size * kMaxRed;
-  for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
-  if (!team.sync(&c.sync_ok)) return false;
-  KIOPS_TICK(11);
-  // thread t loads rank t's partials (ranks t + kThreads, ... added on top), then the fixed block tree
-  // over only as many warps as hold ranks
+// Sum the published partials of all ranks into red[0..K): thread t loads rank t's partials (ranks
+// t + kThreads, ... added on top), then the fixed block tree over only as many warps as hold ranks.
+__device__ inline void grid_sum_partials(GridTeam& team, Ctl& c, const double* buf, int K) {
   const int nw = team.size >= kThreads ? kWarps : (team.size + 31) / 32;
   for (int k0 = 0; k0 < K; k0 += kRegK) {
     const int cnt = K - k0 < kRegK ? K - k0 : kRegK;
@@ -322,8 +329,39 @@ __device__ inline bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* p
     }
     block_reduce_to(c, acc, cnt, c.red + k0, nw);
   }
+}
+
+template <>
+__device__ inline bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K,
+                                        bool prof_on) {
+  double* buf = partials + (size_t)parity * team.size * kMaxRed;
+  for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
+  if (!team.sync(&c.sync_ok)) return false;
+  KIOPS_TICK(11);
+  grid_sum_partials(team, c, buf, K);
   parity ^= 1;
   return true;
+}
+
+// finish_reduce followed by work that needs the barrier but not the sums (the fused path issues its
+// prefetch of the next raw tile there, overlapping the coefficient computation).
+template <class Team, class Hook>
+__device__ __forceinline__ bool finish_reduce_hook(Team& team, Ctl& c, double* partials, int& parity, int K,
+                                                   bool prof_on, Hook&& hook) {
+  if constexpr (std::is_same<Team, GridTeam>::value) {
+    double* buf = partials + (size_t)parity * team.size * kMaxRed;
+    for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
+    if (!team.sync(&c.sync_ok)) return false;
+    KIOPS_TICK(11);
+    grid_sum_partials(team, c, buf, K);
+    hook();
+    parity ^= 1;
+    return true;
+  } else {
+    if (!finish_reduce<Team>(team, c, partials, parity, K, prof_on)) return false;
+    hook();
+    return true;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -428,6 +466,15 @@ __device__ __forceinline__ T bcol(const SolveArgs& a, int t, size_t r) {
   if constexpr (sizeof(T) == 4) return a.bf[(size_t)t * a.ldv + r];
   else return __ldg(a.b[a.p - t] + r);
 }
+// Asynchronous global -> shared copies of one element (completed by cp_async_wait_all).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ T diag_val(const SolveArgs& a, int sp, int q, uint32_t pt) {
   if constexpr (sizeof(T) == 4) {
@@ -615,6 +662,7 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
   T* raw = (T*)a.raw;
   const bool pend = c.fin_pending != 0;
   const T* src = pend ? raw + (size_t)((j - 1) & 1) * ldv : V + (size_t)(j - 1) * ldv;  // v_j before finalising
+  const bool staged = pend && a.stage_on && c.pre_j == j;  // raw x_j already in shared memory
   T* vj = V + (size_t)(j - 1) * ldv;
   T* xo = raw + (size_t)(j & 1) * ldv;  // raw x_{j+1}
   const int fnw = pend ? c.fin_nwin : 0;
@@ -627,69 +675,126 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
   const T* w0 = V + (size_t)(i0 - 1) * ldv;  // dot window of step j (v_j itself comes from shared memory)
   const T* w1 = V + (size_t)(i0 + (nwin > 1 ? 1 : 0) - 1) * ldv;
   const T* w2 = V + (size_t)(i0 + (nwin > 2 ? 2 : 0) - 1) * ldv;
+  // shared-memory ring: v_k's finalised tile (with halo) sits in slot (k-1) % ring_n; entries below
+  // max(ring_lo, j - ring_n + 1) are stale
+  const int nr = a.ring_n;
+  const int ring_valid_from = nr > 0 ? max(c.ring_lo, j - nr + 1) : (1 << 30);
   if (rank < a.tile_gx * a.tile_gy) {
     const int bx = rank % a.tile_gx, by = rank / a.tile_gx;
     const int x0 = bx * a.tile_w, y0 = by * a.tile_h;
     const int tw = min(a.tile_w, (int)nx - x0), th = min(a.tile_h, (int)ny - y0);
     if (tw > 0 && th > 0) {
       const int hw = tw + 2, hh = th + 2, plane = hw * hh;
-      T* st = (T*)smem;
-      for (int e = tid; e < ns * plane; e += kThreads) {
-        const int sp = e / plane, rem = e - sp * plane, hy = rem / hw, hx = rem - hy * hw;
-        int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-        bool inside = true;
-        if (op.periodic) {
-          gx = gx < 0 ? gx + (int)nx : (gx >= (int)nx ? gx - (int)nx : gx);
-          gy = gy < 0 ? gy + (int)ny : (gy >= (int)ny ? gy - (int)ny : gy);
-        } else if (gx < 0 || gx >= (int)nx || gy < 0 || gy >= (int)ny) {
-          inside = false;
-        }
-        T v = T(0);
-        if (inside) {
-          const size_t r = (size_t)sp * npts + (size_t)gy * nx + gx;
-          v = src[r];
-          if (pend) {
-            v = fma(-fh0, f0[r], v);
-            if (fnw > 1) v = fma(-fh1, f1[r], v);
-            if (fnw > 2) v = fma(-fh2, f2[r], v);
-            v = v * frs;
-            if (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) vj[r] = v;
+      T* ring = (T*)smem;
+      const size_t rstride = (size_t)ns * plane;
+      T* st = nr > 0 ? ring + (size_t)((j - 1) % nr) * rstride : ring;
+      const T* stage = (const T*)(smem + a.sm_stage);
+      T* cache = (T*)(smem + a.sm_cache);
+      const bool cfill = a.cache_on && !c.cache_ok;
+      const int E = ns * tw * th;
+      // halo point e -> 2 r + (1 if the point is this block's own), ~0u outside a non-periodic grid
+      unsigned* tbl = (unsigned*)(smem + a.sm_tbl);
+      const bool tok = a.stage_on && c.tbl_ok;
+      auto rslot = [&](int k) -> const T* { return ring + (size_t)((k - 1) % nr) * rstride; };
+      const bool rf0 = pend && fnw > 0 && c.fin_i0 >= ring_valid_from;
+      const bool rf1 = pend && fnw > 1 && c.fin_i0 + 1 >= ring_valid_from;
+      const bool rf2 = pend && fnw > 2 && c.fin_i0 + 2 >= ring_valid_from;
+      const T* g0 = rf0 ? rslot(c.fin_i0) : nullptr;
+      const T* g1 = rf1 ? rslot(c.fin_i0 + 1) : nullptr;
+      const T* g2 = rf2 ? rslot(c.fin_i0 + 2) : nullptr;
+      // finalisation over tile + halo; TOK: the index table is filled (no index arithmetic)
+      const bool wtbl = a.stage_on, periodic = op.periodic;  // (the argument block is in shared memory)
+      auto finalize = [&](auto tok_tag) {
+        constexpr bool TOK = decltype(tok_tag)::value;
+        for (int e = tid; e < ns * plane; e += kThreads) {
+          unsigned code;
+          if constexpr (TOK) {
+            code = tbl[e];
+          } else {
+            const int sp = e / plane, rem = e - sp * plane, hy = rem / hw, hx = rem - hy * hw;
+            int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+            bool inside = true;
+            if (periodic) {
+              gx = gx < 0 ? gx + (int)nx : (gx >= (int)nx ? gx - (int)nx : gx);
+              gy = gy < 0 ? gy + (int)ny : (gy >= (int)ny ? gy - (int)ny : gy);
+            } else if (gx < 0 || gx >= (int)nx || gy < 0 || gy >= (int)ny) {
+              inside = false;
+            }
+            const unsigned own = (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) ? 1u : 0u;
+            code = inside ? 2u * ((unsigned)sp * npts + (unsigned)gy * nx + (unsigned)gx) + own : ~0u;
+            if (wtbl) tbl[e] = code;
           }
+          T v = T(0);
+          if (code != ~0u) {
+            const size_t r = code >> 1;
+            v = staged ? stage[e] : src[r];
+            if (pend) {
+              v = fma(-fh0, rf0 ? g0[e] : f0[r], v);
+              if (fnw > 1) v = fma(-fh1, rf1 ? g1[e] : f1[r], v);
+              if (fnw > 2) v = fma(-fh2, rf2 ? g2[e] : f2[r], v);
+              v = v * frs;
+              if (code & 1u) vj[r] = v;
+            }
+          }
+          st[e] = v;
         }
-        st[e] = v;
+      };
+      if (tok) finalize(std::true_type{});
+      else finalize(std::false_type{});
+      if (cfill) {  // B columns and coupling fields of the tile's own points (each thread its own e)
+        for (int e = tid; e < E; e += kThreads) {
+          const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
+          const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
+          const size_t r = (size_t)sp * npts + pt;
+          for (int t = 0; t < p; ++t) cache[(size_t)t * E + e] = bcol<T>(a, t, r);
+          for (int q = 0; q < ns; ++q)
+            if (op.diag[sp][q]) cache[(size_t)(p + q) * E + e] = diag_val<T>(a, sp, q, pt);
+        }
       }
       __syncthreads();
       KIOPS_TICK(12);
-      for (int e = tid; e < ns * tw * th; e += kThreads) {
-        const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
-        const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
-        const size_t r = (size_t)sp * npts + pt;
-        const int h = sp * plane + (ly + 1) * hw + (lx + 1);
-        const double* cf = op.coef[sp];
-        const T ctr = st[h];
-        T xv = T(cf[0]) * ctr;
-        xv = fma(T(cf[1]), st[h - 1], xv);
-        xv = fma(T(cf[2]), st[h + 1], xv);
-        xv = fma(T(cf[3]), st[h - hw], xv);
-        xv = fma(T(cf[4]), st[h + hw], xv);
-        for (int q = 0; q < ns; ++q)
-          if (op.diag[sp][q]) xv = fma(diag_val<T>(a, sp, q, pt), st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
-        for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), bcol<T>(a, t, r), xv);
-        xo[r] = xv;
-        const T v0 = (i0 == j) ? ctr : w0[r];
-        acc.add(0, v0, xv);
-        acc.add(kChunk, ctr, v0);
-        if (nwin > 1) {
-          const T v1 = (i0 + 1 == j) ? ctr : w1[r];
-          acc.add(1, v1, xv);
-          acc.add(kChunk + 1, ctr, v1);
+      const bool rw0 = i0 != j && i0 >= ring_valid_from, rw1 = nwin > 1 && i0 + 1 != j && i0 + 1 >= ring_valid_from;
+      const T* q0 = rw0 ? rslot(i0) : nullptr;
+      const T* q1 = rw1 ? rslot(i0 + 1) : nullptr;
+      // A~ v_j on the own points and the step's dots; CACHE: B and coupling values from shared memory
+      auto compute = [&](auto cache_tag) {
+        constexpr bool CACHE = decltype(cache_tag)::value;
+        for (int e = tid; e < E; e += kThreads) {
+          const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
+          const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
+          const size_t r = (size_t)sp * npts + pt;
+          const int h = sp * plane + (ly + 1) * hw + (lx + 1);
+          const double* cf = op.coef[sp];
+          const T ctr = st[h];
+          T xv = T(cf[0]) * ctr;
+          xv = fma(T(cf[1]), st[h - 1], xv);
+          xv = fma(T(cf[2]), st[h + 1], xv);
+          xv = fma(T(cf[3]), st[h - hw], xv);
+          xv = fma(T(cf[4]), st[h + hw], xv);
+          for (int q = 0; q < ns; ++q)
+            if (op.diag[sp][q]) {
+              const T dv = CACHE ? cache[(size_t)(p + q) * E + e] : diag_val<T>(a, sp, q, pt);
+              xv = fma(dv, st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
+            }
+          for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), CACHE ? cache[(size_t)t * E + e] : bcol<T>(a, t, r), xv);
+          xo[r] = xv;
+          const T v0 = (i0 == j) ? ctr : (rw0 ? q0[h] : w0[r]);
+          acc.add(0, v0, xv);
+          acc.add(kChunk, ctr, v0);
+          if (nwin > 1) {
+            const T v1 = (i0 + 1 == j) ? ctr : (rw1 ? q1[h] : w1[r]);
+            acc.add(1, v1, xv);
+            acc.add(kChunk + 1, ctr, v1);
+          }
+          if (nwin > 2) {  // i0 + 2 == j
+            acc.add(2, ctr, xv);
+            acc.add(kChunk + 2, ctr, ctr);
+          }
+          acc.add(2 * kChunk, xv, xv);
         }
-        if (nwin > 2) {  // i0 + 2 == j
-          acc.add(2, ctr, xv);
-          acc.add(kChunk + 2, ctr, ctr);
-        }
-        acc.add(2 * kChunk, xv, xv);
-      }
+      };
+      if (a.cache_on) compute(std::true_type{});
+      else compute(std::false_type{});
     }
   }
   if (lead && tid < p) {  // tail rows: finalised tail of v_j (c.tail) and the shift K of Theorem 1
@@ -707,6 +812,27 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
       }
     }
     acc.add(2 * kChunk, xv, xv);
+  }
+}
+
+// Fused path: issue the asynchronous copies of raw x_jn (written by every block before the barrier that
+// was passed) over this block's tile + halo into the stage, from the halo index table.  Threads below
+// `first` issue none (thread 0 computes the step's coefficients meanwhile); the copies are waited for
+// before the block barrier that opens the next step.
+template <typename T>
+__device__ void fused_prefetch(const SolveArgs& a, int rank, int jn, double* smem, int first) {
+  const OpDesc& op = a.op;
+  if (rank >= a.tile_gx * a.tile_gy || (int)threadIdx.x < first) return;
+  const int x0 = (rank % a.tile_gx) * a.tile_w, y0 = (rank / a.tile_gx) * a.tile_h;
+  const int tw = min(a.tile_w, (int)op.nx - x0), th = min(a.tile_h, (int)op.ny - y0);
+  if (tw <= 0 || th <= 0) return;
+  const int nel = op.nspecies * (tw + 2) * (th + 2);
+  const T* src = (const T*)a.raw + (size_t)((jn - 1) & 1) * (size_t)a.ldv;
+  T* stage = (T*)(smem + a.sm_stage);
+  const unsigned* tbl = (const unsigned*)(smem + a.sm_tbl);
+  for (int e = threadIdx.x - first; e < nel; e += kThreads - first) {
+    const unsigned code = tbl[e];
+    if (code != ~0u) cp_async_elem(stage + e, src + (code >> 1));
   }
 }
 
@@ -748,6 +874,15 @@ __device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, 
   const bool prof_on = a.prof != nullptr && team.rank == 0;
   const int n = a.expm_only ? a.expm_n : (aug ? c.j + 1 : c.j);
   const size_t ldm = (size_t)(a.m_max + 1) * (a.m_max + 1);
+  // the fused path's shared-memory ring, stage and cache live in this region: wait for this thread's
+  // copies in flight and mark them all stale
+  cp_async_wait_all();
+  if (threadIdx.x == 0) {
+    c.ring_lo = 1 << 30;
+    c.pre_j = 0;
+    c.cache_ok = 0;
+    c.tbl_ok = 0;
+  }
   double* sA = smem_dyn;
   double* sB = smem_dyn + kTile * kMaxN;
   // ||tau H~||_1 from the running column sums (every block holds the same values)
@@ -951,6 +1086,10 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     for (int k = 0; k < 16; ++k) c.prof[k] = 0;
     c.prof_last = clock64();
     c.ell = 0;
+    c.ring_lo = 1 << 30;
+    c.pre_j = 0;
+    c.cache_ok = 0;
+    c.tbl_ok = 0;
   }
   __syncthreads();
 
@@ -1037,6 +1176,8 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         c.kappa = 2.0;
         c.qp1_est = 0.0;
         c.fin_pending = 0;
+        c.ring_lo = 1 << 30;
+        c.pre_j = 0;
       }
       __syncthreads();
       double acc[kRegK];
@@ -1075,17 +1216,21 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       const T* vj = V + (size_t)(j - 1) * ldv;
       T* x = V + (size_t)j * ldv;
       if (tid < p) {
-        if (fused && c.fin_pending) {  // finalise the pending tail with the arithmetic of the normalise pass
-          const size_t rr = (size_t)N + tid;
-          T xv = ((const T*)a.raw)[(size_t)((j - 1) & 1) * ldv + rr];
-          for (int u = 0; u < c.fin_nwin; ++u) xv = fma(-T(c.fin_h[u]), V[(size_t)(c.fin_i0 + u - 1) * ldv + rr], xv);
+        if (fused && c.fin_pending) {
+          // finalise the pending tail with the arithmetic of the normalise pass; the raw tail of x_j is
+          // K v_{j-1} and the window's tails are kept per block, so no global value is needed
+          T xv = tid + 1 < p ? T(c.vtail[(j - 1) % kGramRing][tid + 1]) : T(0);
+          for (int u = 0; u < c.fin_nwin; ++u)
+            xv = fma(-T(c.fin_h[u]), T(c.vtail[(c.fin_i0 + u) % kGramRing][tid]), xv);
           xv = xv * T(c.fin_rs);
           c.tail[tid] = (double)xv;
         } else {
           c.tail[tid] = (double)vj[N + tid];
         }
+        c.vtail[j % kGramRing][tid] = c.tail[tid];
         c.ntail[tid] = c.nu * c.tail[tid];
       }
+      if (fused) cp_async_wait_all();  // the stage prefetched during the last step
       __syncthreads();
       // pass 0 computes x = A~ v_j, stores it raw, and reduces <v_i, x>, <x, x>, <v_j, v_i> for the
       // first kChunk window entries; later passes reread x for further window entries (m_o > kChunk).
@@ -1096,6 +1241,11 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         dacc.zero();
         fused_st2d_phase<T>(a, c, team.rank, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
         __syncthreads();
+        if (tid == 0) {
+          c.ring_lo = (c.ring_lo <= j - 1) ? c.ring_lo : j;  // v_j is now in the ring
+          c.cache_ok = a.cache_on;
+          c.tbl_ok = a.stage_on;
+        }
         KIOPS_TICK(13);
         double acc[kRegK];
         dacc.to_double(acc);
@@ -1231,7 +1381,16 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       for (int k = tid; k < Ktot; k += kThreads) c.blk[k] = c.red[k];
       __syncthreads();
       KIOPS_TICK(2);
-      if (!finish_reduce<Team>(team, c, a.partials, parity, Ktot, prof_on)) goto stop;
+      {
+        // fused path: x_{j+1} is complete once the barrier is passed; stage its tile for step j + 1
+        auto prefetch = [&]() {
+          if (fused && a.stage_on && c.tbl_ok && j < c.m) {
+            fused_prefetch<T>(a, team.rank, j + 1, smem_dyn, 32);
+            if (tid == 0) c.pre_j = j + 1;
+          }
+        };
+        if (!finish_reduce_hook<Team>(team, c, a.partials, parity, Ktot, prof_on, prefetch)) goto stop;
+      }
       KIOPS_TICK(3);
       // ---- MGS coefficients from CGS dots and the Gram entries (Algorithm 2 lines 7-10):
       // h_i = <v_i, x> - sum_{k<i} h_k <v_i, v_k>;  ||x - sum h_i v_i||^2 expanded over the window
@@ -1490,6 +1649,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     }
   }
 stop:
+  cp_async_wait_all();  // no copy of the fused path outlives the block
   __syncthreads();
   if (lead && tid == 0) {
     int st = c.status;

@@ -51,6 +51,13 @@ def test_defaults_match_the_paper(libpath):
                                                            pc["kappa_default"], pc["tau_clip_high"], pc["m_o_default"])
 
 
+def test_engineering_defaults(libpath):
+    from paper_1804_05126_gb300 import kiops
+    cfg = kiops.kiops_config_default()
+    assert cfg.fuse_stencil == 1 and cfg.fused_smem == -1 and cfg.batch_team_blocks == 0
+    assert cfg.grid_blocks == 0 and cfg.profile == 0 and cfg.normalize_B == 1
+
+
 def test_status_strings_and_null_handling(libpath):
     from paper_1804_05126_gb300 import kiops
     L = kiops.lib()
