@@ -113,17 +113,22 @@ typedef struct {
 typedef struct kiops_ctx kiops_ctx;
 typedef struct kiops_op kiops_op;
 
+/* Boundary treatment of the stencil operators: the value of x at an index just outside the grid.
+ * KIOPS_BC_DIRICHLET: 0 (homogeneous Dirichlet); KIOPS_BC_PERIODIC: the index wraps;
+ * KIOPS_BC_NEUMANN: reflection about the boundary point, x(-1) = x(1) and x(n) = x(n-2) (homogeneous
+ * Neumann with the second-order ghost point; needs n >= 2 in every dimension). */
+enum { KIOPS_BC_DIRICHLET = 0, KIOPS_BC_PERIODIC = 1, KIOPS_BC_NEUMANN = 2 };
+
 /* 5-point 2D stencil (1 or 2 species) with a pointwise coupling block: unknowns species-blocked
  * [u; v], each x-fastest (index = s*nx*ny + iy*nx + ix).  For species s:
  *   (A x)_s(ix,iy) = coef[s][0] x_s(ix,iy) + coef[s][1] x_s(ix-1,iy) + coef[s][2] x_s(ix+1,iy)
  *                  + coef[s][3] x_s(ix,iy-1) + coef[s][4] x_s(ix,iy+1) + sum_r diag[s][r][pt] x_r(ix,iy)
- * Outside the grid x = 0 (periodic = 0, homogeneous Dirichlet) or indices wrap (periodic = 1).
- * diag[s][r] are device pointers of nx*ny FP64 values or NULL (= 0).  This covers the Jacobians of the
- * paper's 2D ADR and Gray-Scott test problems (section 4). */
+ * with x outside the grid given by bc.  diag[s][r] are device pointers of nx*ny FP64 values or NULL
+ * (= 0).  This covers the Jacobians of the paper's 2D ADR and Gray-Scott test problems (section 4). */
 typedef struct {
   int64_t nx, ny;
   int nspecies;            /* 1 or 2 */
-  int periodic;
+  int bc;                  /* KIOPS_BC_* */
   double coef[2][5];
   const double* diag[2][2];
 } kiops_stencil2d_desc;
@@ -133,7 +138,7 @@ typedef struct {
  *            + c[6] x(i+ez) + diag[i] x(i);  diag is a device pointer of N FP64 values or NULL. */
 typedef struct {
   int64_t nx, ny, nz;
-  int periodic;
+  int bc;                  /* KIOPS_BC_* */
   double coef[7];
   const double* diag;
 } kiops_stencil3d_desc;
@@ -268,6 +273,51 @@ kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* 
 kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]);
 /* Stop the server after the queued work (waits for the kernel), free its memory. */
 kiops_status kiops_server_stop(kiops_ctx* ctx);
+
+/* ---- Exponential integrators (section 4) ------------------------------------------------------------
+ * Constant-step integration of the paper's nonlinear 2D test problems with the stiffly accurate schemes of
+ * section 4 in their grouped ("mixed") form of section 2: per step one Task I call gives both stage
+ * vectors (phi_1 at the two stage nodes), one Task II call (eqs 10-11, A = h J_n, tau = 1) gives u_{n+1};
+ * EXPRB5s3 adds a Task I call for the phi_3 terms of its third stage.  Each call starts from the Krylov
+ * dimension its counterpart ended with in the previous step (section 3.6).  All in FP64.
+ *   EPIRK4s3  (eq 50): nodes 1/8, 1/9; b_3 = h(1892 r2 + 1458 (r3 - 2 r2)), b_4 = h(-42336 r2 - 34992 (r3 - 2 r2))
+ *   EPIRK4s3A (eq 51): nodes 1/2, 2/3; b_3 = h(32 r2 - 27/2 r3), b_4 = h(-144 r2 + 81 r3)
+ *   EXPRB5s3  (eq 53): nodes 1/2, 9/10; third stage + (27/25 phi_3(A/2) + 729/125 phi_3(9A/10)) h r2;
+ *                      b_3 = h(18 r2 - 250/81 r3), b_4 = h(-60 r2 + 500/27 r3)
+ * with r2 = r(U_n2), r3 = r(U_n3) and r(U) = f(U) - f(u_n) - J_n (U - u_n) (section 2). */
+enum { KIOPS_PDE_ADR2D = 0, KIOPS_PDE_GRAY_SCOTT2D = 1 };
+enum { KIOPS_EPIRK4S3 = 0, KIOPS_EPIRK4S3A = 1, KIOPS_EXPRB5S3 = 2 };
+
+/* KIOPS_PDE_ADR2D: u_t = eps Lap u - alpha (u_x + u_y) + gamma u (u - 1/2)(1 - u) on [0,1]^2, homogeneous
+ *   Neumann, n x n vertex grid including the boundary (spacing 1/(n-1)); param = {eps, alpha, gamma}
+ *   (section 4: 1/100, -10, 100).  N = n^2.
+ * KIOPS_PDE_GRAY_SCOTT2D: u_t = d_u Lap u - u v^2 + a (1 - u), v_t = d_v Lap v + u v^2 - (a + b) v on the
+ *   periodic unit square, grid x = i/n; param = {d_u, d_v, a, b} (section 4: 0.2, 0.1, 0.04, 0.06).
+ *   N = 2 n^2, species-blocked [u; v].
+ * Second-order centred differences, x fastest. */
+typedef struct {
+  int kind;                 /* KIOPS_PDE_* */
+  int64_t n;                /* points per dimension (>= 2) */
+  double param[4];
+} kiops_pde;
+
+typedef struct {
+  int64_t steps;            /* time steps taken */
+  int64_t kiops_calls;      /* phi-function solves */
+  int64_t matvecs, substeps, rejected;  /* summed over the solves */
+  int m_last[3];            /* final Krylov dimension of each call slot of the last step */
+} kiops_integrate_stats;
+
+/* f = f(u) of the test problem (device vectors of N FP64 values).  Waits for the context's stream. */
+kiops_status kiops_pde_rhs(kiops_ctx* ctx, const kiops_pde* pde, const double* u, double* f);
+
+/* Integrate from t0 to t1 > t0 in nsteps equal steps with the scheme KIOPS_EPIRK4S3 / _EPIRK4S3A /
+ * _EXPRB5S3; u (device, N FP64) holds u(t0) on entry and u(t1) on return.  tol is each solve's tolerance,
+ * m_init the first step's starting Krylov dimension.  The context allocates its integrator workspace
+ * (about 16 N FP64 values) on first use.  Errors of a solve are returned as they are (stats then count
+ * the steps completed). */
+kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, double t0, double t1, int64_t nsteps,
+                             double tol, int m_init, double* u, kiops_integrate_stats* stats);
 
 /* Size of the fixed device scratch used by kiops_solve_noalloc (bytes). */
 #define KIOPS_NOALLOC_SCRATCH_BYTES (32u << 20)

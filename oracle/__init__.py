@@ -44,11 +44,19 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bc_code(op: dict) -> int:
+    """Boundary of a stencil description: op["bc"] in {"dirichlet", "periodic", "neumann"}, else the
+    boolean op["periodic"]."""
+    if op.get("bc") is not None:
+        return {"dirichlet": 0, "periodic": 1, "neumann": 2}[op["bc"]]
+    return 1 if op.get("periodic") else 0
+
+
 class _Op(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int64),
                 ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("vals", C.c_void_p),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
-                ("nspecies", C.c_int), ("periodic", C.c_int),
+                ("nspecies", C.c_int), ("bc", C.c_int),
                 ("coef", (C.c_double * 7) * 2), ("diag", (C.c_void_p * 2) * 2),
                 ("dense", C.c_void_p)]
 
@@ -111,7 +119,7 @@ def _make_op(op: dict):
     elif k == "stencil2d":
         s.kind = 1
         s.nx, s.ny, s.nz = int(op["nx"]), int(op["ny"]), 1
-        s.nspecies, s.periodic = int(op["nspecies"]), int(bool(op["periodic"]))
+        s.nspecies, s.bc = int(op["nspecies"]), _bc_code(op)
         s.n = s.nx * s.ny * s.nspecies
         for sp in range(s.nspecies):
             for c in range(5):
@@ -122,7 +130,7 @@ def _make_op(op: dict):
     elif k == "stencil3d":
         s.kind = 2
         s.nx, s.ny, s.nz = int(op["nx"]), int(op["ny"]), int(op["nz"])
-        s.nspecies, s.periodic = 1, int(bool(op["periodic"]))
+        s.nspecies, s.bc = 1, _bc_code(op)
         s.n = s.nx * s.ny * s.nz
         for c in range(7):
             s.coef[0][c] = float(op["coef"][c])

@@ -50,7 +50,7 @@ typedef struct {
   /* stencils: grid sizes, species count (2D only), boundary type */
   int64_t nx, ny, nz;
   int nspecies;             /* 1 or 2 (2D); species-blocked unknown ordering [u; v] */
-  int periodic;             /* 0: homogeneous Dirichlet, 1: periodic */
+  int bc;                   /* 0: homogeneous Dirichlet, 1: periodic, 2: homogeneous Neumann */
   double coef[2][7];        /* per species: centre, -x, +x, -y, +y, (-z, +z) */
   const double* diag[2][2]; /* diag[r][c][pt]: pointwise coupling from species c into species r; NULL = 0 */
   /* dense (row-major n x n) */
@@ -80,10 +80,21 @@ enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2, ORACLE_ENOTCONV = 3 
 /* y = A x for the operator; follows the definitions of the test problems' Jacobians (section 4). */
 static double stencil_x(const oracle_op* A, const double* x, int s, int64_t ix, int64_t iy, int64_t iz) {
   int64_t nx = A->nx, ny = A->ny, nz = A->kind == 2 ? A->nz : 1;
-  if (A->periodic) {
+  if (A->bc == 1) {
     ix = (ix + nx) % nx;
     iy = (iy + ny) % ny;
     iz = (iz + nz) % nz;
+  } else if (A->bc == 2) {
+    /* homogeneous Neumann, second-order ghost point: the value one step outside equals the value one
+       step inside (x(-1) = x(1), x(n) = x(n-2)) */
+    if (ix < 0) ix = -ix;
+    if (ix >= nx) ix = 2 * (nx - 1) - ix;
+    if (iy < 0) iy = -iy;
+    if (iy >= ny) iy = 2 * (ny - 1) - iy;
+    if (nz > 1) {
+      if (iz < 0) iz = -iz;
+      if (iz >= nz) iz = 2 * (nz - 1) - iz;
+    }
   } else if (ix < 0 || ix >= nx || iy < 0 || iy >= ny || iz < 0 || iz >= nz) {
     return 0.0;
   }

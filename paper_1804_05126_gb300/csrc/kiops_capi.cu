@@ -47,6 +47,8 @@ struct kiops_ctx {
   TaylorTable tt{};
   bool busy = false;
   KiopsServer* server = nullptr;
+  double* integ = nullptr;      // integrator workspace (kiops_integrate)
+  size_t integ_bytes = 0;
 };
 
 struct kiops_op {
@@ -559,6 +561,7 @@ kiops_status kiops_destroy(kiops_ctx* ctx) {
   if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   if (ctx->stage_dev) cudaFree(ctx->stage_dev);
+  if (ctx->integ) cudaFree(ctx->integ);
   delete ctx;
   return KIOPS_OK;
 }
@@ -612,6 +615,8 @@ kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   *op = nullptr;
   if (d->nx < 1 || d->ny < 1 || (d->nspecies != 1 && d->nspecies != 2) || d->nx * d->ny * d->nspecies > INT32_MAX)
     return fail(ctx, KIOPS_EINVAL, "invalid 2D stencil description (sizes, species, or more than 2^31-1 unknowns)");
+  if (d->bc < KIOPS_BC_DIRICHLET || d->bc > KIOPS_BC_NEUMANN || (d->bc == KIOPS_BC_NEUMANN && (d->nx < 2 || d->ny < 2)))
+    return fail(ctx, KIOPS_EINVAL, "invalid boundary code %d (Neumann needs at least 2 points per dimension)", d->bc);
   kiops_op* o = new (std::nothrow) kiops_op();
   if (!o) return KIOPS_ENOMEM;
   o->ctx = ctx;
@@ -621,7 +626,7 @@ kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   o->d.ny = d->ny;
   o->d.nz = 1;
   o->d.nspecies = d->nspecies;
-  o->d.periodic = d->periodic ? 1 : 0;
+  o->d.bc = d->bc;
   o->d.n = d->nx * d->ny * d->nspecies;
   for (int s = 0; s < 2; ++s) {
     for (int k = 0; k < 5; ++k) o->d.coef[s][k] = s < d->nspecies ? d->coef[s][k] : 0.0;
@@ -636,6 +641,9 @@ kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   *op = nullptr;
   if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx * d->ny * d->nz > INT32_MAX)
     return fail(ctx, KIOPS_EINVAL, "invalid 3D stencil description (sizes or more than 2^31-1 unknowns)");
+  if (d->bc < KIOPS_BC_DIRICHLET || d->bc > KIOPS_BC_NEUMANN ||
+      (d->bc == KIOPS_BC_NEUMANN && (d->nx < 2 || d->ny < 2 || d->nz < 2)))
+    return fail(ctx, KIOPS_EINVAL, "invalid boundary code %d (Neumann needs at least 2 points per dimension)", d->bc);
   kiops_op* o = new (std::nothrow) kiops_op();
   if (!o) return KIOPS_ENOMEM;
   o->ctx = ctx;
@@ -645,7 +653,7 @@ kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   o->d.ny = d->ny;
   o->d.nz = d->nz;
   o->d.nspecies = 1;
-  o->d.periodic = d->periodic ? 1 : 0;
+  o->d.bc = d->bc;
   o->d.n = d->nx * d->ny * d->nz;
   for (int k = 0; k < 7; ++k) o->d.coef[0][k] = d->coef[k];
   o->d.diag[0][0] = d->diag;
@@ -1344,6 +1352,171 @@ kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]) {
   info[3] = S->sd.teams[0];
   info[4] = S->sd.teams[1];
   info[5] = S->sd.team_blocks[1];
+  return KIOPS_OK;
+}
+
+
+// ---- Exponential integrators (section 4) -------------------------------------------------------------
+static kiops_status pde_dev(kiops_ctx* ctx, const kiops_pde* pde, kiops_k::PdeDev& P) {
+  if (!pde) return fail(ctx, KIOPS_EINVAL, "NULL problem");
+  if (pde->kind != KIOPS_PDE_ADR2D && pde->kind != KIOPS_PDE_GRAY_SCOTT2D)
+    return fail(ctx, KIOPS_EINVAL, "unknown test problem %d", pde->kind);
+  if (pde->n < 2 || (pde->kind == KIOPS_PDE_GRAY_SCOTT2D ? 2 : 1) * pde->n * pde->n > INT32_MAX)
+    return fail(ctx, KIOPS_EINVAL, "grid size n = %lld outside [2, 2^31-1 unknowns]", (long long)pde->n);
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(pde->param[k])) return fail(ctx, KIOPS_EINVAL, "parameter %d is not finite", k);
+  std::memset(&P, 0, sizeof(P));
+  P.kind = pde->kind;
+  P.n = pde->n;
+  if (pde->kind == KIOPS_PDE_ADR2D) {
+    P.ns = 1;
+    P.bc = KIOPS_BC_NEUMANN;
+    P.dx = 1.0 / (double)(pde->n - 1);
+  } else {
+    P.ns = 2;
+    P.bc = KIOPS_BC_PERIODIC;
+    P.dx = 1.0 / (double)pde->n;
+  }
+  for (int k = 0; k < 4; ++k) P.prm[k] = pde->param[k];
+  return KIOPS_OK;
+}
+
+kiops_status kiops_pde_rhs(kiops_ctx* ctx, const kiops_pde* pde, const double* u, double* f) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (!u || !f) return fail(ctx, KIOPS_EINVAL, "NULL u or f");
+  kiops_k::PdeDev P;
+  kiops_status st = pde_dev(ctx, pde, P);
+  if (st) return st;
+  KCHECK(ctx, kiops_k::launch_pde_eval(P, u, 1.0, f, nullptr, ctx->sms, ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  return KIOPS_OK;
+}
+
+kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, double t0, double t1, int64_t nsteps,
+                             double tol, int m_init, double* u, kiops_integrate_stats* stats) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  kiops_k::PdeDev P;
+  kiops_status st = pde_dev(ctx, pde, P);
+  if (st) return st;
+  if (scheme < KIOPS_EPIRK4S3 || scheme > KIOPS_EXPRB5S3) return fail(ctx, KIOPS_EINVAL, "unknown scheme %d", scheme);
+  if (!u) return fail(ctx, KIOPS_EINVAL, "NULL u");
+  if (!(t1 > t0) || !std::isfinite(t0) || !std::isfinite(t1) || nsteps < 1)
+    return fail(ctx, KIOPS_EINVAL, "need t1 > t0 (finite) and nsteps >= 1");
+  if (!(tol > 0.0) || m_init < 1) return fail(ctx, KIOPS_EINVAL, "tol must be > 0 and m_init >= 1");
+  // stage nodes (increasing, as Task I wants them) and the b_3, b_4 weights: eqs 50, 51, 53 (eq 11 grouping)
+  double c2, c3;
+  kiops_k::SchemeDev S{};
+  if (scheme == KIOPS_EPIRK4S3) {
+    c2 = 1.0 / 8.0;
+    c3 = 1.0 / 9.0;
+    S = {1892.0, 1458.0, -42336.0, -34992.0, -2.0};
+  } else if (scheme == KIOPS_EPIRK4S3A) {
+    c2 = 0.5;
+    c3 = 2.0 / 3.0;
+    S = {32.0, -13.5, -144.0, 81.0, 0.0};
+  } else {
+    c2 = 0.5;
+    c3 = 0.9;
+    S = {18.0, -250.0 / 81.0, -60.0, 500.0 / 27.0, 0.0};
+  }
+  const double nodes[2] = {std::min(c2, c3), std::max(c2, c3)};
+  const int64_t npts = P.n * P.n, N = npts * P.ns;
+  // workspace: zero, hf, W[2], U2, U3, b3, b4, Z[2], w, h r2 (N each), coupling fields (4 x npts)
+  const size_t need = (size_t)(12 * N + 4 * npts) * sizeof(double);
+  if (need > ctx->integ_bytes) {
+    if (ctx->integ) cudaFree(ctx->integ);
+    ctx->integ = nullptr;
+    ctx->integ_bytes = 0;
+    KCHECK(ctx, cudaMalloc((void**)&ctx->integ, need));
+    ctx->integ_bytes = need;
+  }
+  double* base = ctx->integ;
+  double *zero = base, *hf = base + N, *U2 = base + 4 * N, *U3 = base + 5 * N;
+  double* W[2] = {base + 2 * N, base + 3 * N};
+  double *b3 = base + 6 * N, *b4 = base + 7 * N, *w = base + 10 * N, *hr2 = base + 11 * N;
+  double* Z[2] = {base + 8 * N, base + 9 * N};
+  double* fields[4] = {base + 12 * N, base + 12 * N + npts, base + 12 * N + 2 * npts, base + 12 * N + 3 * npts};
+  KCHECK(ctx, cudaMemsetAsync(zero, 0, (size_t)N * sizeof(double), ctx->stream));
+  // A = h J_n: the stencil part scaled by h, the coupling fields h dR(u_n) (rewritten every step)
+  const double h = (t1 - t0) / (double)nsteps;
+  kiops_stencil2d_desc d;
+  std::memset(&d, 0, sizeof(d));
+  d.nx = d.ny = P.n;
+  d.nspecies = P.ns;
+  d.bc = P.bc;
+  const double idx2 = 1.0 / (P.dx * P.dx);
+  for (int sp = 0; sp < P.ns; ++sp) {
+    double dd, aa = 0.0;
+    if (P.kind == KIOPS_PDE_ADR2D) {
+      dd = P.prm[0] * idx2;
+      aa = P.prm[1] / (2.0 * P.dx);
+    } else {
+      dd = P.prm[sp] * idx2;
+    }
+    const double cf[5] = {-4.0 * dd, dd + aa, dd - aa, dd + aa, dd - aa};
+    for (int k = 0; k < 5; ++k) d.coef[sp][k] = h * cf[k];
+  }
+  d.diag[0][0] = fields[0];
+  if (P.ns == 2) {
+    d.diag[0][1] = fields[1];
+    d.diag[1][0] = fields[2];
+    d.diag[1][1] = fields[3];
+  }
+  kiops_op* A = nullptr;
+  st = kiops_op_stencil2d(ctx, &A, &d);
+  if (st) return st;
+  std::unique_ptr<kiops_op, kiops_status (*)(kiops_op*)> A_guard(A, kiops_op_destroy);
+  int m_slot[3] = {m_init, m_init, m_init};
+  auto tally = [&](const kiops_stats& s, int slot) {
+    m_slot[slot] = s.m_last;
+    if (stats) {
+      stats->kiops_calls += 1;
+      stats->matvecs += s.matvecs;
+      stats->substeps += s.substeps;
+      stats->rejected += s.rejected;
+      stats->m_last[slot] = s.m_last;
+    }
+  };
+  for (int64_t n = 0; n < nsteps; ++n) {
+    // h f(u_n) and the fields of A = h J_n
+    KCHECK(ctx, kiops_k::launch_pde_eval(P, u, h, hf, fields, ctx->sms, ctx->stream));
+    // Task I: phi_1(c A) h f(u_n) at both nodes
+    {
+      const double* bb[2] = {zero, hf};
+      double* const ww[2] = {W[0], W[1]};
+      kiops_stats s1{};
+      st = kiops_solve_task1(ctx, A, nodes, 2, 1, bb, tol, m_slot[0], 2, KIOPS_FP64, ww, &s1);
+      if (st) return st;
+      tally(s1, 0);
+    }
+    const double* W2 = c2 == nodes[0] ? W[0] : W[1];
+    const double* W3 = c3 == nodes[0] ? W[0] : W[1];
+    KCHECK(ctx, kiops_k::launch_stages(N, u, W2, c2, W3, c3, U2, U3, ctx->sms, ctx->stream));
+    if (scheme == KIOPS_EXPRB5S3) {
+      // Task I: phi_3(c A) h r(U_n2) at c = 1/2, 9/10; U_n3 += 27/25 Z(1/2) + 729/125 Z(9/10)
+      KCHECK(ctx, kiops_k::launch_remainder(P, u, U2, h, hr2, ctx->sms, ctx->stream));
+      const double* bb[4] = {zero, zero, zero, hr2};
+      double* const zz[2] = {Z[0], Z[1]};
+      kiops_stats s2{};
+      st = kiops_solve_task1(ctx, A, nodes, 2, 3, bb, tol, m_slot[1], 2, KIOPS_FP64, zz, &s2);
+      if (st) return st;
+      tally(s2, 1);
+      KCHECK(ctx, kiops_k::launch_axpy2(N, U3, 27.0 / 25.0, Z[0], 729.0 / 125.0, Z[1], ctx->sms, ctx->stream));
+    }
+    // b_3, b_4 from r(U_n2), r(U_n3); Task II (eq 10, tau = 1) gives u_{n+1} - u_n
+    KCHECK(ctx, kiops_k::launch_assemble(P, u, U2, U3, h, S, b3, b4, ctx->sms, ctx->stream));
+    {
+      const double* bb[5] = {zero, hf, zero, b3, b4};
+      kiops_stats s3{};
+      st = kiops_solve(ctx, A, 1.0, 4, bb, tol, m_slot[2], 2, KIOPS_FP64, w, &s3);
+      if (st) return st;
+      tally(s3, 2);
+    }
+    KCHECK(ctx, kiops_k::launch_axpy2(N, u, 1.0, w, 0.0, nullptr, ctx->sms, ctx->stream));
+    if (stats) stats->steps = n + 1;
+  }
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
   return KIOPS_OK;
 }
 

@@ -22,7 +22,10 @@
 
 namespace kiops_dev {
 
-constexpr int kThreads = 256;
+#ifndef KIOPS_THREADS
+#define KIOPS_THREADS 256
+#endif
+constexpr int kThreads = KIOPS_THREADS;  // threads per block (256 or 512)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxM = 256;                 // largest m_max
 constexpr int kMaxN = kMaxM + 1;           // largest exponential size n = j + 1
@@ -47,7 +50,7 @@ struct OpDesc {
   const double* vals;
   int64_t nx, ny, nz;
   int nspecies;
-  int periodic;
+  int bc;                    // 0 homogeneous Dirichlet, 1 periodic, 2 homogeneous Neumann (reflection)
   double coef[2][7];
   const double* diag[2][2];
 };
@@ -367,16 +370,21 @@ __device__ __forceinline__ bool finish_reduce_hook(Team& team, Ctl& c, double* p
 // ------------------------------------------------------------------------------------------------
 // Operators: row r of A x (matrix-free; Algorithm 2 lines 4-6 apply A to the first N entries).
 // ------------------------------------------------------------------------------------------------
+// Index just outside [0, n) under the operator's boundary rule; returns -1 where the value is 0.
+__device__ __forceinline__ int64_t bc_index(int bc, int64_t i, int64_t n) {
+  if (i >= 0 && i < n) return i;
+  if (bc == 1) return i < 0 ? i + n : i - n;
+  if (bc == 2) return i < 0 ? -i : 2 * (n - 1) - i;
+  return -1;
+}
+
 template <typename T>
 __device__ __forceinline__ T st_val(const OpDesc& op, const T* x, int s, int64_t ix, int64_t iy, int64_t iz,
                                     int64_t nz) {
-  if (op.periodic) {
-    ix = ix < 0 ? ix + op.nx : (ix >= op.nx ? ix - op.nx : ix);
-    iy = iy < 0 ? iy + op.ny : (iy >= op.ny ? iy - op.ny : iy);
-    iz = iz < 0 ? iz + nz : (iz >= nz ? iz - nz : iz);
-  } else if (ix < 0 || ix >= op.nx || iy < 0 || iy >= op.ny || iz < 0 || iz >= nz) {
-    return T(0);
-  }
+  ix = bc_index(op.bc, ix, op.nx);
+  iy = bc_index(op.bc, iy, op.ny);
+  iz = bc_index(op.bc, iz, nz);
+  if (ix < 0 || iy < 0 || iz < 0) return T(0);
   return x[(int64_t)s * op.nx * op.ny * nz + (iz * op.ny + iy) * op.nx + ix];
 }
 
@@ -498,11 +506,16 @@ __device__ __forceinline__ T apply_row_fast(const SolveArgs& a, const T* __restr
     const uint32_t iy = pt / nx, ix = pt - iy * nx;
     const T* xs = x + (size_t)sp * npts;
     T w, e, so, no;
-    if (op.periodic) {
+    if (op.bc == 1) {
       w = xs[ix == 0 ? pt + nx - 1 : pt - 1];
       e = xs[ix + 1 == nx ? pt + 1 - nx : pt + 1];
       so = xs[iy == 0 ? pt + npts - nx : pt - nx];
       no = xs[iy + 1 == ny ? pt + nx - npts : pt + nx];
+    } else if (op.bc == 2) {  // reflection: the missing neighbour is the opposite one
+      w = xs[ix == 0 ? pt + 1 : pt - 1];
+      e = xs[ix + 1 == nx ? pt - 1 : pt + 1];
+      so = xs[iy == 0 ? pt + nx : pt - nx];
+      no = xs[iy + 1 == ny ? pt - nx : pt + nx];
     } else {
       w = ix > 0 ? xs[pt - 1] : T(0);
       e = ix + 1 < nx ? xs[pt + 1] : T(0);
@@ -523,7 +536,14 @@ __device__ __forceinline__ T apply_row_fast(const SolveArgs& a, const T* __restr
     const uint32_t iz = r / nxy, rem = r - iz * nxy;
     const uint32_t iy = rem / nx, ix = rem - iy * nx;
     T xm, xp, ym, yp, zm, zp;
-    if (op.periodic) {
+    if (op.bc == 2) {
+      xm = x[ix == 0 ? r + 1 : r - 1];
+      xp = x[ix + 1 == nx ? r - 1 : r + 1];
+      ym = x[iy == 0 ? r + nx : r - nx];
+      yp = x[iy + 1 == ny ? r - nx : r + nx];
+      zm = x[iz == 0 ? r + nxy : r - nxy];
+      zp = x[iz + 1 == nz ? r - nxy : r + nxy];
+    } else if (op.bc == 1) {
       xm = x[ix == 0 ? r + nx - 1 : r - 1];
       xp = x[ix + 1 == nx ? r + 1 - nx : r + 1];
       ym = x[iy == 0 ? r + nxy - nx : r - nx];
@@ -587,7 +607,9 @@ static __device__ __noinline__ void mm_team(const double* A, Band bA, const doub
                         const Ctl& c, const MmEpi& epi, double* sA, double* sB) {
   const Band bC = band_product(bA, bB, n);
   const int nt = (n + kTile - 1) / kTile;
-  const int out = threadIdx.x >> 2, part = threadIdx.x & 3;
+  constexpr int kParts = kThreads / (kTile * kTile);  // threads per output entry (inner-range stripes)
+  static_assert(kParts * kTile * kTile == kThreads && kParts <= 32 && (kParts & (kParts - 1)) == 0, "tile map");
+  const int out = threadIdx.x / kParts, part = threadIdx.x % kParts;
   const int ti_l = out / kTile, tk_l = out % kTile;
   for (int tile = rank; tile < nt * nt; tile += size) {
     const int ti = tile / nt, tk = tile - ti * nt;
@@ -619,16 +641,16 @@ static __device__ __noinline__ void mm_team(const double* A, Band bA, const doub
     // four independent chains per thread (FP64 dependent latency is 64 cycles on this GPU)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int l = part;
-    for (; l + 12 < nl; l += 16) {
+    for (; l + 3 * kParts < nl; l += 4 * kParts) {
       s0 = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s0);
-      s1 = fma(sA[ti_l * kMaxN + l + 4], sB[(l + 4) * kTile + tk_l], s1);
-      s2 = fma(sA[ti_l * kMaxN + l + 8], sB[(l + 8) * kTile + tk_l], s2);
-      s3 = fma(sA[ti_l * kMaxN + l + 12], sB[(l + 12) * kTile + tk_l], s3);
+      s1 = fma(sA[ti_l * kMaxN + l + kParts], sB[(l + kParts) * kTile + tk_l], s1);
+      s2 = fma(sA[ti_l * kMaxN + l + 2 * kParts], sB[(l + 2 * kParts) * kTile + tk_l], s2);
+      s3 = fma(sA[ti_l * kMaxN + l + 3 * kParts], sB[(l + 3 * kParts) * kTile + tk_l], s3);
     }
-    for (; l < nl; l += 4) s0 = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s0);
+    for (; l < nl; l += kParts) s0 = fma(sA[ti_l * kMaxN + l], sB[l * kTile + tk_l], s0);
     double s = (s0 + s1) + (s2 + s3);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
+#pragma unroll
+    for (int o = 1; o < kParts; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (part == 0 && row < n && col < n) {
       double e = 0.0;
       if (epi.nterms > 0) {
@@ -692,7 +714,7 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
       T* cache = (T*)(smem + a.sm_cache);
       const bool cfill = a.cache_on && !c.cache_ok;
       const int E = ns * tw * th;
-      // halo point e -> 2 r + (1 if the point is this block's own), ~0u outside a non-periodic grid
+      // halo point e -> 2 r + (1 if the point is this block's own), ~0u outside a Dirichlet grid
       unsigned* tbl = (unsigned*)(smem + a.sm_tbl);
       const bool tok = a.stage_on && c.tbl_ok;
       auto rslot = [&](int k) -> const T* { return ring + (size_t)((k - 1) % nr) * rstride; };
@@ -703,7 +725,8 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
       const T* g1 = rf1 ? rslot(c.fin_i0 + 1) : nullptr;
       const T* g2 = rf2 ? rslot(c.fin_i0 + 2) : nullptr;
       // finalisation over tile + halo; TOK: the index table is filled (no index arithmetic)
-      const bool wtbl = a.stage_on, periodic = op.periodic;  // (the argument block is in shared memory)
+      const bool wtbl = a.stage_on;  // (the argument block is in shared memory)
+      const int bc = op.bc;
       auto finalize = [&](auto tok_tag) {
         constexpr bool TOK = decltype(tok_tag)::value;
         for (int e = tid; e < ns * plane; e += kThreads) {
@@ -713,13 +736,9 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
           } else {
             const int sp = e / plane, rem = e - sp * plane, hy = rem / hw, hx = rem - hy * hw;
             int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-            bool inside = true;
-            if (periodic) {
-              gx = gx < 0 ? gx + (int)nx : (gx >= (int)nx ? gx - (int)nx : gx);
-              gy = gy < 0 ? gy + (int)ny : (gy >= (int)ny ? gy - (int)ny : gy);
-            } else if (gx < 0 || gx >= (int)nx || gy < 0 || gy >= (int)ny) {
-              inside = false;
-            }
+            gx = (int)bc_index(bc, gx, nx);
+            gy = (int)bc_index(bc, gy, ny);
+            const bool inside = gx >= 0 && gy >= 0;
             const unsigned own = (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) ? 1u : 0u;
             code = inside ? 2u * ((unsigned)sp * npts + (unsigned)gy * nx + (unsigned)gx) + own : ~0u;
             if (wtbl) tbl[e] = code;

@@ -1,6 +1,9 @@
 // Entry points of the kernel translation units (each compiled on its own, in parallel).
 #pragma once
 
+#include <cstdint>
+#include <cuda_runtime.h>
+
 namespace kiops_k {
 void* solve_kernel_f64(int kind);   // grid engine, FP64 basis
 void* solve_kernel_f32(int kind);   // grid engine, FP32 basis
@@ -8,4 +11,28 @@ void* team_kernel_f64(int kind);    // batch team engine, FP64 basis
 void* team_kernel_f32(int kind);    // batch team engine, FP32 basis
 void* noalloc_kernel(int kind);     // single block, argument block by value (FP64)
 void* server_kernel();              // persistent serving kernel (every kind and precision)
+
+// Integrators (kiops_integrate.cu).  A test problem of section 4 on an n x n grid.
+struct PdeDev {
+  int kind;       // 0: 2D ADR (Neumann), 1: 2D Gray-Scott (periodic)
+  int ns;         // species
+  int bc;         // 1 periodic, 2 Neumann (reflection)
+  int64_t n;      // points per dimension
+  double dx;      // grid spacing
+  double prm[4];  // ADR: eps, alpha, gamma; Gray-Scott: d_u, d_v, a, b
+};
+// Weights of r2 and r3 in b_3 and b_4: b_k = h (x_k r2 + y_k (r3 + z r2)).
+struct SchemeDev {
+  double x3, y3, x4, y4, z;
+};
+cudaError_t launch_pde_eval(const PdeDev& P, const double* u, double h, double* hf, double* const fields[4], int sms,
+                            cudaStream_t st);
+cudaError_t launch_stages(int64_t N, const double* u, const double* W2, double c2, const double* W3, double c3,
+                          double* U2, double* U3, int sms, cudaStream_t st);
+cudaError_t launch_remainder(const PdeDev& P, const double* un, const double* U, double h, double* out, int sms,
+                             cudaStream_t st);
+cudaError_t launch_assemble(const PdeDev& P, const double* un, const double* U2, const double* U3, double h,
+                            const SchemeDev& S, double* b3, double* b4, int sms, cudaStream_t st);
+cudaError_t launch_axpy2(int64_t N, double* y, double a1, const double* x1, double a2, const double* x2, int sms,
+                         cudaStream_t st);
 }  // namespace kiops_k

@@ -55,13 +55,24 @@ class kiops_trace_rec(C.Structure):
                 ("omega", C.c_double), ("tau_new", C.c_double)]
 
 
+BC_DIRICHLET, BC_PERIODIC, BC_NEUMANN = 0, 1, 2
+
+
+def bc_code(desc: dict) -> int:
+    """KIOPS_BC_* of a stencil description: desc["bc"] in {"dirichlet", "periodic", "neumann"}, else the
+    boolean desc["periodic"]."""
+    if desc.get("bc") is not None:
+        return {"dirichlet": BC_DIRICHLET, "periodic": BC_PERIODIC, "neumann": BC_NEUMANN}[desc["bc"]]
+    return BC_PERIODIC if desc.get("periodic") else BC_DIRICHLET
+
+
 class kiops_stencil2d_desc(C.Structure):
-    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nspecies", C.c_int), ("periodic", C.c_int),
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nspecies", C.c_int), ("bc", C.c_int),
                 ("coef", (C.c_double * 5) * 2), ("diag", (C.c_void_p * 2) * 2)]
 
 
 class kiops_stencil3d_desc(C.Structure):
-    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("periodic", C.c_int),
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("bc", C.c_int),
                 ("coef", C.c_double * 7), ("diag", C.c_void_p)]
 
 
@@ -74,6 +85,41 @@ class kiops_server_config(C.Structure):
 class kiops_request(C.Structure):
     _fields_ = [("A", C.c_void_p), ("tau", C.c_double), ("p", C.c_int), ("b", C.POINTER(C.c_void_p)),
                 ("tol", C.c_double), ("m_init", C.c_int), ("m_o", C.c_int), ("prec", C.c_int), ("w", C.c_void_p)]
+
+
+class kiops_pde(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int64), ("param", C.c_double * 4)]
+
+
+class kiops_integrate_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("kiops_calls", C.c_int64), ("matvecs", C.c_int64), ("substeps", C.c_int64),
+                ("rejected", C.c_int64), ("m_last", C.c_int * 3)]
+
+    def as_dict(self) -> dict:
+        return {"steps": self.steps, "kiops_calls": self.kiops_calls, "matvecs": self.matvecs,
+                "substeps": self.substeps, "rejected": self.rejected, "m_last": list(self.m_last)}
+
+
+PDE_ADR2D, PDE_GRAY_SCOTT2D = 0, 1
+SCHEMES = {"epirk4s3": 0, "epirk4s3a": 1, "exprb5s3": 2}
+
+
+def pde_struct(pde: dict) -> kiops_pde:
+    """kiops_pde of a test-problem description {"pde": "adr2d", "n", "eps", "alpha", "gamma"} or
+    {"pde": "gray_scott2d", "n", "du", "dv", "a", "b"}."""
+    d = kiops_pde()
+    d.n = int(pde["n"])
+    if pde["pde"] == "adr2d":
+        d.kind = PDE_ADR2D
+        vals = [pde["eps"], pde["alpha"], pde["gamma"], 0.0]
+    elif pde["pde"] == "gray_scott2d":
+        d.kind = PDE_GRAY_SCOTT2D
+        vals = [pde["du"], pde["dv"], pde["a"], pde["b"]]
+    else:
+        raise ValueError(f"unknown test problem {pde['pde']!r}")
+    for k, v in enumerate(vals):
+        d.param[k] = float(v)
+    return d
 
 
 _lock = threading.Lock()
@@ -115,6 +161,9 @@ _SIGS = {
                            C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p), C.POINTER(kiops_stats)], C.c_int),
     "kiops_solve_noalloc": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
                              C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
+    "kiops_pde_rhs": ([C.c_void_p, C.POINTER(kiops_pde), C.c_void_p, C.c_void_p], C.c_int),
+    "kiops_integrate": ([C.c_void_p, C.POINTER(kiops_pde), C.c_int, C.c_double, C.c_double, C.c_int64, C.c_double,
+                         C.c_int, C.c_void_p, C.POINTER(kiops_integrate_stats)], C.c_int),
 }
 
 
@@ -252,6 +301,18 @@ def kiops_solve_batch(ctx, reqs: list[kiops_request]) -> list[dict]:
     return [stats[i].as_dict() for i in range(n)]
 
 
+def kiops_pde_rhs(ctx, pde: kiops_pde, u_ptr, f_ptr) -> None:
+    _check(ctx, lib().kiops_pde_rhs(ctx, C.byref(pde), u_ptr, f_ptr), "kiops_pde_rhs")
+
+
+def kiops_integrate(ctx, pde: kiops_pde, scheme: int, t0: float, t1: float, nsteps: int, tol: float, m_init: int,
+                    u_ptr) -> dict:
+    st = kiops_integrate_stats()
+    _check(ctx, lib().kiops_integrate(ctx, C.byref(pde), scheme, t0, t1, nsteps, tol, m_init, u_ptr, C.byref(st)),
+           "kiops_integrate")
+    return st.as_dict()
+
+
 def kiops_solve_noalloc(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, w_ptr) -> dict:
     """The allocation-free solve (FP64, one thread block, fixed device scratch); see include/kiops.h."""
     st = kiops_stats()
@@ -335,7 +396,7 @@ class Operator:
                                        put(desc["colind"], torch.int32), put(desc["vals"], torch.float64))
         elif k == "stencil2d":
             d = kiops_stencil2d_desc()
-            d.nx, d.ny, d.nspecies, d.periodic = int(desc["nx"]), int(desc["ny"]), int(desc["nspecies"]), int(bool(desc["periodic"]))
+            d.nx, d.ny, d.nspecies, d.bc = int(desc["nx"]), int(desc["ny"]), int(desc["nspecies"]), bc_code(desc)
             for s in range(d.nspecies):
                 for c in range(5):
                     d.coef[s][c] = float(desc["coef"][s][c])
@@ -345,7 +406,7 @@ class Operator:
             self.handle = kiops_op_stencil2d(ctx, d)
         elif k == "stencil3d":
             d = kiops_stencil3d_desc()
-            d.nx, d.ny, d.nz, d.periodic = int(desc["nx"]), int(desc["ny"]), int(desc["nz"]), int(bool(desc["periodic"]))
+            d.nx, d.ny, d.nz, d.bc = int(desc["nx"]), int(desc["ny"]), int(desc["nz"]), bc_code(desc)
             for c in range(7):
                 d.coef[c] = float(desc["coef"][c])
             d.diag = put(desc["diag"], torch.float64) if desc.get("diag") is not None else None
@@ -484,6 +545,22 @@ class Solver:
 
     def server_stop(self) -> None:
         kiops_server_stop(self.ctx)
+
+    # ---- exponential integrators on the section 4 test problems
+    def pde_rhs(self, pde: dict, u):
+        """f(u) of the test problem (u: CUDA float64 tensor of N values)."""
+        import torch
+        u = u.contiguous()
+        f = torch.empty_like(u)
+        kiops_pde_rhs(self.ctx, pde_struct(pde), u.data_ptr(), f.data_ptr())
+        return f
+
+    def integrate(self, pde: dict, scheme: str, u, t0: float, t1: float, nsteps: int, tol: float = 1e-10,
+                  m_init: int = 10):
+        """Integrate in place (u: contiguous CUDA float64 tensor) from t0 to t1 in nsteps steps of the
+        scheme ("epirk4s3", "epirk4s3a", "exprb5s3"); returns the statistics."""
+        assert u.is_contiguous() and u.dtype.is_floating_point and u.element_size() == 8
+        return kiops_integrate(self.ctx, pde_struct(pde), SCHEMES[scheme], t0, t1, nsteps, tol, m_init, u.data_ptr())
 
     def expm(self, a):
         import torch
