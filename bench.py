@@ -268,6 +268,35 @@ def measure_patterns(dev):
         "note": "half the requests FP32 basis (tol 1e-6), half FP64 (tol 1e-10); latency = completion - arrival"}
     srv.close()
     seq.close()
+
+    # integrators (section 4): the paper's 400 x 400 ADR problem over t in [0, 0.1], h = 0.0025 (40 steps)
+    integ = kiops.Solver(device=dev.index)
+    pde = W.pde_adr2d(400)
+    u0 = torch.as_tensor(W.pde_initial_condition(pde), device=dev)
+    res = {}
+    for scheme in ("epirk4s3", "epirk4s3a", "exprb5s3"):
+        u = u0.clone()
+        integ.integrate(pde, scheme, u, 0.0, 0.0025, 1, 1e-10)  # warm-up (one step)
+        u = u0.clone()
+        t, st = timed(lambda: integ.integrate(pde, scheme, u, 0.0, 0.1, 40, 1e-10))
+        res[scheme] = {"ms": 1e3 * t, "steps_per_s": 40 / t, "phi_solves_per_s": st["kiops_calls"] / t,
+                       "kiops_calls": st["kiops_calls"], "matvecs": st["matvecs"]}
+    out["integrators_adr2d_400"] = {"t_end": 0.1, "steps": 40, "tol": 1e-10, **res}
+    integ.close()
+
+    # m_o sweep (section 3.3): incomplete orthogonalisation lengths up to full Arnoldi on the 512^2 ADR solve
+    sw = kiops.Solver(device=dev.index)
+    P = W.problem_adr2d()
+    op = sw.operator(P.op)
+    b = torch.as_tensor(P.b, device=dev)
+    sweep = {}
+    for m_o in (1, 2, 3, 4, 8, 129):
+        sw.solve(op, P.tau, b, P.tol, m_o=m_o)
+        t, (w, st) = timed(lambda: sw.solve(op, P.tau, b, P.tol, m_o=m_o))
+        sweep[str(m_o)] = {"ms": 1e3 * t, "matvecs": st["matvecs"], "substeps": st["substeps"],
+                           "rejected": st["rejected"], "status": st["status"]}
+    out["m_o_sweep_adr2d_512"] = {"note": "129 = full Arnoldi (m_max = 128)", **sweep}
+    sw.close()
     return out
 
 

@@ -81,6 +81,14 @@ typedef struct {
                               the cross-block sum, 4 = the tile's B columns and coupling fields; -1 (default) =
                               automatic.  A combination that would lower the co-resident block count is
                               dropped.  Results are bit-identical for every value. */
+  int scenario;            /* 0 (default): Algorithm 4 chooses the next m and tau.  1: after an iteration in
+                              Algorithm 4's vary-m branch the cheaper of the two scenarios of section 3.2 is
+                              taken, by the cost of eq 40 with eqs 41-42: A keeps m and takes tau from eq 44
+                              (gamma 0.9 after an accepted, 0.6 after a rejected iteration), B keeps tau and
+                              takes m from eq 46 (ties keep B).  nz(A~) counts the operator's stored nonzeros
+                              (CSR nnz; 5 or 7 per unknown for stencils plus one per unknown and coupling
+                              field); N_mult is the multiplication count of Higham's scaling-and-squaring Pade
+                              method for the 1-norm of tau H~.  Both costs are in every trace record. */
 } kiops_config;
 
 typedef struct {
@@ -106,8 +114,10 @@ typedef struct {
   int j;                   /* Krylov dimension of the iteration */
   int accepted;
   int breakdown;
-  int m_new;               /* Algorithm 4 suggestion */
+  int m_new;               /* Algorithm 4 suggestion (or the cost model's, cfg.scenario = 1) */
   double tau, t_now, eps, omega, tau_new;
+  double cost_a, cost_b;   /* eq 40 for scenario A (keep m, tau from eq 44) and B (keep tau, m from eq 46); see
+                              kiops_config.scenario; 0 on breakdown or when no interval is left */
 } kiops_trace_rec;
 
 typedef struct kiops_ctx kiops_ctx;

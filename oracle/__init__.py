@@ -64,13 +64,13 @@ class _Op(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("m_min", C.c_int), ("m_max", C.c_int), ("m_o", C.c_int), ("normalize", C.c_int),
                 ("breakdown_tol", C.c_double), ("max_substeps", C.c_int64), ("max_iterations", C.c_int64),
-                ("literal_last_row", C.c_int)]
+                ("literal_last_row", C.c_int), ("scenario", C.c_int)]
 
 
 class _Trace(C.Structure):
     _fields_ = [("substep", C.c_int64), ("j", C.c_int), ("tau", C.c_double), ("t_now", C.c_double),
                 ("eps", C.c_double), ("omega", C.c_double), ("accepted", C.c_int), ("breakdown", C.c_int),
-                ("m_new", C.c_int), ("tau_new", C.c_double)]
+                ("m_new", C.c_int), ("tau_new", C.c_double), ("cost_a", C.c_double), ("cost_b", C.c_double)]
 
 
 def _load():
@@ -193,18 +193,22 @@ def iop(op: dict, b: np.ndarray, v: np.ndarray, m: int, m_o: int = 2, breakdown_
 
 def kiops(op: dict, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_min: int = 10, m_max: int = 128,
           m_o: int = 2, normalize: bool = True, breakdown_tol: float = 1e-12, max_substeps: int = 10**6,
-          max_iterations: int = 10**7, literal_last_row: bool = False, trace_cap: int = 100000):
+          max_iterations: int = 10**7, literal_last_row: bool = False, trace_cap: int = 100000,
+          scenario: int = 0):
     """Algorithm 1 (Task II).  b has shape (p+1, N) in natural order b_0..b_p.
 
     Returns (w, stats, trace): stats = dict(substeps, rejected, matvecs, m_last, iterations, status),
-    trace = list of per-iteration dicts (j, tau, t_now, eps, omega, accepted, breakdown, m_new, tau_new).
+    trace = list of per-iteration dicts (j, tau, t_now, eps, omega, accepted, breakdown, m_new, tau_new, and
+    the eq 40 costs cost_a / cost_b of the two scenarios).  scenario = 1 lets the cheaper scenario replace
+    Algorithm 4's change of m (reading R9 of the C source).
     """
     lib = _load()
     s, keep = _make_op(op)
     b = np.ascontiguousarray(b, dtype=np.float64)
     p = b.shape[0] - 1
     n = b.shape[1]
-    o = _Opts(m_min, m_max, m_o, int(normalize), breakdown_tol, max_substeps, max_iterations, int(literal_last_row))
+    o = _Opts(m_min, m_max, m_o, int(normalize), breakdown_tol, max_substeps, max_iterations, int(literal_last_row),
+              int(scenario))
     w = np.empty(n)
     st = np.zeros(5, dtype=np.int64)
     tr = (_Trace * max(trace_cap, 1))()
@@ -214,7 +218,8 @@ def kiops(op: dict, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_m
     stats = dict(substeps=int(st[0]), rejected=int(st[1]), matvecs=int(st[2]), m_last=int(st[3]),
                  iterations=int(st[4]), status=int(rc))
     trace = [dict(substep=t.substep, j=t.j, tau=t.tau, t_now=t.t_now, eps=t.eps, omega=t.omega,
-                  accepted=bool(t.accepted), breakdown=bool(t.breakdown), m_new=t.m_new, tau_new=t.tau_new)
+                  accepted=bool(t.accepted), breakdown=bool(t.breakdown), m_new=t.m_new, tau_new=t.tau_new,
+                  cost_a=t.cost_a, cost_b=t.cost_b)
              for t in tr[: tl.value]]
     return w, stats, trace
 
@@ -230,7 +235,7 @@ def kiops_task1(op: dict, T, b: np.ndarray, tol: float, m_init: int = 10, m_min:
     p = b.shape[0] - 1
     n = b.shape[1]
     T = np.ascontiguousarray(T, dtype=np.float64)
-    o = _Opts(m_min, m_max, m_o, int(normalize), breakdown_tol, max_substeps, max_iterations, 0)
+    o = _Opts(m_min, m_max, m_o, int(normalize), breakdown_tol, max_substeps, max_iterations, 0, 0)
     W = np.empty((len(T), n))
     st = np.zeros(5, dtype=np.int64)
     tr = (_Trace * 1)()

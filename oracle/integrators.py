@@ -30,37 +30,16 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from paper_1804_05126_gb300 import workloads as WL
 
 SCHEMES = ("epirk4s3", "epirk4s3a", "exprb5s3")
 
 
 # ----------------------------------------------------------------------------------- test problems
-def adr2d(n: int, eps: float = 0.01, alpha: float = -10.0, gamma: float = 100.0) -> dict:
-    """The 2D ADR problem of section 4 on an n x n vertex grid with homogeneous Neumann boundaries."""
-    return {"pde": "adr2d", "n": n, "ns": 1, "bc": "neumann", "dx": 1.0 / (n - 1),
-            "eps": eps, "alpha": alpha, "gamma": gamma}
-
-
-def gray_scott2d(n: int, du: float = 0.2, dv: float = 0.1, a: float = 0.04, b: float = 0.06) -> dict:
-    """The 2D Gray-Scott problem of section 4 on the periodic n x n grid x = i/n."""
-    return {"pde": "gray_scott2d", "n": n, "ns": 2, "bc": "periodic", "dx": 1.0 / n,
-            "du": du, "dv": dv, "a": a, "b": b}
-
-
-def grid(pde: dict):
-    n = pde["n"]
-    x = np.arange(n) * pde["dx"]
-    return np.meshgrid(x, x, indexing="xy")  # X[iy, ix] = x_ix, Y[iy, ix] = y_iy
-
-
-def initial_condition(pde: dict) -> np.ndarray:
-    """Initial data of section 4 (species-blocked, x fastest)."""
-    X, Y = grid(pde)
-    if pde["pde"] == "adr2d":
-        return (256.0 * (X * Y * (1 - X) * (1 - Y)) ** 2 + 0.3).ravel()
-    u = 1.0 - np.exp(-150.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2))
-    v = np.exp(-150.0 * ((X - 0.5) ** 2 + 2.0 * (Y - 0.5) ** 2))
-    return np.concatenate([u.ravel(), v.ravel()])
+# The problem descriptions and initial data are inputs, shared with the CUDA path's callers.
+adr2d = WL.pde_adr2d
+gray_scott2d = WL.pde_gray_scott2d
+initial_condition = WL.pde_initial_condition
 
 
 def _neighbours(pde: dict, z: np.ndarray):

@@ -31,6 +31,16 @@
  *   R6  happy breakdown when ||x|| <= breakdown_tol * ||A~ v_j|| (Algorithm 2 line 12).
  *   R7  ||B||_1 is the matrix 1-norm (largest column sum); nu = mu = 1 when it is 0 or p = 0.
  *   R8  Task I: the intermediate outputs of Algorithm 3 line 15 use beta (line 14) as their scale.
+ *   R9  Cost model (eqs 40-42), evaluated after every iteration that did not break down.  Scenario A
+ *       keeps m and takes tau_A from eq 44 (gamma = 0.9 after an accepted iteration, 0.6 after a
+ *       rejected one, clipped as in Algorithm 4 lines 9-16); scenario B keeps tau and takes m_B from
+ *       eq 46 as in R4.  t_end - t_now is the remaining interval of R5 (cost 0 when none is left).
+ *       nz(A~) in eq 41 counts the operator's stored nonzeros only (the B block is the separate
+ *       (2p-1)N + p term): CSR nnz, 5 (2D) or 7 (3D) per unknown for a stencil plus one per unknown
+ *       and coupling field, n^2 dense.  N_mult in eq 42 is the multiplication count of [47] for a
+ *       matrix of the 1-norm of tau H~ (scaled by tau_A/tau for scenario A): pi_m = 2, 3, 4, 5, 6
+ *       for Pade degrees 3, 5, 7, 9, 13 plus the s squarings.  With opts.scenario = 1 the cheaper
+ *       scenario replaces Algorithm 4's choice in its line 18 branch (ties keep scenario B).
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,6 +74,7 @@ typedef struct {
   int64_t max_substeps;
   int64_t max_iterations;
   int literal_last_row;     /* R1 switch */
+  int scenario;             /* R9: 0 Algorithm 4, 1 the cheaper scenario of eq 40 */
 } oracle_opts;
 
 typedef struct {
@@ -73,6 +84,7 @@ typedef struct {
   int accepted, breakdown;
   int m_new;
   double tau_new;
+  double cost_a, cost_b;    /* eq 40 for scenario A (tau_A, m) and B (tau, m_B) (R9); 0 on breakdown */
 } oracle_trace;
 
 enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2, ORACLE_ENOTCONV = 3 };
@@ -258,6 +270,46 @@ int oracle_expm(int n, const double* a, double* f) {
 }
 
 /* ------------------------------------------------------------------------------------------------
+ * Cost model of section 3.2 (eqs 40-42), reading R9.
+ * ---------------------------------------------------------------------------------------------- */
+static double op_nonzeros(const oracle_op* A) {
+  if (A->kind == 0) return (double)A->rowptr[A->n];
+  if (A->kind == 3) return (double)A->n * (double)A->n;
+  double npts = (double)A->nx * (double)A->ny * (double)(A->kind == 2 ? A->nz : 1);
+  int ns = A->kind == 2 ? 1 : A->nspecies;
+  double nz = (A->kind == 2 ? 7.0 : 5.0) * npts * ns;
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c)
+      if (A->diag[r][c]) nz += npts;
+  return nz;
+}
+
+/* multiplications of the scaling-and-squaring Pade method of [47] for a matrix of 1-norm x */
+static double n_mult(double x) {
+  static const double theta[5] = {1.495585217958292e-2, 2.539398330063230e-1, 9.504178996162932e-1,
+                                  2.097847961257068e0, 5.371920351148152e0};
+  static const double pi_m[5] = {2, 3, 4, 5, 6};
+  for (int d = 0; d < 4; ++d)
+    if (x <= theta[d]) return pi_m[d];
+  int s = x > theta[4] ? ceil_log2(x / theta[4]) : 0;
+  return pi_m[4] + (s > 0 ? s : 0);
+}
+
+static double cost_iop(double m, double N, double p, double nz) { /* eq 41 */
+  return m * ((2.0 * nz + (2.0 * p - 1.0) * N + p) + 8.0 * (N + p)) - 4.0 * (N + p) + 3.0 * (N + p) * m;
+}
+
+static double cost_exp(double nmult, double m, double p) { /* eq 42 */
+  return nmult * (2.0 * (m + p) - 1.0) * (m + p) * (m + p);
+}
+
+/* eq 40: the cost of finishing the remaining interval rem with steps tau and dimension m */
+static double cost_remaining(double rem, double tau, double m, double N, double p, double nz, double nmult) {
+  if (!(rem > 0.0) || !(tau > 0.0)) return 0.0;
+  return ceil(rem / tau) * (cost_iop(m, N, p, nz) + cost_exp(nmult, m, p));
+}
+
+/* ------------------------------------------------------------------------------------------------
  * Augmented matrix-vector product (Algorithm 2 lines 4-6; Theorem 1 with B = [b_p, ..., b_1]).
  * x has N + p entries: x[0:N] the state, x[N+t] (t = 0..p-1) the tail; tail row t pairs with
  * column t of B, which is b_{p-t}.  nu scales B (section 3.7).
@@ -431,6 +483,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
     ht[0 * n + j] = tau * 1.0;
     if (o->literal_last_row)
       for (int c = 1; c <= j; ++c) ht[j * n + (c - 1)] = tau * h[j * ldh + (c - 1)];
+    const double hnorm = norm1(n, ht); /* ||tau H~||_1, for the cost model (R9) */
     if (oracle_expm(n, ht, F) != ORACLE_OK) { rc = ORACLE_ENOTCONV; break; }
 
     /* line 19: eqs 36, 38; line 22: eq 39 */
@@ -486,10 +539,34 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
       m_new = (int)mn;
     }
 
+    /* R9: eq 40 for both scenarios; opts.scenario = 1 takes the cheaper one in the line 18 branch */
+    double cost_a = 0.0, cost_b = 0.0;
+    if (!breakdown) {
+      double tau_a = tau * pow((accepted ? gamma : gamma_max) / omega, 1.0 / qp1);
+      if (accepted && !(tau_a <= 5.0 * tau)) tau_a = 5.0 * tau;
+      if (!(tau_a >= tau / 5.0)) tau_a = tau / 5.0;
+      if (tau_a > remaining) tau_a = remaining;
+      double mb = (double)m + log(omega / gamma) / log(kappa);
+      double lo = floor(0.75 * (double)m), hi = ceil(4.0 * (double)m / 3.0);
+      if (!(mb >= lo)) mb = lo;
+      if (mb > hi) mb = hi;
+      mb = ceil(mb);
+      if (mb < m_min) mb = m_min;
+      if (mb > m_max) mb = m_max;
+      const double nz = op_nonzeros(A);
+      cost_a = cost_remaining(remaining, tau_a, (double)m, (double)N, (double)p, nz, n_mult(hnorm * (tau_a / tau)));
+      cost_b = cost_remaining(remaining, tau, mb, (double)N, (double)p, nz, n_mult(hnorm));
+      if (o->scenario == 1 && j < m_max && cost_a < cost_b) {
+        tau_new = tau_a;
+        m_new = m;
+      }
+    }
+
     if (trace && trace_len && *trace_len < trace_cap) {
       oracle_trace* tr = &trace[*trace_len];
       tr->substep = substeps; tr->j = j; tr->tau = tau; tr->t_now = t_now; tr->eps = eps; tr->omega = omega;
       tr->accepted = accepted; tr->breakdown = breakdown; tr->m_new = m_new; tr->tau_new = tau_new;
+      tr->cost_a = cost_a; tr->cost_b = cost_b;
       *trace_len += 1;
     }
     iters++;

@@ -54,6 +54,7 @@ struct kiops_ctx {
 struct kiops_op {
   kiops_ctx* ctx;
   OpDesc d;
+  double nz = 0.0;  // stored nonzeros (the cost model's nz(A))
 };
 
 namespace {
@@ -312,6 +313,8 @@ kiops_status prepare(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const
   a.tt = ctx->tt;
   a.trace_cap = trace_cap;
   a.prec = prec == KIOPS_FP32_BASIS ? 1 : 0;
+  a.scenario = ctx->cfg.scenario == 1 ? 1 : 0;
+  a.nz_op = A->nz;
   int64_t ldv = 0;
   int64_t df_elems = 0;  // FP32 copies of the coupling fields: nspecies^2 fields of the grid's points
   if (A->d.kind == OP_ST2D) df_elems = (int64_t)A->d.nspecies * A->d.nspecies * A->d.nx * A->d.ny;
@@ -455,6 +458,8 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
       trace[i].eps = tmp[i].eps;
       trace[i].omega = tmp[i].omega;
       trace[i].tau_new = tmp[i].tau_new;
+      trace[i].cost_a = tmp[i].cost_a;
+      trace[i].cost_b = tmp[i].cost_b;
     }
     if (trace_len) *trace_len = n;
   }
@@ -497,6 +502,7 @@ kiops_status kiops_config_default(kiops_config* cfg) {
   cfg->fuse_stencil = 1;
   cfg->batch_team_blocks = 0;
   cfg->fused_smem = -1;
+  cfg->scenario = 0;
   return KIOPS_OK;
 }
 
@@ -606,6 +612,7 @@ kiops_status kiops_op_csr(kiops_ctx* ctx, kiops_op** op, int64_t n, int64_t nnz,
   o->d.rowptr = rowptr;
   o->d.colind = colind;
   o->d.vals = vals;
+  o->nz = (double)nnz;
   *op = o;
   return KIOPS_OK;
 }
@@ -632,6 +639,10 @@ kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
     for (int k = 0; k < 5; ++k) o->d.coef[s][k] = s < d->nspecies ? d->coef[s][k] : 0.0;
     for (int r = 0; r < 2; ++r) o->d.diag[s][r] = (s < d->nspecies && r < d->nspecies) ? d->diag[s][r] : nullptr;
   }
+  o->nz = 5.0 * (double)o->d.n;
+  for (int s = 0; s < 2; ++s)
+    for (int r = 0; r < 2; ++r)
+      if (o->d.diag[s][r]) o->nz += (double)(d->nx * d->ny);
   *op = o;
   return KIOPS_OK;
 }
@@ -657,6 +668,7 @@ kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   o->d.n = d->nx * d->ny * d->nz;
   for (int k = 0; k < 7; ++k) o->d.coef[0][k] = d->coef[k];
   o->d.diag[0][0] = d->diag;
+  o->nz = (double)o->d.n * (d->diag ? 8.0 : 7.0);
   *op = o;
   return KIOPS_OK;
 }

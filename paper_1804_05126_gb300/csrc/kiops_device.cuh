@@ -70,6 +70,7 @@ struct TraceRec {
   int64_t substep;
   int j, accepted, breakdown, m_new;
   double tau, t_now, eps, omega, tau_new;
+  double cost_a, cost_b;
 };
 
 struct SolveArgs {
@@ -100,6 +101,8 @@ struct SolveArgs {
   int64_t* trace_len;
   long long* prof;           // non-NULL: cycles spent per phase, rank 0 view (16 counters)
   TaylorTable tt;
+  int scenario;              // 1: the cheaper scenario of eq 40 replaces Algorithm 4's change of m
+  double nz_op;              // stored nonzeros of A (nz in eq 41)
   // 2D stencils: lagged normalisation on 2D tiles (one barrier per Krylov step), see fused_st2d_phase
   int fused;                 // 1: use the tiled lagged path
   int tile_gx, tile_gy, tile_w, tile_h;
@@ -146,6 +149,28 @@ __device__ __forceinline__ int ceil_log2(double x) {
   int e;
   double f = frexp(x, &e);
   return f == 0.5 ? e - 1 : e;
+}
+
+// Cost model of section 3.2.  Multiplications of Higham's scaling-and-squaring Pade method (the
+// algorithm the paper cites for its exponential) for a matrix of 1-norm x: pi_m = 2, 3, 4, 5, 6 for
+// the degrees 3, 5, 7, 9, 13 chosen by the thresholds theta_m of Higham (2005, Table 2.3), plus the
+// squarings of the degree-13 branch.
+__device__ __forceinline__ double pade_mults(double x) {
+  const double theta[5] = {1.495585217958292e-2, 2.539398330063230e-1, 9.504178996162932e-1, 2.097847961257068e0,
+                           5.371920351148152e0};
+  for (int d = 0; d < 4; ++d)
+    if (x <= theta[d]) return (double)(2 + d);
+  const int s = x > theta[4] ? ceil_log2(x / theta[4]) : 0;
+  return 6.0 + (s > 0 ? s : 0);
+}
+
+// eq 40 with eq 41 (m Krylov steps) and eq 42 (the exponential); 0 when no interval is left.
+__device__ __forceinline__ double scenario_cost(double rem, double tau, double m, double N, double p, double nz,
+                                                double nmult) {
+  if (!(rem > 0.0) || !(tau > 0.0)) return 0.0;
+  const double iop = m * ((2.0 * nz + (2.0 * p - 1.0) * N + p) + 8.0 * (N + p)) - 4.0 * (N + p) + 3.0 * (N + p) * m;
+  const double ex = nmult * (2.0 * (m + p) - 1.0) * (m + p) * (m + p);
+  return ceil(rem / tau) * (iop + ex);
 }
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -221,6 +246,7 @@ struct Ctl {
   double yint[kMaxN];           // Task I: first column of exp(tau~ H_j) for an intermediate output
   double t_sub, tau_sub;        // start time and step of the substep that was just accepted
   int ring_lo;                  // fused path: v_ring_lo .. v_j are in the shared-memory ring
+  double hnorm;                 // ||tau H~||_1 of the last exponential (cost model)
   int pre_j;                    // fused path: the stage holds raw x_{pre_j} (0: nothing staged)
   int cache_ok;                 // fused path: the B / coupling cache is filled
   int tbl_ok;                   // fused path: the halo index table is filled
@@ -918,6 +944,7 @@ __device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, 
       nrm *= aug ? c.tau : scale;
     }
     c.red[0] = nrm;
+    if (aug && !a.expm_only) c.hnorm = nrm;
   }
   __syncthreads();
   if (a.expm_only) {
@@ -1607,10 +1634,34 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         if (mn > a.m_max) mn = a.m_max;
         m_new = (int)mn;
       }
+      // cost model (section 3.2, eqs 40-42) for scenario A (keep m, tau from eq 44) and B (keep tau, m
+      // from eq 46); with a.scenario = 1 the cheaper one replaces the change of m above (ties keep B)
+      double cost_a = 0.0, cost_b = 0.0;
+      if (!c.breakdown) {
+        double tau_a = c.tau * pow((accepted ? gamma : gamma_max) / omega, 1.0 / qp1);
+        if (accepted && !(tau_a <= 5.0 * c.tau)) tau_a = 5.0 * c.tau;
+        if (!(tau_a >= c.tau / 5.0)) tau_a = c.tau / 5.0;
+        if (tau_a > remaining) tau_a = remaining;
+        double mb = (double)c.m + log(omega / gamma) / log(c.kappa);
+        const double lo = floor(0.75 * (double)c.m), hi = ceil(4.0 * (double)c.m / 3.0);
+        if (!(mb >= lo)) mb = lo;
+        if (mb > hi) mb = hi;
+        mb = ceil(mb);
+        if (mb < a.m_min) mb = a.m_min;
+        if (mb > a.m_max) mb = a.m_max;
+        cost_a = scenario_cost(remaining, tau_a, (double)c.m, (double)N, (double)p, a.nz_op,
+                               pade_mults(c.hnorm * (tau_a / c.tau)));
+        cost_b = scenario_cost(remaining, c.tau, mb, (double)N, (double)p, a.nz_op, pade_mults(c.hnorm));
+        if (a.scenario == 1 && j < a.m_max && cost_a < cost_b) {
+          tau_new = tau_a;
+          m_new = c.m;
+        }
+      }
       if (lead && a.trace && *a.trace_len < a.trace_cap) {
         TraceRec& tr = a.trace[*a.trace_len];
         tr.substep = c.substeps; tr.j = j; tr.accepted = accepted; tr.breakdown = c.breakdown; tr.m_new = m_new;
         tr.tau = c.tau; tr.t_now = c.t_now; tr.eps = eps; tr.omega = omega; tr.tau_new = tau_new;
+        tr.cost_a = cost_a; tr.cost_b = cost_b;
         *a.trace_len += 1;
       }
       c.iters += 1;

@@ -7,7 +7,8 @@ them with their own code.
 An operator description is a plain dict:
 
 * ``{"kind": "csr", "n", "rowptr" (int32), "colind" (int32), "vals" (float64)}``
-* ``{"kind": "stencil2d", "nx", "ny", "nspecies" (1|2), "periodic" (bool), "coef" (nspecies x 5:
+* ``{"kind": "stencil2d", "nx", "ny", "nspecies" (1|2), "periodic" (bool) or "bc" ("dirichlet" |
+  "periodic" | "neumann"), "coef" (nspecies x 5:
   centre, -x, +x, -y, +y), "diag" {(r, c): float64 array of nx*ny}}`` — unknowns are species-blocked
   ``[u; v]``, each x-fastest; ``diag[(r, c)]`` couples species c into species r pointwise.
 * ``{"kind": "stencil3d", "nx", "ny", "nz", "periodic", "coef" (7: centre, -x, +x, -y, +y, -z, +z),
@@ -213,3 +214,32 @@ def request_stream(count: int, seed: int = 1005, rate: float = 2000.0, n_range=(
                        precision="fp32_basis" if mixed else "fp64", meta={"n": n, "adv": adv, "shift": shift})
         out.append((t, prob))
     return out
+
+
+# ---------------------------------------------------------------- nonlinear test problems (section 4)
+def pde_adr2d(n: int, eps: float = 0.01, alpha: float = -10.0, gamma: float = 100.0) -> dict:
+    """The 2D advection-diffusion-reaction problem of section 4, u_t = eps Lap u - alpha (u_x + u_y) +
+    gamma u (u - 1/2)(1 - u) on [0,1]^2 with homogeneous Neumann boundaries, on an n x n vertex grid
+    that includes the boundary (spacing 1/(n-1))."""
+    return {"pde": "adr2d", "n": n, "ns": 1, "bc": "neumann", "dx": 1.0 / (n - 1),
+            "eps": eps, "alpha": alpha, "gamma": gamma}
+
+
+def pde_gray_scott2d(n: int, du: float = 0.2, dv: float = 0.1, a: float = 0.04, b: float = 0.06) -> dict:
+    """The 2D Gray-Scott problem of section 4, u_t = d_u Lap u - u v^2 + a (1 - u), v_t = d_v Lap v +
+    u v^2 - (a + b) v, on the periodic unit square with the n x n grid x = i/n."""
+    return {"pde": "gray_scott2d", "n": n, "ns": 2, "bc": "periodic", "dx": 1.0 / n,
+            "du": du, "dv": dv, "a": a, "b": b}
+
+
+def pde_initial_condition(pde: dict) -> np.ndarray:
+    """Initial data of section 4 (species-blocked, x fastest): ADR u = 256 (x y (1-x)(1-y))^2 + 0.3;
+    Gray-Scott u = 1 - exp(-150 ((x-1/2)^2 + (y-1/2)^2)), v = exp(-150 ((x-1/2)^2 + 2 (y-1/2)^2))."""
+    n = pde["n"]
+    x = np.arange(n) * pde["dx"]
+    X, Y = np.meshgrid(x, x, indexing="xy")  # X[iy, ix] = x_ix
+    if pde["pde"] == "adr2d":
+        return (256.0 * (X * Y * (1 - X) * (1 - Y)) ** 2 + 0.3).ravel()
+    u = 1.0 - np.exp(-150.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2))
+    v = np.exp(-150.0 * ((X - 0.5) ** 2 + 2.0 * (Y - 0.5) ** 2))
+    return np.concatenate([u.ravel(), v.ravel()])

@@ -285,3 +285,21 @@ def test_task1_outputs_match_oracle(make, T, m_max):
     assert st["status"] == 0 and st["substeps"] == st_ref["substeps"]
     for l in range(len(T)):
         assert rel(ws[l].cpu().numpy(), Wr[l]) <= 10 * P.tol, l
+
+
+@pytest.mark.parametrize("scenario", [0, 1])
+@pytest.mark.parametrize("make", [W.problem_lap1d, lambda: W.problem_adr2d(n=61, seed=21),
+                                  lambda: W.problem_gray_scott(n=37, seed=6, precision="fp64", tol=1e-8, tau=1.0)])
+def test_cost_model_costs_and_scenario_choice_match_oracle(make, scenario):
+    """Section 3.2: the eq 40 costs of both scenarios in every trace record, and the decisions and result
+    when the cheaper scenario is taken (cfg.scenario = 1), against the oracle."""
+    P = make()
+    s = kiops.Solver(device=0, scenario=scenario)
+    w, st, tr = gpu_solve(s, P, trace=True)
+    s.close()
+    w_ref, st_ref, tr_ref = oracle_solve(P, scenario=scenario)
+    assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"], t["m_new"]) for t in tr] == [(t["j"], t["accepted"], t["m_new"]) for t in tr_ref]
+    for t, r in zip(tr, tr_ref):
+        for k in ("cost_a", "cost_b", "tau_new"):
+            assert t[k] == pytest.approx(r[k], rel=1e-12, abs=0.0), (k, t, r)

@@ -348,3 +348,38 @@ def test_task1_last_time_equals_task2_scaled():
     Wt, _ = oracle.kiops_task1(P.op, T, P.b, P.tol)
     w2, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
     assert rel(Wt[-1], w2 / P.tau**2) < 1e-12
+
+
+# ---------------------------------------------------------------- cost model (section 3.2, eqs 40-42)
+def test_cost_model_prefers_changing_m_as_the_paper_observes():
+    """Section 3.2: keeping tau and changing m (scenario B) is almost always the cheaper completion.  On
+    the 1D Laplacian and the 2D ADR workloads the eq 40 cost of B is at most that of A in every
+    iteration but a few late ones of the long 1D solve (where the m^3 exponential cost dominates)."""
+    for P in (W.problem_lap1d(), W.problem_adr2d(n=64, seed=3)):
+        _, st, tr = oracle.kiops(P.op, P.tau, P.b, P.tol)
+        live = [t for t in tr if not t["breakdown"] and t["cost_a"] > 0]
+        assert live and all(t["cost_a"] > 0 and t["cost_b"] > 0 for t in live)
+        share_b = sum(t["cost_b"] <= t["cost_a"] for t in live) / len(live)
+        assert share_b >= 0.85, (P.name, share_b)
+
+
+def test_cost_model_costs_grow_with_the_krylov_dimension():
+    """Within a substep that keeps rejecting, every scenario-B cost exceeds the previous one (eq 41 is
+    increasing in m, eq 42 in m + p), and A's cost is 0 exactly when nothing is left to integrate."""
+    P = W.problem_lap1d()
+    _, _, tr = oracle.kiops(P.op, P.tau, P.b, P.tol)
+    rej = [t for t in tr if not t["accepted"]]
+    assert len(rej) >= 3
+    assert all(b["cost_b"] > a["cost_b"] for a, b in zip(rej, rej[1:]))
+    last = tr[-1]
+    assert last["accepted"] and last["cost_a"] == 0.0 and last["cost_b"] == 0.0
+
+
+@pytest.mark.parametrize("make", [W.problem_lap1d, lambda: W.problem_adr2d(n=20, seed=4)])
+def test_cost_model_scenario_choice_still_meets_the_tolerance(make):
+    """With the cheaper scenario chosen by eq 40 the solver still returns the phi-combination within its
+    tolerance of the exact dense exponential of the augmented matrix."""
+    P = make()
+    w, st, tr = oracle.kiops(P.op, P.tau, P.b, P.tol, scenario=1)
+    assert st["status"] == 0
+    assert err_ok(w, exact_dense(oracle.dense_matrix(P.op), P.b, P.tau), P.tol)
