@@ -102,9 +102,10 @@ typedef struct {
   int grid_blocks;         /* blocks of the launch */
   int status;              /* kiops_status of the device run */
   double err_est;          /* last error estimate eps_m (eq 36) */
-  /* SM cycles by phase when cfg.profile is set: 0 setup, 1 start vector, 2 step matvec+dots, 3 step
-   * all-reduce, 4 step coefficients, 5 step normalise, 6 expm powers, 7 expm Horner, 8 expm squarings,
-   * 9 control, 10 update; other entries 0. */
+  /* SM cycles by phase when cfg.profile is set (rank-0 view): 0 setup, 1 start vector, 2 step matvec+dots
+   * and block reduction, 3 step cross-block sum, 4 step coefficients, 5 step normalise, 6 expm powers,
+   * 7 expm Horner, 8 expm squarings, 9 control, 10 update, 11 grid barrier waits, 12 tiled path:
+   * finalisation of v_j, 13 tiled path: A~ v_j and dots; other entries 0. */
   int64_t phase_cycles[16];
 } kiops_stats;
 
