@@ -108,6 +108,11 @@ void build_taylor_table(TaylorTable& tt) {
     tt.theta[tt.count] = lo;
     tt.count++;
   }
+  for (int k = 0; k < 64; ++k) {  // 1/k! by repeated division, the order the device used to take
+    double v = 1.0;
+    for (int i = 2; i <= k; ++i) v /= (double)i;
+    tt.invfact[k] = v;
+  }
 }
 
 int max_r(const TaylorTable& tt) {

@@ -64,6 +64,7 @@ struct TaylorTable {
   int r[kMaxDeg];
   int q[kMaxDeg];
   double theta[kMaxDeg];
+  double invfact[64];  // 1/k! by repeated division (k <= largest degree)
 };
 
 struct TraceRec {
@@ -500,6 +501,21 @@ __device__ __forceinline__ T bcol(const SolveArgs& a, int t, size_t r) {
   if constexpr (sizeof(T) == 4) return a.bf[(size_t)t * a.ldv + r];
   else return __ldg(a.b[a.p - t] + r);
 }
+// xv + sum_t ntail[t] * B(r, t) in the order t = 0..p-1, with every B value loaded before the first
+// product so that the loads overlap (p is a run-time count, the loads would otherwise be serialised).
+template <typename T>
+__device__ __forceinline__ T add_btail(const SolveArgs& a, const double* ntail, int p, size_t r, T xv) {
+  constexpr int kB = 4;
+  T bv[kB];
+#pragma unroll
+  for (int t = 0; t < kB; ++t) bv[t] = t < p ? bcol<T>(a, t, r) : T(0);
+#pragma unroll
+  for (int t = 0; t < kB; ++t)
+    if (t < p) xv = fma(T(ntail[t]), bv[t], xv);
+  for (int t = kB; t < p; ++t) xv = fma(T(ntail[t]), bcol<T>(a, t, r), xv);
+  return xv;
+}
+
 // Asynchronous global -> shared copies of one element (completed by cp_async_wait_all).
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
@@ -792,8 +808,10 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
           const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
           const size_t r = (size_t)sp * npts + pt;
           for (int t = 0; t < p; ++t) cache[(size_t)t * E + e] = bcol<T>(a, t, r);
-          for (int q = 0; q < ns; ++q)
-            if (op.diag[sp][q]) cache[(size_t)(p + q) * E + e] = diag_val<T>(a, sp, q, pt);
+          for (int q = 0; q < ns; ++q)  // the point's own coupling entry is kept merged with the centre
+            if (op.diag[sp][q])
+              cache[(size_t)(p + q) * E + e] = q == sp ? T(op.coef[sp][0]) + diag_val<T>(a, sp, q, pt)
+                                                       : diag_val<T>(a, sp, q, pt);
         }
       }
       __syncthreads();
@@ -811,17 +829,36 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
           const int h = sp * plane + (ly + 1) * hw + (lx + 1);
           const double* cf = op.coef[sp];
           const T ctr = st[h];
-          T xv = T(cf[0]) * ctr;
-          xv = fma(T(cf[1]), st[h - 1], xv);
-          xv = fma(T(cf[2]), st[h + 1], xv);
-          xv = fma(T(cf[3]), st[h - hw], xv);
-          xv = fma(T(cf[4]), st[h + hw], xv);
-          for (int q = 0; q < ns; ++q)
-            if (op.diag[sp][q]) {
-              const T dv = CACHE ? cache[(size_t)(p + q) * E + e] : diag_val<T>(a, sp, q, pt);
-              xv = fma(dv, st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
-            }
-          for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), CACHE ? cache[(size_t)t * E + e] : bcol<T>(a, t, r), xv);
+          T xv;
+          if constexpr (CACHE) {
+            // centre: (c_0 + own coupling entry) v with the sum read from the cache, then the neighbours,
+            // the other species' coupling and the B block, all from shared memory
+            T cc = T(cf[0]);
+            if (op.diag[sp][sp]) cc = cache[(size_t)(p + sp) * E + e];
+            xv = cc * ctr;
+            xv = fma(T(cf[1]), st[h - 1], xv);
+            xv = fma(T(cf[2]), st[h + 1], xv);
+            xv = fma(T(cf[3]), st[h - hw], xv);
+            xv = fma(T(cf[4]), st[h + hw], xv);
+            for (int q = 0; q < ns; ++q)
+              if (q != sp && op.diag[sp][q]) xv = fma(cache[(size_t)(p + q) * E + e], st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
+            for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), cache[(size_t)t * E + e], xv);
+          } else {
+            // the same arithmetic from global memory, every coupling and B value loaded before its use so
+            // that the loads overlap
+            const int qo = 1 - sp;
+            const bool has_own = op.diag[sp][sp] != nullptr, has_oth = ns == 2 && op.diag[sp][qo] != nullptr;
+            const T d_own = has_own ? diag_val<T>(a, sp, sp, pt) : T(0);
+            const T d_oth = has_oth ? diag_val<T>(a, sp, qo, pt) : T(0);
+            const T cc = has_own ? T(cf[0]) + d_own : T(cf[0]);
+            xv = cc * ctr;
+            xv = fma(T(cf[1]), st[h - 1], xv);
+            xv = fma(T(cf[2]), st[h + 1], xv);
+            xv = fma(T(cf[3]), st[h - hw], xv);
+            xv = fma(T(cf[4]), st[h + hw], xv);
+            if (has_oth) xv = fma(d_oth, st[qo * plane + (ly + 1) * hw + (lx + 1)], xv);
+            xv = add_btail<T>(a, c.ntail, p, r, xv);
+          }
           xo[r] = xv;
           const T v0 = (i0 == j) ? ctr : (rw0 ? q0[h] : w0[r]);
           acc.add(0, v0, xv);
@@ -930,23 +967,33 @@ __device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, 
   }
   double* sA = smem_dyn;
   double* sB = smem_dyn + kTile * kMaxN;
-  // ||tau H~||_1 from the running column sums (every block holds the same values)
-  if (threadIdx.x == 0) {
-    double nrm;
-    if (a.expm_only) {
-      nrm = 0.0;  // computed below from the input
-    } else {
-      nrm = aug ? 1.0 : 0.0;  // column j+1 of H~ is e_1
-      for (int k = 1; k <= c.j; ++k) {
-        double col = c.colabs[k] + (k < c.j ? c.sub[k] : 0.0);
-        nrm = col > nrm ? col : nrm;
+  // ||tau H~||_1 from the running column sums (every block holds the same values): a block-wide max,
+  // exact in any order
+  {
+    double mx = 0.0;
+    if (!a.expm_only)
+      for (int k = 1 + threadIdx.x; k <= c.j; k += kThreads) {
+        const double col = c.colabs[k] + (k < c.j ? c.sub[k] : 0.0);
+        mx = col > mx ? col : mx;
       }
-      nrm *= aug ? c.tau : scale;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = y > mx ? y : mx;
     }
-    c.red[0] = nrm;
-    if (aug && !a.expm_only) c.hnorm = nrm;
+    if ((threadIdx.x & 31) == 0) c.wred[threadIdx.x >> 5][0] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double nrm = 0.0;
+      if (!a.expm_only) {
+        nrm = aug ? 1.0 : 0.0;  // column j+1 of H~ is e_1
+        for (int w = 0; w < kWarps; ++w) nrm = c.wred[w][0] > nrm ? c.wred[w][0] : nrm;
+        nrm *= aug ? c.tau : scale;
+      }
+      c.red[0] = nrm;
+      if (aug && !a.expm_only) c.hnorm = nrm;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (a.expm_only) {
     // column sums of |a| by one warp per column group, same order in every block
     if (threadIdx.x == 0) {
@@ -960,13 +1007,21 @@ __device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, 
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  // degree choice: squarings s_i and products of every tabulated degree in parallel, then the cheapest
+  // (first on ties)
+  if (threadIdx.x < a.tt.count) {
+    const int i = threadIdx.x;
     const double nrm = c.red[0];
+    int s = 0;
+    if (nrm > a.tt.theta[i]) s = ceil_log2(nrm / a.tt.theta[i]);
+    if (s < 0) s = 0;
+    c.wred[0][i] = (double)s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     int best_i = 0, best_cost = 1 << 30, best_s = 0;
     for (int i = 0; i < a.tt.count; ++i) {
-      int s = 0;
-      if (nrm > a.tt.theta[i]) s = ceil_log2(nrm / a.tt.theta[i]);
-      if (s < 0) s = 0;
+      const int s = (int)c.wred[0][i];
       const int cost = a.tt.r[i] - 1 + a.tt.q[i] - 1 + s;
       if (cost < best_cost) { best_cost = cost; best_i = i; best_s = s; }
     }
@@ -1012,12 +1067,7 @@ __device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, 
   if (a.expm_only) bT = bX;
   KIOPS_TICK(6);
   // Horner in X^r: T = B_{q-1}; T = T X^r + B_i, B_i = sum_{t<r} coef(i r + t) X^t, coef(k) = 1/k!
-  auto coef = [&](int k) -> double {
-    if (k > deg) return 0.0;
-    double v = 1.0;
-    for (int i = 2; i <= k; ++i) v /= (double)i;
-    return v;
-  };
+  auto coef = [&](int k) -> double { return k > deg ? 0.0 : a.tt.invfact[k]; };
   if (threadIdx.x < r) c.hc[threadIdx.x] = coef((q - 1) * r + threadIdx.x);
   __syncthreads();
   for (int64_t e = (int64_t)team.rank * kThreads + threadIdx.x; e < (int64_t)n * n; e += (int64_t)team.size * kThreads) {
@@ -1318,10 +1368,26 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           const bool hasB = rB < r1;
           T xa = apply_row_fast<T, KIND>(a, vjr, (uint32_t)rA);
           T xb = hasB ? apply_row_fast<T, KIND>(a, vjr, (uint32_t)rB) : T(0);
-          for (int t = 0; t < p; ++t) {  // B block: weights from shared memory
-            const T wt = T(c.ntail[t]);
-            xa = fma(wt, bcol<T>(a, t, (size_t)rA), xa);
-            if (hasB) xb = fma(wt, bcol<T>(a, t, (size_t)rB), xb);
+          {  // B block (weights from shared memory): every load before the first product, same order
+            constexpr int kB = 4;
+            T ba[kB], bb[kB];
+#pragma unroll
+            for (int t = 0; t < kB; ++t) {
+              ba[t] = t < p ? bcol<T>(a, t, (size_t)rA) : T(0);
+              bb[t] = (t < p && hasB) ? bcol<T>(a, t, (size_t)rB) : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < kB; ++t)
+              if (t < p) {
+                const T wt = T(c.ntail[t]);
+                xa = fma(wt, ba[t], xa);
+                if (hasB) xb = fma(wt, bb[t], xb);
+              }
+            for (int t = kB; t < p; ++t) {
+              const T wt = T(c.ntail[t]);
+              xa = fma(wt, bcol<T>(a, t, (size_t)rA), xa);
+              if (hasB) xb = fma(wt, bcol<T>(a, t, (size_t)rB), xb);
+            }
           }
           const T vja = vjr[rA], vjb = hasB ? vjr[rB] : T(0);
           const T wa0 = w0[rA], wb0 = hasB ? w0[rB] : T(0);
@@ -1635,9 +1701,10 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         m_new = (int)mn;
       }
       // cost model (section 3.2, eqs 40-42) for scenario A (keep m, tau from eq 44) and B (keep tau, m
-      // from eq 46); with a.scenario = 1 the cheaper one replaces the change of m above (ties keep B)
+      // from eq 46); with a.scenario = 1 the cheaper one replaces the change of m above (ties keep B).
+      // Evaluated only when it decides or is recorded (its pow / log chain is serial FP64 latency).
       double cost_a = 0.0, cost_b = 0.0;
-      if (!c.breakdown) {
+      if (!c.breakdown && (a.scenario == 1 || (lead && a.trace))) {
         double tau_a = c.tau * pow((accepted ? gamma : gamma_max) / omega, 1.0 / qp1);
         if (accepted && !(tau_a <= 5.0 * c.tau)) tau_a = 5.0 * c.tau;
         if (!(tau_a >= c.tau / 5.0)) tau_a = c.tau / 5.0;
