@@ -642,6 +642,7 @@ kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   o->d.n = d->nx * d->ny * d->nspecies;
   for (int s = 0; s < 2; ++s) {
     for (int k = 0; k < 5; ++k) o->d.coef[s][k] = s < d->nspecies ? d->coef[s][k] : 0.0;
+    for (int k = 0; k < 7; ++k) o->d.coef_f[s][k] = (float)o->d.coef[s][k];
     for (int r = 0; r < 2; ++r) o->d.diag[s][r] = (s < d->nspecies && r < d->nspecies) ? d->diag[s][r] : nullptr;
   }
   o->nz = 5.0 * (double)o->d.n;
@@ -672,6 +673,7 @@ kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
   o->d.bc = d->bc;
   o->d.n = d->nx * d->ny * d->nz;
   for (int k = 0; k < 7; ++k) o->d.coef[0][k] = d->coef[k];
+  for (int k = 0; k < 7; ++k) o->d.coef_f[0][k] = (float)d->coef[k];
   o->d.diag[0][0] = d->diag;
   o->nz = (double)o->d.n * (d->diag ? 8.0 : 7.0);
   *op = o;

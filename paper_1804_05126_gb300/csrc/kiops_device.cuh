@@ -52,8 +52,17 @@ struct OpDesc {
   int nspecies;
   int bc;                    // 0 homogeneous Dirichlet, 1 periodic, 2 homogeneous Neumann (reflection)
   double coef[2][7];
+  float coef_f[2][7];        // the same coefficients rounded to FP32 (FP32 basis)
   const double* diag[2][2];
 };
+
+// Stencil coefficients in the basis precision (FP64 -> FP32 conversions run at the FP64 rate on this GPU,
+// so the FP32 copies are made once on the host).
+template <typename T>
+__device__ __forceinline__ const T* coef_ptr(const OpDesc& op, int s) {
+  if constexpr (sizeof(T) == 4) return op.coef_f[s];
+  else return op.coef[s];
+}
 
 // Truncated Taylor degrees evaluated by Paterson-Stockmeyer: deg = r*q - 1 with r-1 matmuls for the
 // powers X^2..X^r and q-1 Horner matmuls in X^r; theta = largest ||X||_1 whose truncation tail
@@ -254,16 +263,25 @@ struct Ctl {
   double vtail[kGramRing][kMaxP];  // fused path: tail of v_k (basis precision) in row k % kGramRing
   int ell;                      // Task I: next output index (Algorithm 1 line 6)
   double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
+  float ntail_f[kMaxP];         // the same weights rounded to FP32 (FP32 basis)
   double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
   double hc[kMaxP + 1];         // Horner epilogue coefficients
   double red[kMaxRed];          // results of the last all-reduce
   double blk[kMaxRed];          // this block's partial sums
   double wred[kWarps][kRegK];
+  float wff[kWarps][kRegK][2];  // FP32 basis: per-warp float-float sums of the step's dots
   long long prof[16];           // cycles by phase (rank 0, thread 0) when profiling
   long long prof_last;
 };
 
 // Phase profiling: thread 0 of rank 0 charges the cycles since the previous tick to a category.
+// The step's B-block weights in the basis precision.
+template <typename T>
+__device__ __forceinline__ const T* ntail_ptr(const Ctl& c) {
+  if constexpr (sizeof(T) == 4) return c.ntail_f;
+  else return c.ntail;
+}
+
 #define KIOPS_TICK(cat)                          \
   do {                                           \
     if (prof_on && threadIdx.x == 0) {           \
@@ -427,12 +445,12 @@ __device__ __forceinline__ T apply_row(const OpDesc& op, const T* x, int64_t r) 
     const int s = (int)(r / npts);
     const int64_t pt = r - (int64_t)s * npts;
     const int64_t iy = pt / op.nx, ix = pt - iy * op.nx;
-    const double* c = op.coef[s];
-    T acc = T(c[0]) * x[r];
-    acc += T(c[1]) * st_val<T>(op, x, s, ix - 1, iy, 0, 1);
-    acc += T(c[2]) * st_val<T>(op, x, s, ix + 1, iy, 0, 1);
-    acc += T(c[3]) * st_val<T>(op, x, s, ix, iy - 1, 0, 1);
-    acc += T(c[4]) * st_val<T>(op, x, s, ix, iy + 1, 0, 1);
+    const T* c = coef_ptr<T>(op, s);
+    T acc = c[0] * x[r];
+    acc += c[1] * st_val<T>(op, x, s, ix - 1, iy, 0, 1);
+    acc += c[2] * st_val<T>(op, x, s, ix + 1, iy, 0, 1);
+    acc += c[3] * st_val<T>(op, x, s, ix, iy - 1, 0, 1);
+    acc += c[4] * st_val<T>(op, x, s, ix, iy + 1, 0, 1);
     for (int q = 0; q < op.nspecies; ++q)
       if (op.diag[s][q]) acc += T(__ldg(op.diag[s][q] + pt)) * x[(int64_t)q * npts + pt];
     return acc;
@@ -440,14 +458,14 @@ __device__ __forceinline__ T apply_row(const OpDesc& op, const T* x, int64_t r) 
     const int64_t nxy = op.nx * op.ny;
     const int64_t iz = r / nxy, rem = r - iz * nxy;
     const int64_t iy = rem / op.nx, ix = rem - iy * op.nx;
-    const double* c = op.coef[0];
-    T acc = T(c[0]) * x[r];
-    acc += T(c[1]) * st_val<T>(op, x, 0, ix - 1, iy, iz, op.nz);
-    acc += T(c[2]) * st_val<T>(op, x, 0, ix + 1, iy, iz, op.nz);
-    acc += T(c[3]) * st_val<T>(op, x, 0, ix, iy - 1, iz, op.nz);
-    acc += T(c[4]) * st_val<T>(op, x, 0, ix, iy + 1, iz, op.nz);
-    acc += T(c[5]) * st_val<T>(op, x, 0, ix, iy, iz - 1, op.nz);
-    acc += T(c[6]) * st_val<T>(op, x, 0, ix, iy, iz + 1, op.nz);
+    const T* c = coef_ptr<T>(op, 0);
+    T acc = c[0] * x[r];
+    acc += c[1] * st_val<T>(op, x, 0, ix - 1, iy, iz, op.nz);
+    acc += c[2] * st_val<T>(op, x, 0, ix + 1, iy, iz, op.nz);
+    acc += c[3] * st_val<T>(op, x, 0, ix, iy - 1, iz, op.nz);
+    acc += c[4] * st_val<T>(op, x, 0, ix, iy + 1, iz, op.nz);
+    acc += c[5] * st_val<T>(op, x, 0, ix, iy, iz - 1, op.nz);
+    acc += c[6] * st_val<T>(op, x, 0, ix, iy, iz + 1, op.nz);
     if (op.diag[0][0]) acc += T(__ldg(op.diag[0][0] + r)) * x[r];
     return acc;
   }
@@ -495,6 +513,53 @@ struct DotAcc<float> {
   }
 };
 
+// (h, l) += (bh, bl) in float-float arithmetic: TwoSum of the high parts, the low parts added to its error,
+// then renormalised (Fast2Sum).
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  const float s = __fadd_rn(h, bh);
+  const float bb = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// Block reduction of the step's dot accumulators into blk[0..K).  FP64 basis: block_reduce.  FP32 basis:
+// each warp sums its lanes' float-float pairs with float-float additions over a fixed xor tree (FP32
+// pipe only: an FP64 operation costs the FP64 pipe as much as ~60 FP32 ones on this GPU), then K threads
+// add the warps' pairs in FP64 in warp order.
+template <typename T>
+__device__ __forceinline__ void block_reduce_dots(Ctl& c, const DotAcc<T>& d, int K) {
+  if constexpr (sizeof(T) == 8) {
+    double acc[kRegK];
+    d.to_double(acc);
+    block_reduce(c, acc, K, 0);
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kRegK; ++k)
+      if (k < K) {
+        float h = d.hi[k], l = d.lo[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float bh = __shfl_xor_sync(0xffffffffu, h, o), bl = __shfl_xor_sync(0xffffffffu, l, o);
+          ff_add(h, l, bh, bl);
+        }
+        if (lane == 0) {
+          c.wff[warp][k][0] = h;
+          c.wff[warp][k][1] = l;
+        }
+      }
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += (double)c.wff[w][threadIdx.x][0] + (double)c.wff[w][threadIdx.x][1];
+      c.blk[threadIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
 // B column t (= b_{p-t}) and pointwise coupling entry in the basis precision.
 template <typename T>
 __device__ __forceinline__ T bcol(const SolveArgs& a, int t, size_t r) {
@@ -504,15 +569,15 @@ __device__ __forceinline__ T bcol(const SolveArgs& a, int t, size_t r) {
 // xv + sum_t ntail[t] * B(r, t) in the order t = 0..p-1, with every B value loaded before the first
 // product so that the loads overlap (p is a run-time count, the loads would otherwise be serialised).
 template <typename T>
-__device__ __forceinline__ T add_btail(const SolveArgs& a, const double* ntail, int p, size_t r, T xv) {
+__device__ __forceinline__ T add_btail(const SolveArgs& a, const T* ntail, int p, size_t r, T xv) {
   constexpr int kB = 4;
   T bv[kB];
 #pragma unroll
   for (int t = 0; t < kB; ++t) bv[t] = t < p ? bcol<T>(a, t, r) : T(0);
 #pragma unroll
   for (int t = 0; t < kB; ++t)
-    if (t < p) xv = fma(T(ntail[t]), bv[t], xv);
-  for (int t = kB; t < p; ++t) xv = fma(T(ntail[t]), bcol<T>(a, t, r), xv);
+    if (t < p) xv = fma(ntail[t], bv[t], xv);
+  for (int t = kB; t < p; ++t) xv = fma(ntail[t], bcol<T>(a, t, r), xv);
   return xv;
 }
 
@@ -564,12 +629,12 @@ __device__ __forceinline__ T apply_row_fast(const SolveArgs& a, const T* __restr
       so = iy > 0 ? xs[pt - nx] : T(0);
       no = iy + 1 < ny ? xs[pt + nx] : T(0);
     }
-    const double* c = op.coef[sp];
-    T acc = T(c[0]) * xs[pt];
-    acc = fma(T(c[1]), w, acc);
-    acc = fma(T(c[2]), e, acc);
-    acc = fma(T(c[3]), so, acc);
-    acc = fma(T(c[4]), no, acc);
+    const T* c = coef_ptr<T>(op, (int)sp);
+    T acc = c[0] * xs[pt];
+    acc = fma(c[1], w, acc);
+    acc = fma(c[2], e, acc);
+    acc = fma(c[3], so, acc);
+    acc = fma(c[4], no, acc);
     for (int q = 0; q < op.nspecies; ++q)
       if (op.diag[sp][q]) acc = fma(diag_val<T>(a, sp, q, pt), x[(size_t)q * npts + pt], acc);
     return acc;
@@ -600,14 +665,14 @@ __device__ __forceinline__ T apply_row_fast(const SolveArgs& a, const T* __restr
       zm = iz > 0 ? x[r - nxy] : T(0);
       zp = iz + 1 < nz ? x[r + nxy] : T(0);
     }
-    const double* c = op.coef[0];
-    T acc = T(c[0]) * x[r];
-    acc = fma(T(c[1]), xm, acc);
-    acc = fma(T(c[2]), xp, acc);
-    acc = fma(T(c[3]), ym, acc);
-    acc = fma(T(c[4]), yp, acc);
-    acc = fma(T(c[5]), zm, acc);
-    acc = fma(T(c[6]), zp, acc);
+    const T* c = coef_ptr<T>(op, 0);
+    T acc = c[0] * x[r];
+    acc = fma(c[1], xm, acc);
+    acc = fma(c[2], xp, acc);
+    acc = fma(c[3], ym, acc);
+    acc = fma(c[4], yp, acc);
+    acc = fma(c[5], zm, acc);
+    acc = fma(c[6], zp, acc);
     if (op.diag[0][0]) acc = fma(diag_val<T>(a, 0, 0, r), x[r], acc);
     return acc;
   }
@@ -714,6 +779,33 @@ static __device__ __noinline__ void mm_team(const double* A, Band bA, const doub
 // block with the same arithmetic), writes the tile's v_j to the basis, and applies A~ from shared memory.
 // Raw vectors x_{j+1} go to a two-slot ring so that no block overwrites a value a neighbour still reads.
 // The arithmetic of every value is the same as in the unfused path.
+// Coordinates (s, y, x) of the flat index e over ns planes of w x h points, stepped by kThreads without
+// divisions (one division each at the start).
+struct TileWalk {
+  int w, h, dx, dy, x, y, s;
+  __device__ __forceinline__ TileWalk(int e, int w_, int h_) : w(w_), h(h_) {
+    const int plane = w * h;
+    s = e / plane;
+    const int rem = e - s * plane;
+    y = rem / w;
+    x = rem - y * w;
+    dy = kThreads / w;
+    dx = kThreads - dy * w;
+  }
+  __device__ __forceinline__ void next() {
+    x += dx;
+    y += dy;
+    if (x >= w) {
+      x -= w;
+      ++y;
+    }
+    while (y >= h) {
+      y -= h;
+      ++s;
+    }
+  }
+};
+
 template <typename T>
 __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, int i0, int nwin, bool lead,
                                  T* V, size_t ldv, double* smem, DotAcc<T>& acc, bool prof_on) {
@@ -771,12 +863,13 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
       const int bc = op.bc;
       auto finalize = [&](auto tok_tag) {
         constexpr bool TOK = decltype(tok_tag)::value;
-        for (int e = tid; e < ns * plane; e += kThreads) {
+        TileWalk wk(tid, hw, hh);
+        for (int e = tid; e < ns * plane; e += kThreads, wk.next()) {
           unsigned code;
           if constexpr (TOK) {
             code = tbl[e];
           } else {
-            const int sp = e / plane, rem = e - sp * plane, hy = rem / hw, hx = rem - hy * hw;
+            const int sp = wk.s, hy = wk.y, hx = wk.x;
             int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
             gx = (int)bc_index(bc, gx, nx);
             gy = (int)bc_index(bc, gy, ny);
@@ -803,14 +896,15 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
       if (tok) finalize(std::true_type{});
       else finalize(std::false_type{});
       if (cfill) {  // B columns and coupling fields of the tile's own points (each thread its own e)
-        for (int e = tid; e < E; e += kThreads) {
-          const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
+        TileWalk wk(tid, tw, th);
+        for (int e = tid; e < E; e += kThreads, wk.next()) {
+          const int sp = wk.s, ly = wk.y, lx = wk.x;
           const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
           const size_t r = (size_t)sp * npts + pt;
           for (int t = 0; t < p; ++t) cache[(size_t)t * E + e] = bcol<T>(a, t, r);
           for (int q = 0; q < ns; ++q)  // the point's own coupling entry is kept merged with the centre
             if (op.diag[sp][q])
-              cache[(size_t)(p + q) * E + e] = q == sp ? T(op.coef[sp][0]) + diag_val<T>(a, sp, q, pt)
+              cache[(size_t)(p + q) * E + e] = q == sp ? coef_ptr<T>(op, sp)[0] + diag_val<T>(a, sp, q, pt)
                                                        : diag_val<T>(a, sp, q, pt);
         }
       }
@@ -822,27 +916,29 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
       // A~ v_j on the own points and the step's dots; CACHE: B and coupling values from shared memory
       auto compute = [&](auto cache_tag) {
         constexpr bool CACHE = decltype(cache_tag)::value;
-        for (int e = tid; e < E; e += kThreads) {
-          const int sp = e / (tw * th), rem = e - sp * (tw * th), ly = rem / tw, lx = rem - ly * tw;
+        TileWalk wk(tid, tw, th);
+        for (int e = tid; e < E; e += kThreads, wk.next()) {
+          const int sp = wk.s, ly = wk.y, lx = wk.x;
           const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
           const size_t r = (size_t)sp * npts + pt;
           const int h = sp * plane + (ly + 1) * hw + (lx + 1);
-          const double* cf = op.coef[sp];
+          const T* cf = coef_ptr<T>(op, sp);
+          const T* nt = ntail_ptr<T>(c);
           const T ctr = st[h];
           T xv;
           if constexpr (CACHE) {
             // centre: (c_0 + own coupling entry) v with the sum read from the cache, then the neighbours,
             // the other species' coupling and the B block, all from shared memory
-            T cc = T(cf[0]);
+            T cc = cf[0];
             if (op.diag[sp][sp]) cc = cache[(size_t)(p + sp) * E + e];
             xv = cc * ctr;
-            xv = fma(T(cf[1]), st[h - 1], xv);
-            xv = fma(T(cf[2]), st[h + 1], xv);
-            xv = fma(T(cf[3]), st[h - hw], xv);
-            xv = fma(T(cf[4]), st[h + hw], xv);
+            xv = fma(cf[1], st[h - 1], xv);
+            xv = fma(cf[2], st[h + 1], xv);
+            xv = fma(cf[3], st[h - hw], xv);
+            xv = fma(cf[4], st[h + hw], xv);
             for (int q = 0; q < ns; ++q)
               if (q != sp && op.diag[sp][q]) xv = fma(cache[(size_t)(p + q) * E + e], st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
-            for (int t = 0; t < p; ++t) xv = fma(T(c.ntail[t]), cache[(size_t)t * E + e], xv);
+            for (int t = 0; t < p; ++t) xv = fma(nt[t], cache[(size_t)t * E + e], xv);
           } else {
             // the same arithmetic from global memory, every coupling and B value loaded before its use so
             // that the loads overlap
@@ -850,14 +946,14 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
             const bool has_own = op.diag[sp][sp] != nullptr, has_oth = ns == 2 && op.diag[sp][qo] != nullptr;
             const T d_own = has_own ? diag_val<T>(a, sp, sp, pt) : T(0);
             const T d_oth = has_oth ? diag_val<T>(a, sp, qo, pt) : T(0);
-            const T cc = has_own ? T(cf[0]) + d_own : T(cf[0]);
+            const T cc = has_own ? cf[0] + d_own : cf[0];
             xv = cc * ctr;
-            xv = fma(T(cf[1]), st[h - 1], xv);
-            xv = fma(T(cf[2]), st[h + 1], xv);
-            xv = fma(T(cf[3]), st[h - hw], xv);
-            xv = fma(T(cf[4]), st[h + hw], xv);
+            xv = fma(cf[1], st[h - 1], xv);
+            xv = fma(cf[2], st[h + 1], xv);
+            xv = fma(cf[3], st[h - hw], xv);
+            xv = fma(cf[4], st[h + hw], xv);
             if (has_oth) xv = fma(d_oth, st[qo * plane + (ly + 1) * hw + (lx + 1)], xv);
-            xv = add_btail<T>(a, c.ntail, p, r, xv);
+            xv = add_btail<T>(a, nt, p, r, xv);
           }
           xo[r] = xv;
           const T v0 = (i0 == j) ? ctr : (rw0 ? q0[h] : w0[r]);
@@ -1325,6 +1421,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         }
         c.vtail[j % kGramRing][tid] = c.tail[tid];
         c.ntail[tid] = c.nu * c.tail[tid];
+        c.ntail_f[tid] = (float)c.ntail[tid];
       }
       if (fused) cp_async_wait_all();  // the stage prefetched during the last step
       __syncthreads();
@@ -1343,9 +1440,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           c.tbl_ok = a.stage_on;
         }
         KIOPS_TICK(13);
-        double acc[kRegK];
-        dacc.to_double(acc);
-        block_reduce(c, acc, 2 * kChunk + 1, 0);
+        block_reduce_dots<T>(c, dacc, 2 * kChunk + 1);
         if (tid == 0) {
           for (int u = 0; u < nwin; ++u) {
             c.red[u] = c.blk[u];
@@ -1379,12 +1474,12 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
 #pragma unroll
             for (int t = 0; t < kB; ++t)
               if (t < p) {
-                const T wt = T(c.ntail[t]);
+                const T wt = ntail_ptr<T>(c)[t];
                 xa = fma(wt, ba[t], xa);
                 if (hasB) xb = fma(wt, bb[t], xb);
               }
             for (int t = kB; t < p; ++t) {
-              const T wt = T(c.ntail[t]);
+              const T wt = ntail_ptr<T>(c)[t];
               xa = fma(wt, bcol<T>(a, t, (size_t)rA), xa);
               if (hasB) xb = fma(wt, bcol<T>(a, t, (size_t)rB), xb);
             }
@@ -1429,9 +1524,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           }
           dacc.add(2 * kChunk, xv, xv);
         }
-        double acc[kRegK];
-        dacc.to_double(acc);
-        block_reduce(c, acc, 2 * kChunk + 1, 0);
+        block_reduce_dots<T>(c, dacc, 2 * kChunk + 1);
         if (tid == 0) {
           for (int u = 0; u < nwin; ++u) {
             c.red[u] = c.blk[u];
@@ -1457,7 +1550,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           if (cb == 0) {
             if (!tailrow) {
               T s = apply_row<T, KIND>(a.op, vj, rr);
-              for (int t = 0; t < p; ++t) s += T(c.ntail[t]) * T(__ldg(a.b[p - t] + rr));
+              for (int t = 0; t < p; ++t) s += ntail_ptr<T>(c)[t] * bcol<T>(a, t, (size_t)rr);
               xv = s;
             } else {
               const int t = (int)(rr - N);
