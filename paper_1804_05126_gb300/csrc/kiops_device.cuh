@@ -358,22 +358,22 @@ __device__ inline bool finish_reduce<CtaTeam>(CtaTeam& team, Ctl& c, double*, in
   return true;
 }
 
-// Sum the published partials of all ranks into red[0..K): thread t loads rank t's partials (ranks
-// t + kThreads, ... added on top), then the fixed block tree over only as many warps as hold ranks.
+// Sum the published partials of all ranks into red[0..K): value k of rank r is at buf[k * size + r] (a
+// warp's loads of one value are contiguous); thread t loads rank t's partials (ranks t + kThreads, ...
+// added on top), then the fixed block tree over only as many warps as hold ranks.
 __device__ inline void grid_sum_partials(GridTeam& team, Ctl& c, const double* buf, int K) {
   const int nw = team.size >= kThreads ? kWarps : (team.size + 31) / 32;
   for (int k0 = 0; k0 < K; k0 += kRegK) {
     const int cnt = K - k0 < kRegK ? K - k0 : kRegK;
     double acc[kRegK];
     const int r = threadIdx.x;
-    const double* src = buf + (size_t)r * kMaxRed + k0;
+    const double* src = buf + (size_t)k0 * team.size;  // value k of rank r at src[k * size + r]
 #pragma unroll
-    for (int k = 0; k < kRegK; ++k) acc[k] = (r < team.size && k < cnt) ? src[k] : 0.0;
+    for (int k = 0; k < kRegK; ++k) acc[k] = (r < team.size && k < cnt) ? src[(size_t)k * team.size + r] : 0.0;
     for (int r2 = r + kThreads; r2 < team.size; r2 += kThreads) {
-      const double* src2 = buf + (size_t)r2 * kMaxRed + k0;
 #pragma unroll
       for (int k = 0; k < kRegK; ++k)
-        if (k < cnt) acc[k] += src2[k];
+        if (k < cnt) acc[k] += src[(size_t)k * team.size + r2];
     }
     block_reduce_to(c, acc, cnt, c.red + k0, nw);
   }
@@ -383,7 +383,7 @@ template <>
 __device__ inline bool finish_reduce<GridTeam>(GridTeam& team, Ctl& c, double* partials, int& parity, int K,
                                         bool prof_on) {
   double* buf = partials + (size_t)parity * team.size * kMaxRed;
-  for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
+  for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)k * team.size + team.rank] = c.blk[k];
   if (!team.sync(&c.sync_ok)) return false;
   KIOPS_TICK(11);
   grid_sum_partials(team, c, buf, K);
@@ -398,7 +398,7 @@ __device__ __forceinline__ bool finish_reduce_hook(Team& team, Ctl& c, double* p
                                                    bool prof_on, Hook&& hook) {
   if constexpr (std::is_same<Team, GridTeam>::value) {
     double* buf = partials + (size_t)parity * team.size * kMaxRed;
-    for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)team.rank * kMaxRed + k] = c.blk[k];
+    for (int k = threadIdx.x; k < K; k += kThreads) buf[(size_t)k * team.size + team.rank] = c.blk[k];
     if (!team.sync(&c.sync_ok)) return false;
     KIOPS_TICK(11);
     grid_sum_partials(team, c, buf, K);
