@@ -330,6 +330,12 @@ kiops_status kiops_pde_rhs(kiops_ctx* ctx, const kiops_pde* pde, const double* u
 kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, double t0, double t1, int64_t nsteps,
                              double tol, int m_init, double* u, kiops_integrate_stats* stats);
 
+/* Self-test of the bounded device-side waits (the paper has no counterpart): one thread block of a two-block
+ * team enters the team barrier that every solve uses; the second arrival never comes, so after timeout_s
+ * (0 < timeout_s <= 5) the wait gives up, raises the abort flag and the kernel returns.  Returns
+ * KIOPS_ETIMEOUT when that happened as designed (the context stays usable), KIOPS_ECUDA otherwise. */
+kiops_status kiops_selftest_wait_timeout(kiops_ctx* ctx, double timeout_s);
+
 /* Size of the fixed device scratch used by kiops_solve_noalloc (bytes). */
 #define KIOPS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -486,6 +486,19 @@ __global__ void op_apply_kernel(OpDesc op, const double* x, double* y) {
     y[r] = apply_row<double, KIND>(op, x, r);
 }
 
+// One block of a two-block team passes the team barrier: the second arrival never comes, so the bounded
+// wait gives up after timeout_ns, raises the abort flag with ST_ETIMEOUT and returns false.  out[0] = 1 if
+// the barrier completed, out[1] = the abort flag.
+__global__ void barrier_timeout_kernel(unsigned int* ctr, int* abort_flag, long long timeout_ns, int* out) {
+  __shared__ int ok;
+  GridTeam team{0, 2, ctr, abort_flag, timeout_ns, 0u};
+  const bool passed = team.sync(&ok);
+  if (threadIdx.x == 0) {
+    out[0] = passed ? 1 : 0;
+    out[1] = ld_volatile_int(abort_flag);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1374,6 +1387,26 @@ kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]) {
   return KIOPS_OK;
 }
 
+
+// ---- Self-test of the bounded device-side waits ----------------------------------------------------------
+kiops_status kiops_selftest_wait_timeout(kiops_ctx* ctx, double timeout_s) {
+  if (!ctx) return KIOPS_EINVAL;
+  if (!(timeout_s > 0.0) || timeout_s > 5.0) return fail(ctx, KIOPS_EINVAL, "timeout_s must be in (0, 5]");
+  void* buf = nullptr;  // counter line, abort flag, results
+  KCHECK(ctx, cudaMalloc(&buf, 512));
+  std::unique_ptr<void, cudaError_t (*)(void*)> guard(buf, cudaFree);
+  char* b = (char*)buf;
+  KCHECK(ctx, cudaMemsetAsync(buf, 0, 512, ctx->stream));
+  barrier_timeout_kernel<<<1, 64, 0, ctx->stream>>>((unsigned int*)b, (int*)(b + 128), (long long)(timeout_s * 1e9),
+                                                    (int*)(b + 256));
+  KCHECK(ctx, cudaGetLastError());
+  int out[2] = {0, 0};
+  KCHECK(ctx, cudaMemcpyAsync(out, b + 256, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+  KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (out[0] == 0 && out[1] == ST_ETIMEOUT)
+    return fail(ctx, KIOPS_ETIMEOUT, "a device-side wait exceeded %.3g s (self-test: expected)", timeout_s);
+  return fail(ctx, KIOPS_ECUDA, "wait self-test: barrier passed = %d, abort flag = %d", out[0], out[1]);
+}
 
 // ---- Exponential integrators (section 4) -------------------------------------------------------------
 static kiops_status pde_dev(kiops_ctx* ctx, const kiops_pde* pde, kiops_k::PdeDev& P) {

@@ -162,6 +162,7 @@ _SIGS = {
     "kiops_solve_noalloc": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_void_p), C.c_double, C.c_int,
                              C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
     "kiops_pde_rhs": ([C.c_void_p, C.POINTER(kiops_pde), C.c_void_p, C.c_void_p], C.c_int),
+    "kiops_selftest_wait_timeout": ([C.c_void_p, C.c_double], C.c_int),
     "kiops_integrate": ([C.c_void_p, C.POINTER(kiops_pde), C.c_int, C.c_double, C.c_double, C.c_int64, C.c_double,
                          C.c_int, C.c_void_p, C.POINTER(kiops_integrate_stats)], C.c_int),
 }
@@ -299,6 +300,11 @@ def kiops_solve_batch(ctx, reqs: list[kiops_request]) -> list[dict]:
     stats = (kiops_stats * max(n, 1))()
     _check(ctx, lib().kiops_solve_batch(ctx, n, arr, stats), "kiops_solve_batch")
     return [stats[i].as_dict() for i in range(n)]
+
+
+def kiops_selftest_wait_timeout(ctx, timeout_s: float) -> int:
+    """Status of the bounded-wait self-test (KIOPS_ETIMEOUT = 4 is the designed outcome)."""
+    return int(lib().kiops_selftest_wait_timeout(ctx, timeout_s))
 
 
 def kiops_pde_rhs(ctx, pde: kiops_pde, u_ptr, f_ptr) -> None:
