@@ -303,3 +303,49 @@ def test_cost_model_costs_and_scenario_choice_match_oracle(make, scenario):
     for t, r in zip(tr, tr_ref):
         for k in ("cost_a", "cost_b", "tau_new"):
             assert t[k] == pytest.approx(r[k], rel=1e-12, abs=0.0), (k, t, r)
+
+
+def _adr3d_problem(n, bc, p, seed, tau=1e-3, tol=1e-9):
+    rng = np.random.default_rng(seed)
+    op = dict(W.adr3d(n, shift=-2.0, adv=(3.0, -1.0, 2.0), diff=1.0), bc=bc)
+    return W.Problem(name=f"adr3d_{n}_{bc}", op=op, b=rng.standard_normal((p + 1, n ** 3)), tau=tau, tol=tol)
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic", "neumann"])
+@pytest.mark.parametrize("n,p", [(9, 2), (24, 4), (50, 1)])
+def test_3d_stencil_boundaries(n, p, bc):
+    """3D 7-point stencils with every boundary (Dirichlet, periodic, reflected Neumann) against the oracle,
+    with the same decisions."""
+    P = _adr3d_problem(n, bc, p, seed=100 + n + p)
+    s = kiops.Solver(device=0)
+    w, st, tr = gpu_solve(s, P, trace=True)
+    s.close()
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+
+
+def test_3d_stencil_fp32_basis():
+    P = _adr3d_problem(40, "dirichlet", 2, seed=7, tol=1e-6)
+    s = kiops.Solver(device=0)
+    w, st = gpu_solve(s, P, precision="fp32_basis")
+    s.close()
+    w_ref, _, _ = oracle_solve(P)
+    assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
+
+
+def test_3d_boundaries_in_batched_teams():
+    """Batched 3D solves with every boundary on teams of blocks against the oracle."""
+    s = kiops.Solver(device=0)
+    probs = [_adr3d_problem(n, bc, 2, seed=200 + n) for n, bc in [(12, "dirichlet"), (16, "neumann"), (10, "periodic")]]
+    items = []
+    for P in probs:
+        op = s.operator(P.op)
+        b = torch.as_tensor(P.b, device="cuda:0")
+        items.append((op, P.tau, b, P.tol, P.m_init, P.m_o, "fp64", torch.empty(P.b.shape[1], dtype=torch.float64, device="cuda:0")))
+    st = s.solve_batch(items, team_blocks=4)
+    torch.cuda.synchronize()
+    for P, it, sti in zip(probs, items, st):
+        w_ref, _, _ = oracle_solve(P)
+        assert sti["status"] == 0 and rel(it[7].cpu().numpy(), w_ref) <= 10 * P.tol
+    s.close()
