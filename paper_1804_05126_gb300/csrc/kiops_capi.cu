@@ -19,6 +19,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>  // header-only NVTX: ranges cost nothing unless a profiler is attached
+
 #include "kiops.h"
 #include "kiops_device.cuh"
 #include "kiops_kernels.h"
@@ -78,6 +80,14 @@ kiops_status fail(kiops_ctx* ctx, kiops_status s, const char* fmt, ...) {
   } while (0)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Host-side NVTX range around an entry point (visible in nsys / ncu timelines).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Truncation tail sum_{k > d} theta^k / k! (terms through exp/lgamma; every term positive).
 double taylor_tail(double theta, int d) {
@@ -385,6 +395,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
                         int m_init, int m_o, kiops_precision prec, double* w, kiops_stats* stats,
                         kiops_trace_rec* trace, int64_t trace_cap, int64_t* trace_len, const double* times = nullptr,
                         int n_times = 0, double* const* wout = nullptr) {
+  NvtxRange nvtx_range("kiops solve");
   if (!ctx) return KIOPS_EINVAL;
   if (trace_len) *trace_len = 0;
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -793,6 +804,7 @@ static double estimate_work(const kiops_ctx* ctx, const kiops_request& r) {
 // team.  K = cfg.batch_team_blocks, or 0 = automatic (the heaviest request's share of the total work,
 // rounded down to a power of two).
 static kiops_status batch_teams(kiops_ctx* ctx, int count, const kiops_request* reqs, kiops_stats* stats) {
+  NvtxRange nvtx_range("kiops batch");
   std::vector<int> order;
   for (int i = 0; i < count; ++i)
     if (reqs[i].tau > 0.0) order.push_back(i);
@@ -939,6 +951,7 @@ kiops_status kiops_set_batch_team_blocks(kiops_ctx* ctx, int team_blocks) {
 }
 
 kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f) {
+  NvtxRange nvtx_range("kiops expm");
   if (!ctx || !a || !f || n < 1 || n > KIOPS_MAX_M + 1) return KIOPS_EINVAL;
   void* fn = pick_kernel(false, OP_CSR);
   kiops_status st = prepare_kernel(ctx, fn);
@@ -994,6 +1007,7 @@ void* g_noalloc_addr[kNoallocMaxDevices] = {};
 extern "C" kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, double tau, int p,
                                             const double* const* b, double tol, int m_init, int m_o, double* w,
                                             kiops_stats* stats) {
+  NvtxRange nvtx_range("kiops solve (no allocation)");
   if (!ctx) return KIOPS_EINVAL;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   const int dev = ctx->cfg.device;
@@ -1446,6 +1460,7 @@ kiops_status kiops_pde_rhs(kiops_ctx* ctx, const kiops_pde* pde, const double* u
 
 kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, double t0, double t1, int64_t nsteps,
                              double tol, int m_init, double* u, kiops_integrate_stats* stats) {
+  NvtxRange nvtx_range("kiops integrate");
   if (!ctx) return KIOPS_EINVAL;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   kiops_k::PdeDev P;
@@ -1531,6 +1546,7 @@ kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, d
     }
   };
   for (int64_t n = 0; n < nsteps; ++n) {
+    NvtxRange step_range("integrator step");
     // h f(u_n) and the fields of A = h J_n
     KCHECK(ctx, kiops_k::launch_pde_eval(P, u, h, hf, fields, ctx->sms, ctx->stream));
     // Task I: phi_1(c A) h f(u_n) at both nodes
