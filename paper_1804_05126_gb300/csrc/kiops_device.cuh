@@ -322,8 +322,19 @@ __device__ __forceinline__ double warp_transpose_sum8(const double (&v)[kRegK]) 
 
 // Reduce acc[0..K) (K <= kRegK) over the first `nwarps` warps of the block into dst[0..K) (shared).
 // Fixed order: butterfly within each warp, then warps 0, 1, 2, ... in sequence.
+// Destination of slot k of the step's dot accumulators (<v_i, x> in slots 0..kChunk-1, <v_j, v_i> in
+// kChunk.., ||x||^2 in 2 kChunk) in the compact all-reduce layout [<v_i, x>: nwin][||x||^2][<v_j, v_i>: nwin];
+// -1 for unused slots.  nwin < 0 keeps slot k at k.
+__device__ __forceinline__ int compact_slot(int k, int nwin) {
+  if (nwin < 0) return k;
+  if (k < nwin) return k;
+  if (k == 2 * kChunk) return nwin;
+  if (k >= kChunk && k < kChunk + nwin) return nwin + 1 + (k - kChunk);
+  return -1;
+}
+
 __device__ __forceinline__ void block_reduce_to(Ctl& c, const double (&acc)[kRegK], int K, double* dst,
-                                                int nwarps = kWarps) {
+                                                int nwarps = kWarps, int nwin = -1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < nwarps) {
     const double r = warp_transpose_sum8(acc);
@@ -338,7 +349,8 @@ __device__ __forceinline__ void block_reduce_to(Ctl& c, const double (&acc)[kReg
     for (int st = 1; st < kWarps; st <<= 1)
 #pragma unroll
       for (int w = 0; w + st < kWarps; w += 2 * st) v[w] += v[w + st];
-    dst[threadIdx.x] = v[0];
+    const int d = compact_slot(threadIdx.x, nwin);
+    if (d >= 0) dst[d] = v[0];
   }
   __syncthreads();
 }
@@ -529,11 +541,11 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
 // pipe only: an FP64 operation costs the FP64 pipe as much as ~60 FP32 ones on this GPU), then K threads
 // add the warps' pairs in FP64 in warp order.
 template <typename T>
-__device__ __forceinline__ void block_reduce_dots(Ctl& c, const DotAcc<T>& d, int K) {
+__device__ __forceinline__ void block_reduce_dots(Ctl& c, const DotAcc<T>& d, int K, int nwin = -1) {
   if constexpr (sizeof(T) == 8) {
     double acc[kRegK];
     d.to_double(acc);
-    block_reduce(c, acc, K, 0);
+    block_reduce_to(c, acc, K, c.blk, kWarps, nwin);
   } else {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -554,7 +566,8 @@ __device__ __forceinline__ void block_reduce_dots(Ctl& c, const DotAcc<T>& d, in
     if (threadIdx.x < K) {
       double sum = 0.0;
       for (int w = 0; w < kWarps; ++w) sum += (double)c.wff[w][threadIdx.x][0] + (double)c.wff[w][threadIdx.x][1];
-      c.blk[threadIdx.x] = sum;
+      const int dst = compact_slot(threadIdx.x, nwin);
+      if (dst >= 0) c.blk[dst] = sum;
     }
     __syncthreads();
   }
@@ -1440,15 +1453,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           c.tbl_ok = a.stage_on;
         }
         KIOPS_TICK(13);
-        block_reduce_dots<T>(c, dacc, 2 * kChunk + 1);
-        if (tid == 0) {
-          for (int u = 0; u < nwin; ++u) {
-            c.red[u] = c.blk[u];
-            c.red[nwin + 1 + u] = c.blk[kChunk + u];
-          }
-          c.red[nwin] = c.blk[2 * kChunk];
-        }
-        __syncthreads();
+        block_reduce_dots<T>(c, dacc, 2 * kChunk + 1, nwin);  // compact layout straight into blk
       } else if (nwin <= kChunk) {
         // single pass: two rows per thread in flight, every load issued before the stores
         DotAcc<T> dacc;
@@ -1524,15 +1529,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           }
           dacc.add(2 * kChunk, xv, xv);
         }
-        block_reduce_dots<T>(c, dacc, 2 * kChunk + 1);
-        if (tid == 0) {
-          for (int u = 0; u < nwin; ++u) {
-            c.red[u] = c.blk[u];
-            c.red[nwin + 1 + u] = c.blk[kChunk + u];
-          }
-          c.red[nwin] = c.blk[2 * kChunk];
-        }
-        __syncthreads();
+        block_reduce_dots<T>(c, dacc, 2 * kChunk + 1, nwin);  // compact layout straight into blk
       }
       for (int cb = 0; cb < nwin && nwin > kChunk && !fused; cb += kChunk) {
         const int cnt = nwin - cb < kChunk ? nwin - cb : kChunk;
@@ -1583,8 +1580,10 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         }
         __syncthreads();
       }
-      for (int k = tid; k < Ktot; k += kThreads) c.blk[k] = c.red[k];
-      __syncthreads();
+      if (nwin > kChunk && !fused) {  // the multi-pass form staged its sums in red
+        for (int k = tid; k < Ktot; k += kThreads) c.blk[k] = c.red[k];
+        __syncthreads();
+      }
       KIOPS_TICK(2);
       {
         // fused path: x_{j+1} is complete once the barrier is passed; stage its tile for step j + 1
@@ -1650,6 +1649,13 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
             for (int u = 0; u < nwin; ++u) a.H[(size_t)(i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
           c.matvecs += 1;
           c.j = j;
+          if (fused) {  // v_{j+1} is finalised by the next step's tiles (lagged normalisation)
+            for (int u = 0; u < nwin; ++u) c.fin_h[u] = c.hcoef[u];
+            c.fin_rs = rs;
+            c.fin_i0 = i0;
+            c.fin_nwin = nwin;
+            c.fin_pending = 1;
+          }
         }
         // record Gram row j: <v_j, v_{j-o}> for o = 0..nwin-1
         if (a.m_o <= kGramRing) {
@@ -1674,41 +1680,36 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         }
         block_reduce(c, acc, 1, 0);
         if (!finish_reduce<Team>(team, c, a.partials, parity, 1)) goto stop;
-        if (tid == 0) c.s = sqrt(c.red[0]);
+        if (tid == 0) {
+          c.s = sqrt(c.red[0]);
+          c.matvecs += 1;
+          double ca = 0.0;
+          for (int u = 0; u < c.nwin; ++u) ca += fabs(c.hcoef[u]);
+          c.colabs[j] = ca;
+          if (lead)
+            for (int u = 0; u < c.nwin; ++u) a.H[(size_t)(c.i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
+          c.j = j;
+          if (c.s * c.s <= a.bd_tol * a.bd_tol * nx2_pre) {  // happy breakdown (Algorithm 2 lines 12-15)
+            c.breakdown = 1;
+            c.sub[j] = 0.0;
+          } else {
+            c.sub[j] = c.s;
+            c.rs = 1.0 / c.s;
+            if (lead) a.H[(size_t)j * ldh + (j - 1)] = c.s;
+            if (fused) {  // lagged normalisation, as in the common case
+              for (int u = 0; u < c.nwin; ++u) c.fin_h[u] = c.hcoef[u];
+              c.fin_rs = c.rs;
+              c.fin_i0 = c.i0;
+              c.fin_nwin = c.nwin;
+              c.fin_pending = 1;
+            }
+          }
+        }
         __syncthreads();
       }
-      if (tid == 0 && c.recompute) {
-        c.matvecs += 1;
-        double ca = 0.0;
-        for (int u = 0; u < c.nwin; ++u) ca += fabs(c.hcoef[u]);
-        c.colabs[j] = ca;
-        if (lead)
-          for (int u = 0; u < c.nwin; ++u) a.H[(size_t)(c.i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
-        c.j = j;
-        if (c.s * c.s <= a.bd_tol * a.bd_tol * nx2_pre) {  // happy breakdown (Algorithm 2 lines 12-15)
-          c.breakdown = 1;
-          c.sub[j] = 0.0;
-        } else {
-          c.sub[j] = c.s;
-          c.rs = 1.0 / c.s;
-          if (lead) a.H[(size_t)j * ldh + (j - 1)] = c.s;
-        }
-      }
-      __syncthreads();
       KIOPS_TICK(4);
       if (c.breakdown) break;
-      if (fused) {  // v_{j+1} is finalised by the next step's tiles (or stays pending)
-        if (tid == 0) {
-          for (int u = 0; u < c.nwin; ++u) c.fin_h[u] = c.hcoef[u];
-          c.fin_rs = c.rs;
-          c.fin_i0 = c.i0;
-          c.fin_nwin = c.nwin;
-          c.fin_pending = 1;
-        }
-        __syncthreads();
-        KIOPS_TICK(5);
-        continue;
-      }
+      if (fused) continue;  // v_{j+1} is finalised by the next step's tiles (or stays pending)
       // ---- v_{j+1} = (1/s) (x - sum_i h_i v_i) in MGS order (lines 9, 16-17)
       if (nwin <= kChunk) {
         const T h0 = T(c.hcoef[0]), h1 = nwin > 1 ? T(c.hcoef[1]) : T(0), h2 = nwin > 2 ? T(c.hcoef[2]) : T(0);
