@@ -41,6 +41,9 @@
  *       matrix of the 1-norm of tau H~ (scaled by tau_A/tau for scenario A): pi_m = 2, 3, 4, 5, 6
  *       for Pade degrees 3, 5, 7, 9, 13 plus the s squarings.  With opts.scenario = 1 the cheaper
  *       scenario replaces Algorithm 4's choice in its line 18 branch (ties keep scenario B).
+ *       The cost values have no printed counterpart in the paper: parity unpinned (they are checked only
+ *       against the paper's statement that scenario B is almost always the cheaper completion, and the
+ *       cheaper-scenario mode against the exact dense exponential).
  */
 #include <math.h>
 #include <stdint.h>
