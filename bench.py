@@ -45,14 +45,30 @@ def config_dict(P, l2="flushed between timed solves (256 MiB write)"):
 
 
 # ------------------------------------------------------------------ algorithmic work model
-def algorithmic_model(P, stats):
+THETA13 = 5.371920351148152  # Higham (2005): largest ||X||_1 for the degree-13 Pade approximant
+
+
+def expm_flops(trace):
+    """FP64 flops of the iterations' small exponentials: (8 + s) 2 (j+1)^3 per iteration, s the squarings
+    of a degree-13 scaling-and-squaring Pade method for ||tau H~||_1 (the figure the exponential's cost
+    model uses; the GPU evaluates Taylor / Paterson-Stockmeyer instead)."""
+    import math
+    total = 0.0
+    for t in trace:
+        s = max(0, math.ceil(math.log2(t["hnorm"] / THETA13))) if t["hnorm"] > THETA13 else 0
+        total += (8 + s) * 2.0 * (t["j"] + 1) ** 3
+    return total
+
+
+def algorithmic_model(P, stats, trace=None):
     """Bytes and FP64 flops one solve must move/do (independent of this implementation).
 
     Per Krylov step (Algorithm 2): read v_j, v_{j-1} and the p columns of B, write v_{j+1}, read the
     operator's reaction field: (p+3)*8*N + 8*N bytes.  Flops per step follow the paper's IOP cost model
     (eq 41): 2 nz(A~) + (2p-1) N + p + 8 (N+p), with nz(A~) = 5N + pN + (p-1) for the 5-point stencil.
     Per accepted substep (Algorithm 3 / start vector): read V(1:N,1:j), write w, read w, write v_1:
-    (8j + 8 + 16) N bytes and 2 j N flops.  Once per solve: ||B||_1 reads p N values.
+    (8j + 8 + 16) N bytes and 2 j N flops.  Once per solve: ||B||_1 reads p N values.  Per iteration the
+    small exponential (expm_flops) when the iterations' trace is given.
     """
     N, p = P.n, P.p
     steps, substeps = stats["matvecs"], stats["substeps"]
@@ -64,8 +80,10 @@ def algorithmic_model(P, stats):
     flops_sub = 2 * j_avg * N
     total_bytes = steps * bytes_step + substeps * bytes_sub + p * 8 * N
     total_flops = steps * flops_step + substeps * flops_sub
-    return {"bytes_per_solve": total_bytes, "fp64_flops_per_solve": total_flops, "bytes_per_step": bytes_step,
-            "flops_per_step": flops_step}
+    exp_flops = expm_flops(trace) if trace else 0.0
+    return {"bytes_per_solve": total_bytes, "fp64_flops_per_solve": total_flops + exp_flops,
+            "bytes_per_step": bytes_step, "flops_per_step": flops_step, "expm_flops_per_solve": exp_flops,
+            "iop_update_flops_per_solve": total_flops}
 
 
 # ------------------------------------------------------------------ clocks
@@ -367,7 +385,17 @@ def run_gpu(args):
         if dist:
             dist.destroy_process_group()
         return
-    model = algorithmic_model(P, st)
+    # one traced and one profiled solve (untimed): the iterations' Krylov dimensions and ||tau H~||_1 for the
+    # exponential's flops, and the exponential's share of the solve time from the device phase counters
+    _, _, trace = solver.solve(op, P.tau, b, P.tol, m_init=P.m_init, m_o=P.m_o, trace=True)
+    prof = kiops.Solver(device=local, profile=True)
+    pop = prof.operator(P.op)
+    _, pst = prof.solve(pop, P.tau, b, P.tol, m_init=P.m_init, m_o=P.m_o)
+    torch.cuda.synchronize(dev)
+    cyc = pst["phase_cycles"]
+    expm_share = (cyc[6] + cyc[7] + cyc[8]) / max(1, sum(cyc))
+    prof.close()
+    model = algorithmic_model(P, st, trace)
     mean_s = total_s / args.steps
     pk = peaks()
     fp64_peak_tflops = 1.25  # nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json
@@ -385,8 +413,12 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp64_peak_tflops, "traffic": traffic,
                      "kernel": "kiops_solve_kernel<double, stencil2d, grid>",
-                     "note": "FP64 flops of the eq-41 IOP cost model + update, per solve / event-timed solve; "
-                             "peak = nominal FP64 (no measured FP64 peak on file)"},
+                     "note": "FP64 flops per solve (eq-41 IOP cost model per Krylov step, the update, and "
+                             "(8+s) 2 (j+1)^3 per small exponential) / event-timed solve; peak = nominal FP64 "
+                             "(no measured FP64 peak on file)",
+                     "flops_per_solve": {"iop_and_update": model["iop_update_flops_per_solve"],
+                                         "exponentials": model["expm_flops_per_solve"]}},
+        "expm_share_of_solve_time": expm_share,
         "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
         "engine": {"blocks": st["grid_blocks"], "kind": "grid (persistent cooperative)"},

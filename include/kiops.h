@@ -119,6 +119,7 @@ typedef struct {
   double tau, t_now, eps, omega, tau_new;
   double cost_a, cost_b;   /* eq 40 for scenario A (keep m, tau from eq 44) and B (keep tau, m from eq 46); see
                               kiops_config.scenario; 0 on breakdown or when no interval is left */
+  double hnorm;            /* ||tau H~||_1 of the iteration's exponential (eq 37) */
 } kiops_trace_rec;
 
 typedef struct kiops_ctx kiops_ctx;

