@@ -89,6 +89,10 @@ typedef struct {
                               (CSR nnz; 5 or 7 per unknown for stencils plus one per unknown and coupling
                               field); N_mult is the multiplication count of Higham's scaling-and-squaring Pade
                               method for the 1-norm of tau H~.  Both costs are in every trace record. */
+  int block_threads;       /* grid engine, FP64 basis: 256 = two blocks of 256 threads per SM, 512 = one block
+                              of 512 threads per SM (half the blocks to reduce over and to synchronise),
+                              0 (default) = automatic: 512 for N <= 65536, else 256.  Other engines and the
+                              FP32 basis use 256. */
 } kiops_config;
 
 typedef struct {

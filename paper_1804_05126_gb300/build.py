@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkiops.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["kiops_kernels_f64.cu", "kiops_kernels_f32.cu", "kiops_server.cu", "kiops_capi.cu", "kiops_integrate.cu"]
+SOURCES = ["kiops_kernels_f64.cu", "kiops_kernels_f64_wide.cu", "kiops_kernels_f32.cu", "kiops_server.cu",
+           "kiops_capi.cu", "kiops_integrate.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

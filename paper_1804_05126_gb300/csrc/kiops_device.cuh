@@ -20,7 +20,12 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
-namespace kiops_dev {
+// A translation unit that builds the kernels with another block size (KIOPS_THREADS) also gives them their
+// own namespace (KIOPS_DEV_NS), so that no kernel or device function of one size shadows the other.
+#ifndef KIOPS_DEV_NS
+#define KIOPS_DEV_NS kiops_dev
+#endif
+namespace KIOPS_DEV_NS {
 
 #ifndef KIOPS_THREADS
 #define KIOPS_THREADS 256
@@ -2042,4 +2047,4 @@ __global__ void __launch_bounds__(kThreads) kiops_server_kernel(const __grid_con
   }
 }
 
-}  // namespace kiops_dev
+}  // namespace KIOPS_DEV_NS

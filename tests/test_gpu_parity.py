@@ -355,3 +355,19 @@ def test_3d_boundaries_in_batched_teams():
         w_ref, _, _ = oracle_solve(P)
         assert sti["status"] == 0 and rel(it[7].cpu().numpy(), w_ref) <= 10 * P.tol
     s.close()
+
+
+@pytest.mark.parametrize("block_threads", [256, 512])
+@pytest.mark.parametrize("make", [W.problem_lap1d, lambda: W.problem_adr2d(n=61, seed=21),
+                                  lambda: W.problem_adr2d(n=512, seed=23),
+                                  lambda: W.problem_gray_scott(n=37, seed=6, precision="fp64", tol=1e-8, tau=1.0)])
+def test_grid_engine_block_sizes(make, block_threads):
+    """The whole-GPU engine with two 256-thread or one 512-thread block per SM: same decisions as the oracle
+    and results within 10 tol."""
+    P = make()
+    s = kiops.Solver(device=0, block_threads=block_threads)
+    w, st, tr = gpu_solve(s, P, trace=True)
+    s.close()
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
+    assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
