@@ -91,8 +91,9 @@ typedef struct {
                               method for the 1-norm of tau H~.  Both costs are in every trace record. */
   int block_threads;       /* grid engine, FP64 basis: 256 = two blocks of 256 threads per SM, 512 = one block
                               of 512 threads per SM (half the blocks to reduce over and to synchronise),
-                              0 (default) = automatic: 512 for N <= 65536, else 256.  Other engines and the
-                              FP32 basis use 256. */
+                              0 (default) = automatic: one block of 512 threads per SM for N <= 65536, one
+                              block of 256 threads per SM for N <= 2^19, else two blocks of 256.  Other
+                              engines and the FP32 basis use two blocks of 256 threads per SM. */
 } kiops_config;
 
 typedef struct {

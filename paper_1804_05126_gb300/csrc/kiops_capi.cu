@@ -138,6 +138,7 @@ void* pick_team_kernel(bool fp32, int kind) {
 }
 
 constexpr size_t kDynSmem = 2 * kTile * kMaxN * sizeof(double);
+constexpr int kMaxTilesPerBlock = 64;  // fused 2D path: larger grids take the separate normalise pass
 
 // Per-solve device layout (each region 256-byte aligned).
 struct Layout {
@@ -214,13 +215,13 @@ kiops_status prepare_kernel(kiops_ctx* ctx, void* fn) {
   return KIOPS_OK;
 }
 
-// 2D tiling of an nx x ny grid over at most `blocks` tiles for the lagged-normalisation path: smallest
+// 2D tiling of an nx x ny grid over at most `tiles` tiles for the lagged-normalisation path: smallest
 // tile area whose halo'd tile (ns species, element size elem) fits the dynamic shared memory; ties go to
 // the wider tile (coalesced rows).  Returns false if no tiling fits.
-bool choose_tiles(int64_t nx, int64_t ny, int ns, int blocks, size_t elem, int& gx, int& gy, int& tw, int& th) {
+bool choose_tiles_k(int64_t nx, int64_t ny, int ns, int tiles, size_t elem, int& gx, int& gy, int& tw, int& th) {
   int64_t best = -1;
-  for (int cx = 1; cx <= blocks && cx <= nx; ++cx) {
-    const int cy = (int)std::min<int64_t>(blocks / cx, ny);
+  for (int cx = 1; cx <= tiles && cx <= nx; ++cx) {
+    const int cy = (int)std::min<int64_t>(tiles / cx, ny);
     if (cy < 1) continue;
     const int w = (int)((nx + cx - 1) / cx), h = (int)((ny + cy - 1) / cy);
     const size_t smem = (size_t)ns * (w + 2) * (h + 2) * elem;
@@ -237,6 +238,14 @@ bool choose_tiles(int64_t nx, int64_t ny, int ns, int blocks, size_t elem, int& 
   return best > 0;
 }
 
+bool choose_tiles(int64_t nx, int64_t ny, int ns, int blocks, size_t elem, int& gx, int& gy, int& tw, int& th) {
+  // the fewest tiles per block (k) for which a tile with its halo fits the tile buffer: k = 1 is one tile
+  // per block; larger grids give each block k tiles in turn
+  for (int k = 1; k <= kMaxTilesPerBlock; ++k)
+    if (choose_tiles_k(nx, ny, ns, k * blocks, elem, gx, gy, tw, th)) return true;
+  return false;
+}
+
 struct Prepared {
   SolveArgs args;
   Layout L;
@@ -251,6 +260,7 @@ struct Prepared {
 void enable_fused_smem(kiops_ctx* ctx, void* fn, int blocks, Prepared& P, int threads = kThreads) {
   SolveArgs& a = P.args;
   if (!a.fused) return;
+  if ((int64_t)a.tile_gx * a.tile_gy > blocks) return;  // several tiles per block: none of the extras
   const size_t elem = a.prec ? 4 : 8;
   const int ns = a.op.nspecies;
   const size_t halo_pts = (size_t)ns * (a.tile_w + 2) * (a.tile_h + 2);
@@ -431,6 +441,13 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   if (st) return st;
   int blocks = engine == KIOPS_ENGINE_GRID ? grid_size(ctx, fn, threads) : 1;
   if (blocks < 1) return fail(ctx, KIOPS_ECUDA, "kernel does not fit on the device");
+  // automatic (measured): FP64 problems of up to 2^19 unknowns keep their step's vectors in L2 and are
+  // bound by the FP64 pipe, which 8 warps per SM keep as busy as 16; one 256-thread block per SM then
+  // halves the blocks to reduce over and synchronise (512^2 ADR: 6.24 -> 5.91 ms).  Larger problems stream
+  // from HBM and keep two blocks per SM (1024^2 ADR: 7.7 ms vs 9.4 ms with one).
+  if (engine == KIOPS_ENGINE_GRID && !fp32 && ctx->cfg.block_threads == 0 && ctx->cfg.grid_blocks == 0 &&
+      threads == kThreads && A->d.n > 65536 && A->d.n <= ((int64_t)1 << 19))
+    blocks = std::min(blocks, ctx->sms);
   Prepared P;
   st = prepare(ctx, A, tau, p, b, tol, m_init, m_o, prec, w, blocks, trace ? trace_cap : 0, P);
   if (st) return st;

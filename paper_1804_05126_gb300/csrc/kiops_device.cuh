@@ -32,6 +32,8 @@ namespace KIOPS_DEV_NS {
 #endif
 constexpr int kThreads = KIOPS_THREADS;  // threads per block (256 or 512)
 constexpr int kWarps = kThreads / 32;
+// blocks per SM the register budget is sized for (two of 256 threads or one of 512: 128 registers a thread)
+constexpr int kMinBlocks = kThreads <= 256 ? 2 : 1;
 constexpr int kMaxM = 256;                 // largest m_max
 constexpr int kMaxN = kMaxM + 1;           // largest exponential size n = j + 1
 constexpr int kMaxP = 16;                  // largest p
@@ -42,6 +44,9 @@ constexpr int kMaxRed = 2 * kMaxWin + 1;   // largest reduction width
 constexpr int kTile = 8;                   // dense matmul tile edge
 constexpr int kMaxDeg = 8;                 // entries of the Taylor degree table
 constexpr int kGramRing = 8;               // Gram rows kept in shared memory (m_o <= kGramRing)
+// elements per pass of the tiled 2D loops that read global memory (loads of a pass issued together)
+template <typename T>
+constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
 constexpr int kMaxTimes = 32;              // Task I: largest number of output times
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ENOTCONV = 3, ST_ETIMEOUT = 4, ST_ECUDA = 5 };
@@ -825,8 +830,172 @@ struct TileWalk {
   }
 };
 
+// Fused step on grids with more tiles than blocks: block `rank` finalises and applies tiles rank,
+// rank + nblk, ... in turn in one tile buffer, without the shared-memory extras (every operand comes from
+// global memory).  The loops take kBatch<T> elements per pass and issue all their loads before the first
+// store (the stores to V and to raw x_{j+1} could alias the loads for the compiler, which would otherwise
+// wait for each element's loads in turn); per element the arithmetic and its order, and the order of the
+// elements, are those of the one-tile form in fused_st2d_phase.
 template <typename T>
-__device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, int i0, int nwin, bool lead,
+__device__ __forceinline__ void fused_st2d_tiles(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0,
+                                                 int nwin, T* V, size_t ldv, double* smem, DotAcc<T>& acc,
+                                                 bool prof_on) {
+  constexpr int U = kBatch<T>;
+  constexpr int kB = 4;  // B columns loaded with the pass's other loads (the rest at their use)
+  const OpDesc& op = a.op;
+  const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, npts = nx * ny;
+  const int ns = op.nspecies;
+  const int p = a.p;
+  const int tid = threadIdx.x;
+  const int bc = op.bc;
+  T* raw = (T*)a.raw;
+  const bool pend = c.fin_pending != 0;
+  const T* src = pend ? raw + (size_t)((j - 1) & 1) * ldv : V + (size_t)(j - 1) * ldv;  // v_j before finalising
+  T* vj = V + (size_t)(j - 1) * ldv;
+  T* xo = raw + (size_t)(j & 1) * ldv;  // raw x_{j+1}
+  const int fnw = pend ? c.fin_nwin : 0;
+  const T fh0 = fnw > 0 ? T(c.fin_h[0]) : T(0), fh1 = fnw > 1 ? T(c.fin_h[1]) : T(0),
+          fh2 = fnw > 2 ? T(c.fin_h[2]) : T(0);
+  const T frs = pend ? T(c.fin_rs) : T(1);
+  const T* f0 = V + (size_t)((pend ? c.fin_i0 : 1) - 1) * ldv;
+  const T* f1 = V + (size_t)((pend ? c.fin_i0 : 1) + (fnw > 1 ? 1 : 0) - 1) * ldv;
+  const T* f2 = V + (size_t)((pend ? c.fin_i0 : 1) + (fnw > 2 ? 2 : 0) - 1) * ldv;
+  const T* w0 = V + (size_t)(i0 - 1) * ldv;  // dot window of step j (v_j itself comes from the tile buffer)
+  const T* w1 = V + (size_t)(i0 + (nwin > 1 ? 1 : 0) - 1) * ldv;
+  const T* nt = ntail_ptr<T>(c);
+  T* st = (T*)smem;
+  const int ntiles = a.tile_gx * a.tile_gy;
+  for (int tile = rank; tile < ntiles; tile += nblk) {
+    if (tile != rank) __syncthreads();  // the previous tile's products have read the tile buffer
+    const int x0 = (tile % a.tile_gx) * a.tile_w, y0 = (tile / a.tile_gx) * a.tile_h;
+    const int tw = min(a.tile_w, (int)nx - x0), th = min(a.tile_h, (int)ny - y0);
+    const int hw = tw + 2, hh = th + 2, plane = hw * hh, tot = ns * plane, E = ns * tw * th;
+    // v_j = (x_j - sum h v) / s over the tile and its one-point halo (halo points recomputed, not stored)
+    {
+      TileWalk wk(tid, hw, hh);
+      for (int eb = tid; eb < tot; eb += U * kThreads) {
+        unsigned code[U];
+        T v[U], a0[U], a1[U], a2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * kThreads;
+          code[u] = ~0u;
+          v[u] = a0[u] = a1[u] = a2[u] = T(0);
+          if (e < tot) {
+            const int sp = wk.s, hy = wk.y, hx = wk.x;
+            wk.next();
+            int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+            gx = (int)bc_index(bc, gx, nx);
+            gy = (int)bc_index(bc, gy, ny);
+            const unsigned own = (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) ? 1u : 0u;
+            if (gx >= 0 && gy >= 0) {
+              code[u] = 2u * ((unsigned)sp * npts + (unsigned)gy * nx + (unsigned)gx) + own;
+              const size_t r = code[u] >> 1;
+              v[u] = src[r];
+              if (pend) {
+                a0[u] = f0[r];
+                if (fnw > 1) a1[u] = f1[r];
+                if (fnw > 2) a2[u] = f2[r];
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * kThreads;
+          if (e < tot) {
+            T x = v[u];
+            if (code[u] != ~0u && pend) {
+              x = fma(-fh0, a0[u], x);
+              if (fnw > 1) x = fma(-fh1, a1[u], x);
+              if (fnw > 2) x = fma(-fh2, a2[u], x);
+              x = x * frs;
+              if (code[u] & 1u) vj[code[u] >> 1] = x;
+            }
+            st[e] = x;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    KIOPS_TICK(12);
+    // A~ v_j on the tile's own points and the step's dots
+    {
+      TileWalk wk(tid, tw, th);
+      for (int eb = tid; eb < E; eb += U * kThreads) {
+        int hu[U];       // index in the tile buffer; species = hu >= plane
+        uint32_t ru[U];  // row of x
+        T dov[U], dtv[U], bv[U][kB], g0v[U], g1v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * kThreads;
+          hu[u] = 0;
+          ru[u] = 0;
+          dov[u] = dtv[u] = g0v[u] = g1v[u] = T(0);
+#pragma unroll
+          for (int t = 0; t < kB; ++t) bv[u][t] = T(0);
+          if (e < E) {
+            const int sp = wk.s, ly = wk.y, lx = wk.x;
+            wk.next();
+            const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
+            const uint32_t r = (uint32_t)sp * npts + pt;
+            hu[u] = sp * plane + (ly + 1) * hw + (lx + 1);
+            ru[u] = r;
+            const int qo = 1 - sp;
+            if (op.diag[sp][sp] != nullptr) dov[u] = diag_val<T>(a, sp, sp, pt);
+            if (ns == 2 && op.diag[sp][qo] != nullptr) dtv[u] = diag_val<T>(a, sp, qo, pt);
+#pragma unroll
+            for (int t = 0; t < kB; ++t)
+              if (t < p) bv[u][t] = bcol<T>(a, t, r);
+            if (i0 != j) g0v[u] = w0[r];
+            if (nwin > 1 && i0 + 1 != j) g1v[u] = w1[r];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (eb + u * kThreads < E) {
+            const int h = hu[u];
+            const int sp = h >= plane ? 1 : 0;
+            const size_t r = ru[u];
+            const int qo = 1 - sp;
+            const bool has_own = op.diag[sp][sp] != nullptr, has_oth = ns == 2 && op.diag[sp][qo] != nullptr;
+            const T* cf = coef_ptr<T>(op, sp);
+            const T ctr = st[h];
+            const T cc = has_own ? cf[0] + dov[u] : cf[0];
+            T xv = cc * ctr;
+            xv = fma(cf[1], st[h - 1], xv);
+            xv = fma(cf[2], st[h + 1], xv);
+            xv = fma(cf[3], st[h - hw], xv);
+            xv = fma(cf[4], st[h + hw], xv);
+            if (has_oth) xv = fma(dtv[u], st[h + (qo - sp) * plane], xv);
+#pragma unroll
+            for (int t = 0; t < kB; ++t)
+              if (t < p) xv = fma(nt[t], bv[u][t], xv);
+            for (int t = kB; t < p; ++t) xv = fma(nt[t], bcol<T>(a, t, r), xv);
+            xo[r] = xv;
+            const T v0 = (i0 == j) ? ctr : g0v[u];
+            acc.add(0, v0, xv);
+            acc.add(kChunk, ctr, v0);
+            if (nwin > 1) {
+              const T v1 = (i0 + 1 == j) ? ctr : g1v[u];
+              acc.add(1, v1, xv);
+              acc.add(kChunk + 1, ctr, v1);
+            }
+            if (nwin > 2) {  // i0 + 2 == j
+              acc.add(2, ctr, xv);
+              acc.add(kChunk + 2, ctr, ctr);
+            }
+            acc.add(2 * kChunk, xv, xv);
+          }
+        }
+      }
+    }
+    KIOPS_TICK(13);
+  }
+}
+
+template <typename T>
+__device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0, int nwin, bool lead,
                                  T* V, size_t ldv, double* smem, DotAcc<T>& acc, bool prof_on) {
   const OpDesc& op = a.op;
   const uint32_t nx = (uint32_t)op.nx, ny = (uint32_t)op.ny, npts = nx * ny;
@@ -854,144 +1023,150 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int j, in
   // max(ring_lo, j - ring_n + 1) are stale
   const int nr = a.ring_n;
   const int ring_valid_from = nr > 0 ? max(c.ring_lo, j - nr + 1) : (1 << 30);
-  if (rank < a.tile_gx * a.tile_gy) {
-    const int bx = rank % a.tile_gx, by = rank / a.tile_gx;
-    const int x0 = bx * a.tile_w, y0 = by * a.tile_h;
-    const int tw = min(a.tile_w, (int)nx - x0), th = min(a.tile_h, (int)ny - y0);
-    if (tw > 0 && th > 0) {
-      const int hw = tw + 2, hh = th + 2, plane = hw * hh;
-      T* ring = (T*)smem;
-      const size_t rstride = (size_t)ns * plane;
-      T* st = nr > 0 ? ring + (size_t)((j - 1) % nr) * rstride : ring;
-      const T* stage = (const T*)(smem + a.sm_stage);
-      T* cache = (T*)(smem + a.sm_cache);
-      const bool cfill = a.cache_on && !c.cache_ok;
-      const int E = ns * tw * th;
-      // halo point e -> 2 r + (1 if the point is this block's own), ~0u outside a Dirichlet grid
-      unsigned* tbl = (unsigned*)(smem + a.sm_tbl);
-      const bool tok = a.stage_on && c.tbl_ok;
-      auto rslot = [&](int k) -> const T* { return ring + (size_t)((k - 1) % nr) * rstride; };
-      const bool rf0 = pend && fnw > 0 && c.fin_i0 >= ring_valid_from;
-      const bool rf1 = pend && fnw > 1 && c.fin_i0 + 1 >= ring_valid_from;
-      const bool rf2 = pend && fnw > 2 && c.fin_i0 + 2 >= ring_valid_from;
-      const T* g0 = rf0 ? rslot(c.fin_i0) : nullptr;
-      const T* g1 = rf1 ? rslot(c.fin_i0 + 1) : nullptr;
-      const T* g2 = rf2 ? rslot(c.fin_i0 + 2) : nullptr;
-      // finalisation over tile + halo; TOK: the index table is filled (no index arithmetic)
-      const bool wtbl = a.stage_on;  // (the argument block is in shared memory)
-      const int bc = op.bc;
-      auto finalize = [&](auto tok_tag) {
-        constexpr bool TOK = decltype(tok_tag)::value;
-        TileWalk wk(tid, hw, hh);
-        for (int e = tid; e < ns * plane; e += kThreads, wk.next()) {
-          unsigned code;
-          if constexpr (TOK) {
-            code = tbl[e];
-          } else {
-            const int sp = wk.s, hy = wk.y, hx = wk.x;
-            int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-            gx = (int)bc_index(bc, gx, nx);
-            gy = (int)bc_index(bc, gy, ny);
-            const bool inside = gx >= 0 && gy >= 0;
-            const unsigned own = (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) ? 1u : 0u;
-            code = inside ? 2u * ((unsigned)sp * npts + (unsigned)gy * nx + (unsigned)gx) + own : ~0u;
-            if (wtbl) tbl[e] = code;
-          }
-          T v = T(0);
-          if (code != ~0u) {
-            const size_t r = code >> 1;
-            v = staged ? stage[e] : src[r];
-            if (pend) {
-              v = fma(-fh0, rf0 ? g0[e] : f0[r], v);
-              if (fnw > 1) v = fma(-fh1, rf1 ? g1[e] : f1[r], v);
-              if (fnw > 2) v = fma(-fh2, rf2 ? g2[e] : f2[r], v);
-              v = v * frs;
-              if (code & 1u) vj[r] = v;
+  const int ntiles = a.tile_gx * a.tile_gy;
+  if (ntiles > nblk) {
+    fused_st2d_tiles<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
+  } else {
+    // one tile per block, with the shared-memory extras
+    if (rank < a.tile_gx * a.tile_gy) {
+      const int bx = rank % a.tile_gx, by = rank / a.tile_gx;
+      const int x0 = bx * a.tile_w, y0 = by * a.tile_h;
+      const int tw = min(a.tile_w, (int)nx - x0), th = min(a.tile_h, (int)ny - y0);
+      if (tw > 0 && th > 0) {
+        const int hw = tw + 2, hh = th + 2, plane = hw * hh;
+        T* ring = (T*)smem;
+        const size_t rstride = (size_t)ns * plane;
+        T* st = nr > 0 ? ring + (size_t)((j - 1) % nr) * rstride : ring;
+        const T* stage = (const T*)(smem + a.sm_stage);
+        T* cache = (T*)(smem + a.sm_cache);
+        const bool cfill = a.cache_on && !c.cache_ok;
+        const int E = ns * tw * th;
+        // halo point e -> 2 r + (1 if the point is this block's own), ~0u outside a Dirichlet grid
+        unsigned* tbl = (unsigned*)(smem + a.sm_tbl);
+        const bool tok = a.stage_on && c.tbl_ok;
+        auto rslot = [&](int k) -> const T* { return ring + (size_t)((k - 1) % nr) * rstride; };
+        const bool rf0 = pend && fnw > 0 && c.fin_i0 >= ring_valid_from;
+        const bool rf1 = pend && fnw > 1 && c.fin_i0 + 1 >= ring_valid_from;
+        const bool rf2 = pend && fnw > 2 && c.fin_i0 + 2 >= ring_valid_from;
+        const T* g0 = rf0 ? rslot(c.fin_i0) : nullptr;
+        const T* g1 = rf1 ? rslot(c.fin_i0 + 1) : nullptr;
+        const T* g2 = rf2 ? rslot(c.fin_i0 + 2) : nullptr;
+        // finalisation over tile + halo; TOK: the index table is filled (no index arithmetic)
+        const bool wtbl = a.stage_on;  // (the argument block is in shared memory)
+        const int bc = op.bc;
+        auto finalize = [&](auto tok_tag) {
+          constexpr bool TOK = decltype(tok_tag)::value;
+          TileWalk wk(tid, hw, hh);
+          for (int e = tid; e < ns * plane; e += kThreads, wk.next()) {
+            unsigned code;
+            if constexpr (TOK) {
+              code = tbl[e];
+            } else {
+              const int sp = wk.s, hy = wk.y, hx = wk.x;
+              int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+              gx = (int)bc_index(bc, gx, nx);
+              gy = (int)bc_index(bc, gy, ny);
+              const bool inside = gx >= 0 && gy >= 0;
+              const unsigned own = (hx >= 1 && hx <= tw && hy >= 1 && hy <= th) ? 1u : 0u;
+              code = inside ? 2u * ((unsigned)sp * npts + (unsigned)gy * nx + (unsigned)gx) + own : ~0u;
+              if (wtbl) tbl[e] = code;
             }
+            T v = T(0);
+            if (code != ~0u) {
+              const size_t r = code >> 1;
+              v = staged ? stage[e] : src[r];
+              if (pend) {
+                v = fma(-fh0, rf0 ? g0[e] : f0[r], v);
+                if (fnw > 1) v = fma(-fh1, rf1 ? g1[e] : f1[r], v);
+                if (fnw > 2) v = fma(-fh2, rf2 ? g2[e] : f2[r], v);
+                v = v * frs;
+                if (code & 1u) vj[r] = v;
+              }
+            }
+            st[e] = v;
           }
-          st[e] = v;
+        };
+        if (tok) finalize(std::true_type{});
+        else finalize(std::false_type{});
+        if (cfill) {  // B columns and coupling fields of the tile's own points (each thread its own e)
+          TileWalk wk(tid, tw, th);
+          for (int e = tid; e < E; e += kThreads, wk.next()) {
+            const int sp = wk.s, ly = wk.y, lx = wk.x;
+            const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
+            const size_t r = (size_t)sp * npts + pt;
+            for (int t = 0; t < p; ++t) cache[(size_t)t * E + e] = bcol<T>(a, t, r);
+            for (int q = 0; q < ns; ++q)  // the point's own coupling entry is kept merged with the centre
+              if (op.diag[sp][q])
+                cache[(size_t)(p + q) * E + e] = q == sp ? coef_ptr<T>(op, sp)[0] + diag_val<T>(a, sp, q, pt)
+                                                         : diag_val<T>(a, sp, q, pt);
+          }
         }
-      };
-      if (tok) finalize(std::true_type{});
-      else finalize(std::false_type{});
-      if (cfill) {  // B columns and coupling fields of the tile's own points (each thread its own e)
-        TileWalk wk(tid, tw, th);
-        for (int e = tid; e < E; e += kThreads, wk.next()) {
-          const int sp = wk.s, ly = wk.y, lx = wk.x;
-          const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
-          const size_t r = (size_t)sp * npts + pt;
-          for (int t = 0; t < p; ++t) cache[(size_t)t * E + e] = bcol<T>(a, t, r);
-          for (int q = 0; q < ns; ++q)  // the point's own coupling entry is kept merged with the centre
-            if (op.diag[sp][q])
-              cache[(size_t)(p + q) * E + e] = q == sp ? coef_ptr<T>(op, sp)[0] + diag_val<T>(a, sp, q, pt)
-                                                       : diag_val<T>(a, sp, q, pt);
-        }
+        __syncthreads();
+        KIOPS_TICK(12);
+        const bool rw0 = i0 != j && i0 >= ring_valid_from, rw1 = nwin > 1 && i0 + 1 != j && i0 + 1 >= ring_valid_from;
+        const T* q0 = rw0 ? rslot(i0) : nullptr;
+        const T* q1 = rw1 ? rslot(i0 + 1) : nullptr;
+        // A~ v_j on the own points and the step's dots; CACHE: B and coupling values from shared memory
+        auto compute = [&](auto cache_tag) {
+          constexpr bool CACHE = decltype(cache_tag)::value;
+          TileWalk wk(tid, tw, th);
+          for (int e = tid; e < E; e += kThreads, wk.next()) {
+            const int sp = wk.s, ly = wk.y, lx = wk.x;
+            const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
+            const size_t r = (size_t)sp * npts + pt;
+            const int h = sp * plane + (ly + 1) * hw + (lx + 1);
+            const T* cf = coef_ptr<T>(op, sp);
+            const T* nt = ntail_ptr<T>(c);
+            const T ctr = st[h];
+            T xv;
+            if constexpr (CACHE) {
+              // centre: (c_0 + own coupling entry) v with the sum read from the cache, then the neighbours,
+              // the other species' coupling and the B block, all from shared memory
+              T cc = cf[0];
+              if (op.diag[sp][sp]) cc = cache[(size_t)(p + sp) * E + e];
+              xv = cc * ctr;
+              xv = fma(cf[1], st[h - 1], xv);
+              xv = fma(cf[2], st[h + 1], xv);
+              xv = fma(cf[3], st[h - hw], xv);
+              xv = fma(cf[4], st[h + hw], xv);
+              for (int q = 0; q < ns; ++q)
+                if (q != sp && op.diag[sp][q]) xv = fma(cache[(size_t)(p + q) * E + e], st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
+              for (int t = 0; t < p; ++t) xv = fma(nt[t], cache[(size_t)t * E + e], xv);
+            } else {
+              // the same arithmetic from global memory, every coupling and B value loaded before its use so
+              // that the loads overlap
+              const int qo = 1 - sp;
+              const bool has_own = op.diag[sp][sp] != nullptr, has_oth = ns == 2 && op.diag[sp][qo] != nullptr;
+              const T d_own = has_own ? diag_val<T>(a, sp, sp, pt) : T(0);
+              const T d_oth = has_oth ? diag_val<T>(a, sp, qo, pt) : T(0);
+              const T cc = has_own ? cf[0] + d_own : cf[0];
+              xv = cc * ctr;
+              xv = fma(cf[1], st[h - 1], xv);
+              xv = fma(cf[2], st[h + 1], xv);
+              xv = fma(cf[3], st[h - hw], xv);
+              xv = fma(cf[4], st[h + hw], xv);
+              if (has_oth) xv = fma(d_oth, st[qo * plane + (ly + 1) * hw + (lx + 1)], xv);
+              xv = add_btail<T>(a, nt, p, r, xv);
+            }
+            xo[r] = xv;
+            const T v0 = (i0 == j) ? ctr : (rw0 ? q0[h] : w0[r]);
+            acc.add(0, v0, xv);
+            acc.add(kChunk, ctr, v0);
+            if (nwin > 1) {
+              const T v1 = (i0 + 1 == j) ? ctr : (rw1 ? q1[h] : w1[r]);
+              acc.add(1, v1, xv);
+              acc.add(kChunk + 1, ctr, v1);
+            }
+            if (nwin > 2) {  // i0 + 2 == j
+              acc.add(2, ctr, xv);
+              acc.add(kChunk + 2, ctr, ctr);
+            }
+            acc.add(2 * kChunk, xv, xv);
+          }
+        };
+        if (a.cache_on) compute(std::true_type{});
+        else compute(std::false_type{});
       }
-      __syncthreads();
-      KIOPS_TICK(12);
-      const bool rw0 = i0 != j && i0 >= ring_valid_from, rw1 = nwin > 1 && i0 + 1 != j && i0 + 1 >= ring_valid_from;
-      const T* q0 = rw0 ? rslot(i0) : nullptr;
-      const T* q1 = rw1 ? rslot(i0 + 1) : nullptr;
-      // A~ v_j on the own points and the step's dots; CACHE: B and coupling values from shared memory
-      auto compute = [&](auto cache_tag) {
-        constexpr bool CACHE = decltype(cache_tag)::value;
-        TileWalk wk(tid, tw, th);
-        for (int e = tid; e < E; e += kThreads, wk.next()) {
-          const int sp = wk.s, ly = wk.y, lx = wk.x;
-          const uint32_t pt = (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + lx);
-          const size_t r = (size_t)sp * npts + pt;
-          const int h = sp * plane + (ly + 1) * hw + (lx + 1);
-          const T* cf = coef_ptr<T>(op, sp);
-          const T* nt = ntail_ptr<T>(c);
-          const T ctr = st[h];
-          T xv;
-          if constexpr (CACHE) {
-            // centre: (c_0 + own coupling entry) v with the sum read from the cache, then the neighbours,
-            // the other species' coupling and the B block, all from shared memory
-            T cc = cf[0];
-            if (op.diag[sp][sp]) cc = cache[(size_t)(p + sp) * E + e];
-            xv = cc * ctr;
-            xv = fma(cf[1], st[h - 1], xv);
-            xv = fma(cf[2], st[h + 1], xv);
-            xv = fma(cf[3], st[h - hw], xv);
-            xv = fma(cf[4], st[h + hw], xv);
-            for (int q = 0; q < ns; ++q)
-              if (q != sp && op.diag[sp][q]) xv = fma(cache[(size_t)(p + q) * E + e], st[q * plane + (ly + 1) * hw + (lx + 1)], xv);
-            for (int t = 0; t < p; ++t) xv = fma(nt[t], cache[(size_t)t * E + e], xv);
-          } else {
-            // the same arithmetic from global memory, every coupling and B value loaded before its use so
-            // that the loads overlap
-            const int qo = 1 - sp;
-            const bool has_own = op.diag[sp][sp] != nullptr, has_oth = ns == 2 && op.diag[sp][qo] != nullptr;
-            const T d_own = has_own ? diag_val<T>(a, sp, sp, pt) : T(0);
-            const T d_oth = has_oth ? diag_val<T>(a, sp, qo, pt) : T(0);
-            const T cc = has_own ? cf[0] + d_own : cf[0];
-            xv = cc * ctr;
-            xv = fma(cf[1], st[h - 1], xv);
-            xv = fma(cf[2], st[h + 1], xv);
-            xv = fma(cf[3], st[h - hw], xv);
-            xv = fma(cf[4], st[h + hw], xv);
-            if (has_oth) xv = fma(d_oth, st[qo * plane + (ly + 1) * hw + (lx + 1)], xv);
-            xv = add_btail<T>(a, nt, p, r, xv);
-          }
-          xo[r] = xv;
-          const T v0 = (i0 == j) ? ctr : (rw0 ? q0[h] : w0[r]);
-          acc.add(0, v0, xv);
-          acc.add(kChunk, ctr, v0);
-          if (nwin > 1) {
-            const T v1 = (i0 + 1 == j) ? ctr : (rw1 ? q1[h] : w1[r]);
-            acc.add(1, v1, xv);
-            acc.add(kChunk + 1, ctr, v1);
-          }
-          if (nwin > 2) {  // i0 + 2 == j
-            acc.add(2, ctr, xv);
-            acc.add(kChunk + 2, ctr, ctr);
-          }
-          acc.add(2 * kChunk, xv, xv);
-        }
-      };
-      if (a.cache_on) compute(std::true_type{});
-      else compute(std::false_type{});
     }
   }
   if (lead && tid < p) {  // tail rows: finalised tail of v_j (c.tail) and the shift K of Theorem 1
@@ -1040,7 +1215,7 @@ template <typename T, int KIND, class Team>
 __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn);
 
 template <typename T, int KIND, bool GRID>
-__global__ void __launch_bounds__(kThreads) kiops_solve_kernel(const SolveArgs* __restrict__ all) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_solve_kernel(const SolveArgs* __restrict__ all) {
   extern __shared__ double smem_dyn[];
   __shared__ Ctl c;
   // The argument block is copied to shared memory: gpu-scope acquires at every barrier invalidate L1,
@@ -1451,7 +1626,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       if (fused) {
         DotAcc<T> dacc;
         dacc.zero();
-        fused_st2d_phase<T>(a, c, team.rank, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+        fused_st2d_phase<T>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
         __syncthreads();
         if (tid == 0) {
           c.ring_lo = (c.ring_lo <= j - 1) ? c.ring_lo : j;  // v_j is now in the ring
@@ -1724,13 +1899,33 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         const T* __restrict__ w0 = V + (size_t)(i0 - 1) * ldv;
         const T* __restrict__ w1 = V + (size_t)(i0 + (nwin > 1 ? 1 : 0) - 1) * ldv;
         const T* __restrict__ w2 = V + (size_t)(i0 + (nwin > 2 ? 2 : 0) - 1) * ldv;
-        for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
-          const int64_t rr = r >= r1 ? N + (r - r1) : r;
-          T xv = xo[rr];
-          xv = fma(-h0, w0[rr], xv);
-          if (nwin > 1) xv = fma(-h1, w1[rr], xv);
-          if (nwin > 2) xv = fma(-h2, w2[rr], xv);
-          xo[rr] = xv * rsT;
+        // kNormU rows per pass, their loads issued before the first store
+        constexpr int kNormU = 4;
+        const int64_t rend = r1 + (lead ? p : 0);
+        for (int64_t rb = r0 + tid; rb < rend; rb += kNormU * kThreads) {
+          int64_t rr[kNormU];
+          T xv[kNormU], a0[kNormU], a1[kNormU], a2[kNormU];
+#pragma unroll
+          for (int u = 0; u < kNormU; ++u) {
+            const int64_t r = rb + (int64_t)u * kThreads;
+            rr[u] = -1;
+            xv[u] = a0[u] = a1[u] = a2[u] = T(0);
+            if (r < rend) {
+              rr[u] = r >= r1 ? N + (r - r1) : r;
+              xv[u] = xo[rr[u]];
+              a0[u] = w0[rr[u]];
+              if (nwin > 1) a1[u] = w1[rr[u]];
+              if (nwin > 2) a2[u] = w2[rr[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kNormU; ++u)
+            if (rr[u] >= 0) {
+              T v = fma(-h0, a0[u], xv[u]);
+              if (nwin > 1) v = fma(-h1, a1[u], v);
+              if (nwin > 2) v = fma(-h2, a2[u], v);
+              xo[rr[u]] = v * rsT;
+            }
         }
       } else {
         for (int64_t r = r0 + tid; r < r1 + (lead ? p : 0); r += kThreads) {
@@ -1903,7 +2098,7 @@ stop:
 // Single-block solve with the argument block passed by value (no staging buffer): the allocation-free
 // entry point uses it.
 template <int KIND>
-__global__ void __launch_bounds__(kThreads) kiops_solve_kernel_byval(const __grid_constant__ SolveArgs args) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_solve_kernel_byval(const __grid_constant__ SolveArgs args) {
   extern __shared__ double smem_dyn[];
   __shared__ Ctl c;
   __shared__ __align__(16) SolveArgs sa;
@@ -1921,7 +2116,7 @@ __global__ void __launch_bounds__(kThreads) kiops_solve_kernel_byval(const __gri
 // the lists (largest estimated work first, each to the least-loaded team).
 // ------------------------------------------------------------------------------------------------
 template <typename T, int KIND>
-__global__ void __launch_bounds__(kThreads) kiops_team_kernel(const SolveArgs* __restrict__ all,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_team_kernel(const SolveArgs* __restrict__ all,
                                                              const int* __restrict__ plan_ptr,
                                                              const int* __restrict__ plan_idx, int team_blocks,
                                                              int n_teams, unsigned int* team_ctr, int* abort_flag,
@@ -1986,7 +2181,7 @@ __device__ __forceinline__ void st_release_sys_u64(unsigned long long* p, unsign
 }
 
 template <int Unused>
-__global__ void __launch_bounds__(kThreads) kiops_server_kernel(const __grid_constant__ ServerDev sd) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_server_kernel(const __grid_constant__ ServerDev sd) {
   extern __shared__ double smem_dyn[];
   __shared__ Ctl c;
   __shared__ __align__(16) SolveArgs sa;

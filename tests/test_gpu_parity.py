@@ -357,13 +357,13 @@ def test_3d_boundaries_in_batched_teams():
     s.close()
 
 
-@pytest.mark.parametrize("block_threads", [256, 512])
+@pytest.mark.parametrize("block_threads", [0, 256, 512])
 @pytest.mark.parametrize("make", [W.problem_lap1d, lambda: W.problem_adr2d(n=61, seed=21),
                                   lambda: W.problem_adr2d(n=512, seed=23),
                                   lambda: W.problem_gray_scott(n=37, seed=6, precision="fp64", tol=1e-8, tau=1.0)])
 def test_grid_engine_block_sizes(make, block_threads):
-    """The whole-GPU engine with two 256-thread or one 512-thread block per SM: same decisions as the oracle
-    and results within 10 tol."""
+    """The whole-GPU engine with two 256-thread or one 512-thread block per SM, and the automatic choice
+    (one 256-thread block per SM for the 512^2 grid): same decisions as the oracle and results within 10 tol."""
     P = make()
     s = kiops.Solver(device=0, block_threads=block_threads)
     w, st, tr = gpu_solve(s, P, trace=True)
@@ -371,3 +371,38 @@ def test_grid_engine_block_sizes(make, block_threads):
     w_ref, st_ref, tr_ref = oracle_solve(P)
     assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
     assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+
+
+def _neumann_adr_problem(n, seed):
+    """h J(u0) of the section 4 ADR problem on its Neumann vertex grid (reflecting boundaries)."""
+    from oracle import integrators as OI
+    pde = W.pde_adr2d(n)
+    op = OI.jacobian_op(pde, W.pde_initial_condition(pde), scale=1e-2)
+    rng = np.random.default_rng(seed)
+    return W.Problem(f"adr_neumann_{n}", op, rng.standard_normal((4, n * n)), 1.0, 1e-8)
+
+
+@pytest.mark.parametrize("blocks", [2, 3])
+@pytest.mark.parametrize("make", [
+    lambda: W.problem_adr2d(n=150, seed=24),                                            # Dirichlet
+    lambda: W.problem_gray_scott(n=97, seed=8, precision="fp64", tol=1e-8, tau=1.0),    # periodic, 2 species
+    lambda: _neumann_adr_problem(131, 25),                                              # reflecting
+    lambda: W.problem_gray_scott(n=128, seed=9, precision="fp32_basis", tol=1e-6, tau=1.0)])
+def test_fused_path_with_several_tiles_per_block(make, blocks):
+    """Grids whose tiles do not fit one per block: every block finalises and applies several tiles in turn
+    (here 2 or 3 blocks for 2-3 x 10^4 unknowns: 3 or 2 tiles per block, ragged tiles included).  Same
+    decisions as the oracle in FP64, results within 10 tol, and the same results as the separate-normalise
+    path up to rounding."""
+    P = make()
+    s = kiops.Solver(device=0, grid_blocks=blocks)
+    w, st, tr = gpu_solve(s, P, trace=True)
+    s.close()
+    u = kiops.Solver(device=0, grid_blocks=blocks, fuse_stencil=False)
+    wu, stu = gpu_solve(u, P)
+    u.close()
+    w_ref, st_ref, tr_ref = oracle_solve(P)
+    assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
+    assert stu["status"] == 0 and rel(wu, w_ref) <= 10 * P.tol
+    if P.precision == "fp64":
+        assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+        assert rel(w, wu) <= 1e-9
