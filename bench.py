@@ -315,7 +315,58 @@ def measure_patterns(dev):
                            "rejected": st["rejected"], "status": st["status"]}
     out["m_o_sweep_adr2d_512"] = {"note": "129 = full Arnoldi (m_max = 128)", **sweep}
     sw.close()
+    out["beyond_l2_step"] = measure_beyond_l2(dev)
     return out
+
+
+STEP_PHASES = (2, 3, 4, 5, 11, 12, 13)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
+
+
+def measure_beyond_l2(dev):
+    """The Krylov step on grids whose step working set exceeds the 129 MB L2: 2048^2 Gray-Scott with the FP32
+    basis (N = 8.4 M) and 2048^2 ADR in FP64 (N = 4.2 M, tau = 1e-2 / 16 so that the Krylov work stays near
+    the 512^2 solve's).  Step time = event-timed solve x the step's share of the device phase counters of a
+    profiled solve / matvecs.  Algorithmic bytes of one step (Algorithm 2, m_o = 2): read v_j, v_{j-1} and
+    the p columns of B, write v_{j+1}: (p + 3) s N, plus the operator's pointwise fields (ns s N)."""
+    import dataclasses
+
+    import torch
+
+    from paper_1804_05126_gb300 import kiops
+
+    hbm = peaks().get("hbm_gbs", 6768.1)
+    cases = [("gray_scott_2048_fp32_basis", W.problem_gray_scott(n=2048), "fp32_basis", 4, 2),
+             ("adr2d_2048_fp64", dataclasses.replace(W.problem_adr2d(n=2048), tau=1e-2 / 16), "fp64", 8, 1)]
+    res = {}
+    for name, P, prec, s_bytes, nfields in cases:
+        sol = kiops.Solver(device=dev.index)
+        prof = kiops.Solver(device=dev.index, profile=True)
+        op, pop = sol.operator(P.op), prof.operator(P.op)
+        b = torch.as_tensor(P.b, device=dev)
+        sol.solve(op, P.tau, b, P.tol, precision=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            _, st = sol.solve(op, P.tau, b, P.tol, precision=prec)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        _, pst = prof.solve(pop, P.tau, b, P.tol, precision=prec)
+        torch.cuda.synchronize(dev)
+        cyc = pst["phase_cycles"]
+        share = sum(cyc[k] for k in STEP_PHASES) / max(1, sum(cyc))
+        step_us = 1e3 * ms * share / st["matvecs"]
+        bytes_step = (P.p + 3) * s_bytes * P.n + nfields * s_bytes * P.n
+        gbs = bytes_step / (step_us * 1e-6) / 1e9
+        res[name] = {"N": P.n, "p": P.p, "ms_per_solve": ms, "matvecs": st["matvecs"], "substeps": st["substeps"],
+                     "step_us": step_us, "step_share_of_solve": share, "bytes_per_step": bytes_step,
+                     "step_gbs": gbs, "step_hbm_frac": gbs / hbm, "grid_blocks": st["grid_blocks"]}
+        sol.close()
+        prof.close()
+    res["note"] = ("step_hbm_frac: algorithmic step bytes / step time / measured copy bandwidth; the FP64 case "
+                   "is bound by the FP64 pipe, not by HBM")
+    return res
 
 
 # ------------------------------------------------------------------ GPU arm

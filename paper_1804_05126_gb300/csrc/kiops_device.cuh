@@ -47,6 +47,8 @@ constexpr int kGramRing = 8;               // Gram rows kept in shared memory (m
 // elements per pass of the tiled 2D loops that read global memory (loads of a pass issued together)
 template <typename T>
 constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
+template <typename T>
+constexpr int kBatchFin = sizeof(T) == 4 ? 8 : 4;  // the finalisation loop (fewer values per element)
 constexpr int kMaxTimes = 32;              // Task I: largest number of output times
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ENOTCONV = 3, ST_ETIMEOUT = 4, ST_ECUDA = 5 };
@@ -872,12 +874,13 @@ __device__ __forceinline__ void fused_st2d_tiles(const SolveArgs& a, Ctl& c, int
     const int hw = tw + 2, hh = th + 2, plane = hw * hh, tot = ns * plane, E = ns * tw * th;
     // v_j = (x_j - sum h v) / s over the tile and its one-point halo (halo points recomputed, not stored)
     {
+      constexpr int UF = kBatchFin<T>;
       TileWalk wk(tid, hw, hh);
-      for (int eb = tid; eb < tot; eb += U * kThreads) {
-        unsigned code[U];
-        T v[U], a0[U], a1[U], a2[U];
+      for (int eb = tid; eb < tot; eb += UF * kThreads) {
+        unsigned code[UF];
+        T v[UF], a0[UF], a1[UF], a2[UF];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 0; u < UF; ++u) {
           const int e = eb + u * kThreads;
           code[u] = ~0u;
           v[u] = a0[u] = a1[u] = a2[u] = T(0);
@@ -901,7 +904,7 @@ __device__ __forceinline__ void fused_st2d_tiles(const SolveArgs& a, Ctl& c, int
           }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 0; u < UF; ++u) {
           const int e = eb + u * kThreads;
           if (e < tot) {
             T x = v[u];
