@@ -4,7 +4,8 @@
   phi_k(z) = (phi_{k-1}(z) - 1/(k-1)!) / z (|z| >= 1), itself pinned to quadrature of eq 3.
 * :func:`augmented` — the matrix A~ and vector v of Theorem 1 (eq 13), built from its definition.
 * :func:`exact_dense` — top N entries of scipy.linalg.expm(tau A~) v (Theorem 1, eq 14).
-* :func:`exact_dst_1d` / :func:`exact_dst_3d` — closed forms for Dirichlet Laplacians (+ constant shift)
+* :func:`exact_dst_1d` / :func:`exact_dst_2d` / :func:`exact_dst_3d` — closed forms for Dirichlet Laplacians
+  (+ constant shift)
   through the orthonormal DST-I eigenbasis, w = sum_k S diag(tau^k phi_k(tau lambda)) S^T b_k.
 """
 from math import factorial
@@ -68,6 +69,18 @@ def exact_dst_1d(n: int, coeff: float, b: np.ndarray, tau: float, shift: float =
     for k in range(b.shape[0]):
         w += _dst(tau**k * phi(k, tau * lam) * _dst(b[k], axes=[0]), axes=[0])
     return w
+
+
+def exact_dst_2d(n: int, diff: float, shift: float, b: np.ndarray, tau: float):
+    h = 1.0 / (n + 1)
+    kk = np.arange(1, n + 1)
+    l1 = diff * (-4.0 / h**2) * np.sin(kk * np.pi * h / 2) ** 2
+    lam = l1[:, None] + l1[None, :] + shift
+    w = np.zeros((n, n))
+    for k in range(b.shape[0]):
+        bk = b[k].reshape(n, n)
+        w += _dst(tau**k * phi(k, tau * lam) * _dst(bk, axes=[0, 1]), axes=[0, 1])
+    return w.reshape(-1)
 
 
 def exact_dst_3d(n: int, diff: float, shift: float, b: np.ndarray, tau: float):

@@ -406,3 +406,36 @@ def test_fused_path_with_several_tiles_per_block(make, blocks):
     if P.precision == "fp64":
         assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
         assert rel(w, wu) <= 1e-9
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32_basis", 1e-6)])
+def test_2048_grid_several_tiles_vs_dst_closed_form(solver, precision, tol):
+    """Full-size pin of the several-tiles path: 2048^2 Dirichlet diffusion + shift (N = 4.2 M, 4 or 2 tiles
+    per block, working set beyond L2) against the DST-I closed form, ||tau A|| ~ 100, p = 3."""
+    from tests.exact import exact_dst_2d
+    n, shift, tau, p = 2048, -10.0, 3e-6, 3
+    h = 1.0 / (n + 1)
+    d = 1.0 / h**2
+    op = {"kind": "stencil2d", "nx": n, "ny": n, "nspecies": 1, "periodic": False,
+          "coef": [[-4.0 * d + shift, d, d, d, d]], "diag": {}}
+    b = np.random.default_rng(31).standard_normal((p + 1, n * n))
+    P = W.Problem("diffusion2d_2048", op, b, tau, tol, precision=precision)
+    w, st = gpu_solve(solver, P)
+    ref = exact_dst_2d(n, 1.0, shift, b, tau)
+    err = rel(w, ref)
+    print(f"2048^2 {precision}: rel err vs DST {err:.2e}, matvecs {st['matvecs']}, substeps {st['substeps']}")
+    assert st["status"] == 0 and err <= 10 * tol
+
+
+def test_3d_160_cube_largest_served_size_vs_dst_closed_form(solver):
+    """The largest grid of the served request mix, 160^3 (N = 4.1 M, 3D stencil, separate normalise pass),
+    against the DST-I closed form: Dirichlet diffusion + shift, ||tau A|| ~ 90, p = 3, FP64, tol 1e-8."""
+    from tests.exact import exact_dst_3d
+    n, shift, tau, p = 160, -20.0, 3e-4, 3
+    b = np.random.default_rng(32).standard_normal((p + 1, n**3))
+    P = W.Problem("diffusion3d_160", W.adr3d(n, shift), b, tau, 1e-8)
+    w, st = gpu_solve(solver, P)
+    ref = exact_dst_3d(n, 1.0, shift, b, tau)
+    err = rel(w, ref)
+    print(f"160^3: rel err vs DST {err:.2e}, matvecs {st['matvecs']}")
+    assert st["status"] == 0 and err <= 10 * P.tol

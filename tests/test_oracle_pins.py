@@ -13,7 +13,7 @@ import scipy.linalg
 
 import oracle
 from paper_1804_05126_gb300 import workloads as W
-from tests.exact import augmented, exact_dense, exact_dst_1d, exact_dst_3d, phi
+from tests.exact import augmented, exact_dense, exact_dst_1d, exact_dst_2d, exact_dst_3d, phi
 from tests.golden_util import paper_constants
 
 
@@ -151,6 +151,24 @@ def test_kiops_3d_diffusion_reaction_vs_dst():
     w, st, _ = oracle.kiops(op, tau, b, tol)
     assert st["status"] == 0
     assert err_ok(w, exact_dst_3d(n, 1.0, shift, b, tau), tol)
+
+
+def test_dst_2d_closed_form_vs_dense_expm():
+    """The 2D DST-I closed form (used at full size against the GPU) equals the dense exponential of the
+    augmented matrix for a Kronecker-sum Dirichlet Laplacian plus shift built here; the oracle agrees."""
+    n, shift, tau = 7, -15.0, 2e-3
+    h = 1.0 / (n + 1)
+    t1 = (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)) / h**2
+    a = np.kron(np.eye(n), t1) + np.kron(t1, np.eye(n)) + shift * np.eye(n * n)
+    rng = np.random.default_rng(12)
+    b = rng.standard_normal((4, n * n))
+    ref = exact_dst_2d(n, 1.0, shift, b, tau)
+    assert rel(ref, exact_dense(a, b, tau)) < 1e-12
+    d = 1.0 / h**2
+    op = {"kind": "stencil2d", "nx": n, "ny": n, "nspecies": 1, "periodic": False,
+          "coef": [[-4.0 * d + shift, d, d, d, d]], "diag": {}}
+    w, st, _ = oracle.kiops(op, tau, b, 1e-10)
+    assert st["status"] == 0 and err_ok(w, ref, 1e-10)
 
 
 def test_kiops_3d_advection_vs_dense():
