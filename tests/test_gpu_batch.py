@@ -78,3 +78,24 @@ def test_autotuner_picks_a_candidate(solver):
     best, timings = tune.tune_batch(solver, items, candidates=(1, 4, 16))
     assert best in (1, 4, 16) and timings[best] == min(timings.values())
     assert tune.cached_team_blocks(items) == best
+
+
+@pytest.mark.parametrize("team_blocks", [2, 3])
+def test_team_engine_2d_grids_with_several_tiles_per_block(solver, team_blocks):
+    """2D stencil requests in the team engine with teams of 2 or 3 blocks: grids of 1.4-3 x 10^4 unknowns
+    need several tiles per block, which each team takes in turn (Dirichlet ADR in FP64, periodic two-species
+    Gray-Scott in FP64 and with the FP32 basis, mixed in one launch); every result within 10 tol of the
+    oracle."""
+    probs = [W.problem_adr2d(n=150, seed=41), W.problem_adr2d(n=121, seed=42, p=2),
+             W.problem_gray_scott(n=97, seed=43, precision="fp64", tol=1e-8, tau=1.0),
+             W.problem_gray_scott(n=128, seed=44, precision="fp32_basis", tol=1e-6, tau=1.0)]
+    items = []
+    for P in probs:
+        items += make_items(solver, [P], precision=P.precision)
+    stats = solver.solve_batch(items, team_blocks=team_blocks)
+    torch.cuda.synchronize()
+    for P, it, st in zip(probs, items, stats):
+        w_ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+        w = it[7].cpu().numpy()
+        assert st["status"] == 0
+        assert np.linalg.norm(w - w_ref) <= 10 * P.tol * np.linalg.norm(w_ref), P.name
