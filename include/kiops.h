@@ -80,7 +80,8 @@ typedef struct {
                               last m_o + 1 basis vectors, 2 = the next raw tile prefetched (cp.async) during
                               the cross-block sum, 4 = the tile's B columns and coupling fields; -1 (default) =
                               automatic.  A combination that would lower the co-resident block count is
-                              dropped.  Results are bit-identical for every value. */
+                              dropped, and grids with more tiles than blocks (each block takes several
+                              tiles in turn) use none.  Results are bit-identical for every value. */
   int scenario;            /* 0 (default): Algorithm 4 chooses the next m and tau.  1: after an iteration in
                               Algorithm 4's vary-m branch the cheaper of the two scenarios of section 3.2 is
                               taken, by the cost of eq 40 with eqs 41-42: A keeps m and takes tau from eq 44
