@@ -44,11 +44,12 @@ constexpr int kMaxRed = 2 * kMaxWin + 1;   // largest reduction width
 constexpr int kTile = 8;                   // dense matmul tile edge
 constexpr int kMaxDeg = 8;                 // entries of the Taylor degree table
 constexpr int kGramRing = 8;               // Gram rows kept in shared memory (m_o <= kGramRing)
-// elements per pass of the tiled 2D loops that read global memory (loads of a pass issued together)
+// elements per pass of the several-tiles 2D loops, which read global memory (the loads of a pass are
+// issued together): products (six values an element) and finalisation (three or four)
 template <typename T>
 constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
 template <typename T>
-constexpr int kBatchFin = sizeof(T) == 4 ? 8 : 4;  // the finalisation loop (fewer values per element)
+constexpr int kBatchFin = sizeof(T) == 4 ? 8 : 4;
 constexpr int kMaxTimes = 32;              // Task I: largest number of output times
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ENOTCONV = 3, ST_ETIMEOUT = 4, ST_ECUDA = 5 };
@@ -834,8 +835,8 @@ struct TileWalk {
 
 // Fused step on grids with more tiles than blocks: block `rank` finalises and applies tiles rank,
 // rank + nblk, ... in turn in one tile buffer, without the shared-memory extras (every operand comes from
-// global memory).  The loops take kBatch<T> elements per pass and issue all their loads before the first
-// store (the stores to V and to raw x_{j+1} could alias the loads for the compiler, which would otherwise
+// global memory).  The loops take kBatchFin<T> (finalisation) or kBatch<T> (products) elements per pass
+// and issue all their loads before the first store (the stores to V and to raw x_{j+1} could alias the loads for the compiler, which would otherwise
 // wait for each element's loads in turn); per element the arithmetic and its order, and the order of the
 // elements, are those of the one-tile form in fused_st2d_phase.
 template <typename T>
