@@ -11,6 +11,9 @@ Functions
 * :func:`expm`   diagonal Pade with scaling and squaring (section 3.3.1, Higham 2005).
 * :func:`apply`  y = A x for an operator description.
 * :func:`iop`    Algorithm 2 alone, returning V and H (for the eq 30 / Theorem 2 invariants).
+* :func:`cost_eq40`, :func:`n_mult`, :func:`op_nonzeros`  the section 3.2 cost model's pieces.
+* :class:`Alg4`  Algorithm 4 with eqs 39, 43-46 for one iteration at a time (the adaptivity memory of the
+  substep is kept between calls), for scripted error-estimate sequences.
 
 Pins (checked in ``tests/test_oracle_pins.py`` against things other than the oracle itself): dense
 ``scipy.linalg.expm`` of the Theorem 1 augmented matrix, the tail of eq 15, DST-I closed forms for
@@ -30,18 +33,24 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kiops_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable flags: it runs on x86_64 and aarch64 hosts)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc at -O3 (portable flags, no -march: it runs on x86_64 and aarch64 hosts and
+    must give the same results on both).  openmp=True builds the all-core variant used only to time the CPU
+    baseline (the parity oracle is the serial build)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        extra = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-std=c11", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 def _bc_code(op: dict) -> int:
@@ -74,29 +83,58 @@ class _Trace(C.Structure):
                 ("hnorm", C.c_double)]
 
 
-def _load():
-    global _lib
+class _Alg4State(C.Structure):
+    _fields_ = [("have_prev", C.c_int), ("prev_j", C.c_int), ("prev_tau", C.c_double), ("prev_omega", C.c_double),
+                ("prev_eps", C.c_double), ("kappa", C.c_double), ("qp1_est", C.c_double)]
+
+
+class _Alg4Out(C.Structure):
+    _fields_ = [("omega", C.c_double), ("accepted", C.c_int), ("kappa", C.c_double), ("qp1", C.c_double),
+                ("remaining", C.c_double), ("tau_new", C.c_double), ("m_new", C.c_int)]
+
+
+def _load(parallel: bool = False):
+    """The serial parity oracle, or (parallel=True) its OpenMP build for the all-core baseline timing."""
+    global _lib, _lib_omp
     with _lock:
+        if parallel:
+            if _lib_omp is None:
+                _lib_omp = _declare(C.CDLL(build(openmp=True)))
+            return _lib_omp
         if _lib is None:
-            lib = C.CDLL(build())
-            lib.oracle_apply.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_void_p]
-            lib.oracle_apply.restype = None
-            lib.oracle_expm.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
-            lib.oracle_expm.restype = C.c_int
-            lib.oracle_iop.argtypes = [C.POINTER(_Op), C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
-                                       C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_int),
-                                       C.POINTER(C.c_int)]
-            lib.oracle_iop.restype = C.c_int
-            lib.oracle_kiops.argtypes = [C.POINTER(_Op), C.c_double, C.c_int, C.c_void_p, C.c_double, C.c_int,
-                                         C.POINTER(_Opts), C.c_void_p, C.c_void_p, C.POINTER(_Trace), C.c_int64,
-                                         C.POINTER(C.c_int64)]
-            lib.oracle_kiops.restype = C.c_int
-            lib.oracle_kiops_task1.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double,
-                                               C.c_int, C.POINTER(_Opts), C.c_void_p, C.c_void_p, C.POINTER(_Trace),
-                                               C.c_int64, C.POINTER(C.c_int64)]
-            lib.oracle_kiops_task1.restype = C.c_int
-            _lib = lib
+            _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """Argument and result types of the exported functions."""
+    lib.oracle_apply.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_void_p]
+    lib.oracle_apply.restype = None
+    lib.oracle_expm.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
+    lib.oracle_expm.restype = C.c_int
+    lib.oracle_iop.argtypes = [C.POINTER(_Op), C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                               C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_int),
+                               C.POINTER(C.c_int)]
+    lib.oracle_iop.restype = C.c_int
+    lib.oracle_kiops.argtypes = [C.POINTER(_Op), C.c_double, C.c_int, C.c_void_p, C.c_double, C.c_int,
+                                 C.POINTER(_Opts), C.c_void_p, C.c_void_p, C.POINTER(_Trace), C.c_int64,
+                                 C.POINTER(C.c_int64)]
+    lib.oracle_kiops.restype = C.c_int
+    lib.oracle_kiops_task1.argtypes = [C.POINTER(_Op), C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double,
+                                       C.c_int, C.POINTER(_Opts), C.c_void_p, C.c_void_p, C.POINTER(_Trace),
+                                       C.c_int64, C.POINTER(C.c_int64)]
+    lib.oracle_kiops_task1.restype = C.c_int
+    lib.oracle_alg4.argtypes = [C.POINTER(_Alg4State), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
+                                C.POINTER(_Alg4Out)]
+    lib.oracle_alg4.restype = None
+    lib.oracle_cost_eq40.argtypes = [C.c_double] * 7
+    lib.oracle_cost_eq40.restype = C.c_double
+    lib.oracle_n_mult.argtypes = [C.c_double]
+    lib.oracle_n_mult.restype = C.c_double
+    lib.oracle_op_nonzeros.argtypes = [C.POINTER(_Op)]
+    lib.oracle_op_nonzeros.restype = C.c_double
+    return lib
 
 
 def _ptr(a):
@@ -192,18 +230,53 @@ def iop(op: dict, b: np.ndarray, v: np.ndarray, m: int, m_o: int = 2, breakdown_
     return V.T.copy(), H, j.value, bool(bd.value)
 
 
+def cost_eq40(remaining: float, tau: float, m: float, n: float, p: float, nz: float, n_mult: float) -> float:
+    """Eq 40 with eqs 41-42: the cost of finishing `remaining` with steps tau and Krylov dimension m."""
+    return float(_load().oracle_cost_eq40(remaining, tau, m, n, p, nz, n_mult))
+
+
+def n_mult(x: float) -> float:
+    """Multiplications of the scaling-and-squaring Pade method of [47] for a matrix of 1-norm x (eq 42)."""
+    return float(_load().oracle_n_mult(x))
+
+
+def op_nonzeros(op: dict) -> float:
+    """nz of eq 41 for an operator description (reading R9: the operator's stored nonzeros)."""
+    s, keep = _make_op(op)
+    return float(_load().oracle_op_nonzeros(C.byref(s)))
+
+
+class Alg4:
+    """The oracle's Algorithm 4 (eq 39, sections 3.6.1-3.6.2, readings R2-R5) driven one iteration at a time:
+    the same function Algorithm 1 calls after every exponential.  The adaptivity memory of the substep
+    (kappa of eq 45, the order estimate of eq 43, the last rejected iteration) is kept between calls."""
+
+    def __init__(self, m_min: int = 10, m_max: int = 128, T_end: float = 1.0, tol: float = 1e-8):
+        self.m_min, self.m_max, self.T_end, self.tol = m_min, m_max, T_end, tol
+        self._st = _Alg4State()
+
+    def step(self, new_substep: bool, j: int, m: int, tau: float, t_now: float, eps: float,
+             breakdown: bool = False) -> dict:
+        out = _Alg4Out()
+        _load().oracle_alg4(C.byref(self._st), int(new_substep), j, m, self.m_min, self.m_max, tau, t_now,
+                            self.T_end, self.tol, eps, int(breakdown), C.byref(out))
+        return {"omega": out.omega, "accepted": bool(out.accepted), "kappa": out.kappa, "qp1": out.qp1,
+                "remaining": out.remaining, "tau_new": out.tau_new, "m_new": out.m_new}
+
+
 def kiops(op: dict, tau: float, b: np.ndarray, tol: float, m_init: int = 10, m_min: int = 10, m_max: int = 128,
           m_o: int = 2, normalize: bool = True, breakdown_tol: float = 1e-12, max_substeps: int = 10**6,
           max_iterations: int = 10**7, literal_last_row: bool = False, trace_cap: int = 100000,
-          scenario: int = 0):
+          scenario: int = 0, parallel: bool = False):
     """Algorithm 1 (Task II).  b has shape (p+1, N) in natural order b_0..b_p.
 
     Returns (w, stats, trace): stats = dict(substeps, rejected, matvecs, m_last, iterations, status),
     trace = list of per-iteration dicts (j, tau, t_now, eps, omega, accepted, breakdown, m_new, tau_new, and
     the eq 40 costs cost_a / cost_b of the two scenarios).  scenario = 1 lets the cheaper scenario replace
-    Algorithm 4's change of m (reading R9 of the C source).
+    Algorithm 4's change of m (reading R9 of the C source).  parallel=True runs the OpenMP build on the
+    threads OMP_NUM_THREADS allows (CPU-baseline timing only; its sums are split over threads).
     """
-    lib = _load()
+    lib = _load(parallel)
     s, keep = _make_op(op)
     b = np.ascontiguousarray(b, dtype=np.float64)
     p = b.shape[0] - 1

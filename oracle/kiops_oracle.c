@@ -7,6 +7,10 @@
  * benchmark may load this code; the product path never does.  It shares no code, header, table or
  * helper with the CUDA implementation.
  *
+ * The vector loops carry OpenMP work-sharing pragmas.  The parity oracle is compiled without OpenMP,
+ * so they are ignored there and every loop runs serially in its written order; a second build with
+ * -fopenmp serves only the all-core timing of the CPU baseline (its sums are then split over threads).
+ *
  * Every function names the passage it follows.  The steps are taken in the paper's order:
  *   Theorem 1 (eqs 13-15, corrigendum eqs 18-19)  augmented matrix  Ã = [[A, B], [0, K]]
  *   Algorithm 1                                    substepping driver (Task II: one output time)
@@ -119,6 +123,7 @@ static double stencil_x(const oracle_op* A, const double* x, int s, int64_t ix, 
 
 void oracle_apply(const oracle_op* A, const double* x, double* y) {
   if (A->kind == 0) {
+#pragma omp parallel for
     for (int64_t i = 0; i < A->n; ++i) {
       double acc = 0.0;
       for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) acc += A->vals[k] * x[A->colind[k]];
@@ -128,6 +133,7 @@ void oracle_apply(const oracle_op* A, const double* x, double* y) {
     int64_t nx = A->nx, ny = A->ny, nz = A->kind == 2 ? A->nz : 1;
     int ns = A->kind == 2 ? 1 : A->nspecies;
     int64_t npts = nx * ny * nz;
+#pragma omp parallel for collapse(3)
     for (int s = 0; s < ns; ++s)
       for (int64_t iz = 0; iz < nz; ++iz)
         for (int64_t iy = 0; iy < ny; ++iy)
@@ -148,6 +154,7 @@ void oracle_apply(const oracle_op* A, const double* x, double* y) {
             y[(int64_t)s * npts + pt] = acc;
           }
   } else {
+#pragma omp parallel for
     for (int64_t i = 0; i < A->n; ++i) {
       double acc = 0.0;
       for (int64_t k = 0; k < A->n; ++k) acc += A->dense[i * A->n + k] * x[k];
@@ -165,6 +172,7 @@ void oracle_apply(const oracle_op* A, const double* x, double* y) {
  * steps, q R = p is solved by Gaussian elimination with partial pivoting, and R is squared s times.
  * ---------------------------------------------------------------------------------------------- */
 static void matmul(int n, const double* a, const double* b, double* c) {
+#pragma omp parallel for
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
       double s = 0.0;
@@ -313,6 +321,14 @@ static double cost_remaining(double rem, double tau, double m, double N, double 
   return ceil(rem / tau) * (cost_iop(m, N, p, nz) + cost_exp(nmult, m, p));
 }
 
+/* The cost model's pieces as exported entry points (for the pins of the tests): eq 40 with eqs 41-42,
+ * the N_mult of [47] and nz(A~) of reading R9. */
+double oracle_cost_eq40(double rem, double tau, double m, double N, double p, double nz, double nmult) {
+  return cost_remaining(rem, tau, m, N, p, nz, nmult);
+}
+double oracle_n_mult(double x) { return n_mult(x); }
+double oracle_op_nonzeros(const oracle_op* A) { return op_nonzeros(A); }
+
 /* ------------------------------------------------------------------------------------------------
  * Augmented matrix-vector product (Algorithm 2 lines 4-6; Theorem 1 with B = [b_p, ..., b_1]).
  * x has N + p entries: x[0:N] the state, x[N+t] (t = 0..p-1) the tail; tail row t pairs with
@@ -325,6 +341,7 @@ static void aug_matvec(const oracle_op* A, int p, const double* const* b, double
   for (int t = 0; t < p; ++t) {
     const double* col = b[p - t];
     double c = nu * x[N + t];
+#pragma omp parallel for
     for (int64_t i = 0; i < N; ++i) y[i] += col[i] * c;
   }
   for (int t = 0; t + 1 < p; ++t) y[N + t] = x[N + t + 1];
@@ -333,6 +350,7 @@ static void aug_matvec(const oracle_op* A, int p, const double* const* b, double
 
 static double dot(const double* a, const double* b, int64_t n) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
@@ -356,6 +374,7 @@ static int iop(const oracle_op* A, int p, const double* const* b, double nu, dou
       const double* vi = V + (size_t)(i - 1) * M;
       double hij = dot(vi, x, M);
       h[(i - 1) * ldh + (j - 1)] = hij;
+#pragma omp parallel for
       for (int64_t r = 0; r < M; ++r) x[r] -= hij * vi[r];
     }
     double s = sqrt(dot(x, x, M));
@@ -366,6 +385,7 @@ static int iop(const oracle_op* A, int p, const double* const* b, double nu, dou
     h[j * ldh + (j - 1)] = s;
     double inv = 1.0 / s;
     double* vn = V + (size_t)j * M;
+#pragma omp parallel for
     for (int64_t r = 0; r < M; ++r) vn[r] = inv * x[r];
   }
   *jp = j;
@@ -394,6 +414,95 @@ int oracle_iop(const oracle_op* A, int p, const double* b_flat, const double* v_
 }
 
 /* ------------------------------------------------------------------------------------------------
+ * Algorithm 4 (with eq 39, section 3.6.1 eqs 43-44 and section 3.6.2 eqs 45-46) for one iteration,
+ * as a pure function of the iteration's outcome and the adaptivity memory of the current substep.
+ *   eq 39        omega = T_end eps / (tau tol); accepted iff omega <= delta = 1.4; omega = 0 on breakdown
+ *   R3           kappa (eq 45) and the order estimate (eq 43 read as R2) start from their defaults at each
+ *                new substep and are updated when this iteration is rejected right after a rejected one:
+ *                kappa = (omega/omega_old)^(1/(m_old - m)) when m changed and tau did not (kappa <= 1 or
+ *                non-finite -> 2); q+1 = log(eps/eps_old)/log(tau/tau_old) when tau changed and m did not
+ *                (<= 0 or non-finite -> m/4, section 3.6.1's q = m/4 - 1)
+ *   lines 4-8    breakdown: tau_new = min(tau, remaining), m_new = m
+ *   lines 9-13   j == m_max and rejected: m_new = j, tau_new = tau (gamma_max/omega)^(1/(q+1)) clipped to
+ *                [tau/5, remaining]
+ *   line 15      j == m_max and accepted: eq 44 with gamma = 0.9, clipped to [tau/5, 5 tau] and remaining
+ *   line 18      otherwise: tau kept, m_new from eq 46 (R4)
+ * "remaining" is R5's: T_end - (T_now + tau) after an accepted iteration, T_end - T_now after a rejected one.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct {
+  int have_prev, prev_j;   /* the previous iteration of this substep was rejected (R3) */
+  double prev_tau, prev_omega, prev_eps;
+  double kappa;            /* eq 45 estimate (default 2, section 3.6.2) */
+  double qp1_est;          /* eq 43 estimate of q+1 (0 = none yet) */
+} oracle_alg4_state;
+
+typedef struct {
+  double omega;
+  int accepted;
+  double kappa, qp1;       /* the values this iteration's decision used */
+  double remaining;
+  double tau_new;
+  int m_new;
+} oracle_alg4_out;
+
+void oracle_alg4(oracle_alg4_state* st, int new_substep, int j, int m, int m_min, int m_max, double tau,
+                 double t_now, double T_end, double tol, double eps, int breakdown, oracle_alg4_out* out) {
+  const double delta = 1.4, gamma = 0.9, gamma_max = 0.6; /* section 3.5, Algorithm 4 lines 2-3 */
+  if (new_substep) {
+    st->have_prev = 0; st->prev_j = 0;
+    st->prev_tau = st->prev_omega = st->prev_eps = 0.0;
+    st->kappa = 2.0; st->qp1_est = 0.0;
+  }
+  const double omega = breakdown ? 0.0 : T_end * eps / (tau * tol); /* eq 39; line 5 */
+  const int accepted = omega <= delta;
+  const double remaining = T_end - (accepted ? t_now + tau : t_now);
+  if (!accepted && st->have_prev) { /* R3 */
+    if (j != st->prev_j && tau == st->prev_tau) {
+      double k = pow(omega / st->prev_omega, 1.0 / (double)(st->prev_j - j)); /* eq 45 */
+      st->kappa = (isfinite(k) && k > 1.0) ? k : 2.0;
+    } else if (j == st->prev_j && tau != st->prev_tau) {
+      double e = log(eps / st->prev_eps) / log(tau / st->prev_tau); /* eq 43, read as R2 */
+      st->qp1_est = (isfinite(e) && e > 0.0) ? e : 0.0;
+    }
+  }
+  const double qp1 = st->qp1_est > 0.0 ? st->qp1_est : (double)j / 4.0; /* section 3.6.1: q = m/4 - 1 */
+  double tau_new;
+  int m_new;
+  if (breakdown) { /* lines 4-8 */
+    tau_new = tau < remaining ? tau : remaining;
+    m_new = m;
+  } else if (j == m_max) { /* lines 9-16 */
+    if (omega > delta) {
+      m_new = j;
+      tau_new = tau * pow(gamma_max / omega, 1.0 / qp1);
+      if (tau_new < tau / 5.0) tau_new = tau / 5.0;
+      if (tau_new > remaining) tau_new = remaining;
+    } else { /* section 3.6.1, eq 44 */
+      m_new = m;
+      tau_new = tau * pow(gamma / omega, 1.0 / qp1);
+      if (!(tau_new <= 5.0 * tau)) tau_new = 5.0 * tau;
+      if (tau_new < tau / 5.0) tau_new = tau / 5.0;
+      if (tau_new > remaining) tau_new = remaining;
+    }
+  } else { /* line 18: section 3.6.2, eq 46, R4 */
+    tau_new = tau;
+    double mn = (double)m + log(omega / gamma) / log(st->kappa);
+    double lo = floor(0.75 * (double)m), hi = ceil(4.0 * (double)m / 3.0);
+    if (!(mn >= lo)) mn = lo;
+    if (mn > hi) mn = hi;
+    mn = ceil(mn);
+    if (mn < m_min) mn = m_min;
+    if (mn > m_max) mn = m_max;
+    m_new = (int)mn;
+  }
+  if (!accepted) { /* lines 26-28 keep the basis; this iteration becomes the "old" one (R3) */
+    st->have_prev = 1; st->prev_j = j; st->prev_tau = tau; st->prev_omega = omega; st->prev_eps = eps;
+  }
+  out->omega = omega; out->accepted = accepted; out->kappa = st->kappa; out->qp1 = qp1;
+  out->remaining = remaining; out->tau_new = tau_new; out->m_new = m_new;
+}
+
+/* ------------------------------------------------------------------------------------------------
  * Algorithm 1 with Algorithms 2-4.
  *   T, n_steps  output times T(1) < ... < T(end) (Task II: one time)
  *   task1       Task I: outputs at every T(l), scaled by (1/T(l))^p (Algorithm 1 lines 31-35)
@@ -408,7 +517,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
                       oracle_trace* trace, int64_t trace_cap, int64_t* trace_len) {
   const double T_end = T[n_steps - 1];
   int ell = 0;  /* current output column (Algorithm 1 line 6) */
-  const double delta = 1.4, gamma = 0.9, gamma_max = 0.6; /* section 3.5, Algorithm 4 line 2 */
+  const double gamma = 0.9, gamma_max = 0.6; /* Algorithm 4 line 2 (scenario A of the cost model, R9) */
   int64_t N = A->n, M = N + p;
   int m_min = o->m_min, m_max = o->m_max, m_o = o->m_o;
   const double* b[8];
@@ -451,9 +560,9 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
   double tau = T_end, t_now = 0.0, beta = 0.0;
   int j = 0, rc = ORACLE_OK;
   int64_t substeps = 0, rejected = 0, matvecs = 0, iters = 0;
-  /* adaptivity memory of the current substep (R3) */
-  int have_prev = 0, prev_j = 0;
-  double prev_tau = 0, prev_omega = 0, prev_eps = 0, kappa = 2.0, qp1_est = 0.0;
+  /* adaptivity memory of the current substep (R3), reset by the first iteration of every substep */
+  oracle_alg4_state a4;
+  int new_sub = 1;
 
   while (t_now < T_end) { /* line 9 */
     if (iters >= o->max_iterations || substeps >= o->max_substeps) { rc = ORACLE_ENOTCONV; break; }
@@ -472,9 +581,10 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
         break;
       }
       double inv = 1.0 / beta;
+#pragma omp parallel for
       for (int64_t r = 0; r < M; ++r) V[r] *= inv; /* line 14 */
       memset(h, 0, (size_t)ldh * ldh * sizeof(double));
-      have_prev = 0; kappa = 2.0; qp1_est = 0.0;
+      new_sub = 1;
     }
     int breakdown = iop(A, p, b, nu, V, h, ldh, &j, m, m_o, o->breakdown_tol, x, &matvecs); /* line 16 */
 
@@ -490,58 +600,18 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
     const double hnorm = norm1(n, ht); /* ||tau H~||_1, for the cost model (R9) */
     if (oracle_expm(n, ht, F) != ORACLE_OK) { rc = ORACLE_ENOTCONV; break; }
 
-    /* line 19: eqs 36, 38; line 22: eq 39 */
-    double eps = 0.0, omega = 0.0;
-    if (!breakdown) {
-      eps = beta * h[j * ldh + (j - 1)] * fabs(F[(j - 1) * n + j]);
-      omega = T_end * eps / (tau * tol);
-    }
-    int accepted = omega <= delta;
+    /* line 19: eqs 36, 38 */
+    double eps = 0.0;
+    if (!breakdown) eps = beta * h[j * ldh + (j - 1)] * fabs(F[(j - 1) * n + j]);
+    /* lines 20-22: eq 39 and Algorithm 4 */
+    oracle_alg4_out d;
+    oracle_alg4(&a4, new_sub, j, m, m_min, m_max, tau, t_now, T_end, tol, eps, breakdown, &d);
+    new_sub = 0;
+    const double omega = d.omega, remaining = d.remaining, qp1 = d.qp1, kappa = d.kappa;
+    const int accepted = d.accepted;
     double t_next = accepted ? t_now + tau : t_now;
-    double remaining = T_end - t_next;
-
-    /* R3: estimates from two consecutive rejections */
-    if (!accepted && have_prev) {
-      if (j != prev_j && tau == prev_tau) {
-        double k = pow(omega / prev_omega, 1.0 / (double)(prev_j - j)); /* eq 45 */
-        kappa = (isfinite(k) && k > 1.0) ? k : 2.0;
-      } else if (j == prev_j && tau != prev_tau) {
-        double e = log(eps / prev_eps) / log(tau / prev_tau); /* eq 43, read as R2 */
-        qp1_est = (isfinite(e) && e > 0.0) ? e : 0.0;
-      }
-    }
-    double qp1 = qp1_est > 0.0 ? qp1_est : (double)j / 4.0; /* section 3.6.1: q = m/4 - 1 */
-
-    /* line 20: Algorithm 4 */
-    double tau_new;
-    int m_new;
-    if (breakdown) { /* lines 4-8 */
-      tau_new = tau < remaining ? tau : remaining;
-      m_new = m;
-    } else if (j == m_max) { /* lines 9-16 */
-      if (omega > delta) {
-        m_new = j;
-        tau_new = tau * pow(gamma_max / omega, 1.0 / qp1);
-        if (tau_new < tau / 5.0) tau_new = tau / 5.0;
-        if (tau_new > remaining) tau_new = remaining;
-      } else { /* section 3.6.1, eq 44 */
-        m_new = m;
-        tau_new = tau * pow(gamma / omega, 1.0 / qp1);
-        if (!(tau_new <= 5.0 * tau)) tau_new = 5.0 * tau;
-        if (tau_new < tau / 5.0) tau_new = tau / 5.0;
-        if (tau_new > remaining) tau_new = remaining;
-      }
-    } else { /* line 18: section 3.6.2, eq 46, R4 */
-      tau_new = tau;
-      double mn = (double)m + log(omega / gamma) / log(kappa);
-      double lo = floor(0.75 * (double)m), hi = ceil(4.0 * (double)m / 3.0);
-      if (!(mn >= lo)) mn = lo;
-      if (mn > hi) mn = hi;
-      mn = ceil(mn);
-      if (mn < m_min) mn = m_min;
-      if (mn > m_max) mn = m_max;
-      m_new = (int)mn;
-    }
+    double tau_new = d.tau_new;
+    int m_new = d.m_new;
 
     /* R9: eq 40 for both scenarios; opts.scenario = 1 takes the cheaper one in the line 18 branch */
     double cost_a = 0.0, cost_b = 0.0;
@@ -604,6 +674,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
         }
       }
       double* wl = W + (size_t)ell * N; /* the last line of Algorithm 3: w = beta V(1:N,1:j) F(1:j,1) */
+#pragma omp parallel for
       for (int64_t r = 0; r < N; ++r) {
         double s = 0.0;
         for (int c = 0; c < j; ++c) s += V[(size_t)c * M + r] * F[c * n + 0];
@@ -615,7 +686,6 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
       substeps++;
     } else { /* lines 26-28: keep the basis */
       rejected++;
-      have_prev = 1; prev_j = j; prev_tau = tau; prev_omega = omega; prev_eps = eps;
     }
     tau = tau_new;
     m = m_new;
