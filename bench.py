@@ -60,30 +60,61 @@ def expm_flops(trace):
     return total
 
 
-def algorithmic_model(P, stats, trace=None):
-    """Bytes and FP64 flops one solve must move/do (independent of this implementation).
+def op_nonzeros(op: dict) -> int:
+    """nz(A~) of eq 41 as the operator's stored nonzeros (the B block is eq 41's separate (2p-1)N + p term):
+    CSR nnz; 5 (2D) or 7 (3D) per unknown plus one per unknown and pointwise coupling field."""
+    if op["kind"] == "csr":
+        return int(op["rowptr"][-1])
+    if op["kind"] == "stencil2d":
+        npts = int(op["nx"]) * int(op["ny"])
+        fields = sum(1 for d in op.get("diag", {}).values() if d is not None)
+        return 5 * npts * int(op["nspecies"]) + fields * npts
+    npts = int(op["nx"]) * int(op["ny"]) * int(op["nz"])
+    return 7 * npts + (npts if op.get("diag") is not None else 0)
 
-    Per Krylov step (Algorithm 2): read v_j, v_{j-1} and the p columns of B, write v_{j+1}, read the
-    operator's reaction field: (p+3)*8*N + 8*N bytes.  Flops per step follow the paper's IOP cost model
-    (eq 41): 2 nz(A~) + (2p-1) N + p + 8 (N+p), with nz(A~) = 5N + pN + (p-1) for the 5-point stencil.
-    Per accepted substep (Algorithm 3 / start vector): read V(1:N,1:j), write w, read w, write v_1:
-    (8j + 8 + 16) N bytes and 2 j N flops.  Once per solve: ||B||_1 reads p N values.  Per iteration the
-    small exponential (expm_flops) when the iterations' trace is given.
+
+def algorithmic_model(P, stats, trace):
+    """Bytes and FP64 flops one solve must move/do (independent of this implementation), from the iterations'
+    trace of an untimed solve with the same decisions.
+
+    Flops: eq 41 summed over the substeps, cost_iop(j) = j[(2 nz + (2p-1)N + p) + 8(N+p)] - 4(N+p) + 3(N+p)j
+    with j the substep's final Krylov dimension (their sum is the matvec count, rejections' extensions
+    included); 2 j N per accepted substep for the update w = beta V(1:N,1:j) F(1:j,1); (8 + s) 2 (j+1)^3 per
+    iteration for the small exponential (expm_flops).
+    Bytes per Krylov step (Algorithm 2): read v_j, v_{j-1} and the p columns of B, write v_{j+1}, read the
+    operator's pointwise fields: (p+3) 8 N + fields 8 N.  Per accepted substep (Algorithm 3 and the next start
+    vector): read V(1:N,1:j), write w, read w, write v_1: (8j + 8 + 16) N.  Once per solve: ||B||_1 reads p N.
     """
     N, p = P.n, P.p
     steps, substeps = stats["matvecs"], stats["substeps"]
-    j_avg = 128  # every substep of this workload ends at m_max (see the recorded trace)
-    bytes_step = (p + 3) * 8 * N + 8 * N
-    nz = 5 * N + p * N + (p - 1)
-    flops_step = 2 * nz + (2 * p - 1) * N + p + 8 * (N + p)
-    bytes_sub = (8 * j_avg + 8 + 16) * N
-    flops_sub = 2 * j_avg * N
-    total_bytes = steps * bytes_step + substeps * bytes_sub + p * 8 * N
-    total_flops = steps * flops_step + substeps * flops_sub
-    exp_flops = expm_flops(trace) if trace else 0.0
-    return {"bytes_per_solve": total_bytes, "fp64_flops_per_solve": total_flops + exp_flops,
-            "bytes_per_step": bytes_step, "flops_per_step": flops_step, "expm_flops_per_solve": exp_flops,
-            "iop_update_flops_per_solve": total_flops}
+    nz = op_nonzeros(P.op)
+    fields = (nz - 5 * N) // N if P.op["kind"] == "stencil2d" else 0
+    acc_j = [t["j"] for t in trace if t["accepted"]]
+    last_j = {}
+    for t in trace:
+        last_j[t["substep"]] = t["j"]
+    assert sum(last_j.values()) == steps and len(acc_j) == substeps
+    per_step = 2 * nz + (2 * p - 1) * N + p + 8 * (N + p) + 3 * (N + p)
+    flops_iop = steps * per_step - 4 * (N + p) * len(last_j)
+    flops_upd = sum(2 * j * N for j in acc_j)
+    bytes_step = (p + 3) * 8 * N + fields * 8 * N
+    total_bytes = steps * bytes_step + sum((8 * j + 8 + 16) * N for j in acc_j) + p * 8 * N
+    exp_flops = expm_flops(trace)
+    return {"bytes_per_solve": total_bytes, "fp64_flops_per_solve": flops_iop + flops_upd + exp_flops,
+            "bytes_per_step": bytes_step, "flops_per_step": per_step, "nz": nz, "expm_flops_per_solve": exp_flops,
+            "iop_flops_per_solve": flops_iop, "update_flops_per_solve": flops_upd}
+
+
+def fp64_peak(solver, device_index):
+    """FP64 peak measured in this run: the library's FMA-chain probe (best of repeated calls) with the SM
+    clocks sampled while it runs."""
+    from paper_1804_05126_gb300 import kiops
+    vals = []
+    with ClockSampler(device_index) as clk:
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 1.0 or len(vals) < 5:
+            vals.append(kiops.kiops_probe_fp64(solver.ctx))
+    return max(vals) / 1e12, clk.summary()
 
 
 # ------------------------------------------------------------------ clocks
@@ -180,19 +211,45 @@ def peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def cpu_baseline(P, budget_s=12.0):
+def _oracle_rate(problems, parallel, budget_s, max_solves):
+    """Solves/s of the oracle over `problems` taken in turn until the budget or the count is reached."""
     import oracle
-    oracle.build()
     t0 = time.perf_counter()
     n = 0
     while True:
-        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+        P = problems[n % len(problems)]
+        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o, parallel=parallel)
         n += 1
-        if time.perf_counter() - t0 > budget_s or n >= 20:
+        if time.perf_counter() - t0 > budget_s or n >= max_solves:
             break
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} complete solves of the {WORKLOAD} workload by the serial FP64 C oracle"}
+    return n / (time.perf_counter() - t0), n
+
+
+def cpu_baseline(P, budget_s=10.0):
+    """The oracle (plain FP64 C, -O3) on the host cores: the headline workload with every host core (OpenMP
+    build) and with one, plus bounded samples of the batched and served workloads.  A reported baseline."""
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    oracle.build(openmp=True)
+    v_all, n_all = _oracle_rate([P], True, budget_s, 20)
+    v_one, n_one = _oracle_rate([P], False, budget_s, 20)
+    batch = W.batch_3d(count=16)
+    v_b, n_b = _oracle_rate(batch, True, budget_s, 16)
+    reqs = [q for _, q in W.request_stream(16, seed=1005, n_range=(16, 64))]
+    v_r, n_r = _oracle_rate(reqs, True, budget_s, 16)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_all} complete solves of the {WORKLOAD} workload by the FP64 C oracle (gcc -O3, OpenMP "
+                      f"over the vector loops and the exponential's products, {cores} threads)",
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1, "sample": f"{n_one} complete solves, serial build"},
+            "samples": {
+                "batched_3d": {"value": v_b, "unit": UNIT, "cores": cores,
+                               "sample": f"{n_b} solves of the first 16 seeded 3D diffusion-reaction instances "
+                                         "(n in 10..40, FP64, tol 1e-8)"},
+                "served_3d_adr": {"value": v_r, "unit": UNIT, "cores": cores,
+                                  "sample": f"{n_r} solves of 16 seeded requests of the served mix with n <= 64 "
+                                            "(all in FP64 at each request's tolerance)"}}}
 
 
 def run_reference(args):
@@ -201,21 +258,24 @@ def run_reference(args):
         return
     P = workload()
     import oracle
-    oracle.build()
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build(openmp=True)
     for _ in range(args.warmup):
-        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o, parallel=True)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
+        oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o, parallel=True)
         times.append(time.perf_counter() - t0)
     value = len(times) / sum(times)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": config_dict(P, l2="n/a (CPU)"),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{len(times)} complete solves, serial FP64 C oracle on the host"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{len(times)} complete solves, FP64 C oracle (gcc -O3, OpenMP, {cores} "
+                                      "threads) on the host"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -449,7 +509,7 @@ def run_gpu(args):
     model = algorithmic_model(P, st, trace)
     mean_s = total_s / args.steps
     pk = peaks()
-    fp64_peak_tflops = 1.25  # nominal GB300 FP64 (recipe table); no measured FP64 peak in MEASURED_PEAKS.json
+    fp64_peak_tflops, probe_clocks = fp64_peak(solver, local)
     achieved_tflops = model["fp64_flops_per_solve"] / mean_s / 1e12
     traffic = dram_traffic()
     lat = sorted(times_ms)
@@ -464,11 +524,16 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp64_peak_tflops, "traffic": traffic,
                      "kernel": "kiops_solve_kernel<double, stencil2d, grid>",
-                     "note": "FP64 flops per solve (eq-41 IOP cost model per Krylov step, the update, and "
-                             "(8+s) 2 (j+1)^3 per small exponential) / event-timed solve; peak = nominal FP64 "
-                             "(no measured FP64 peak on file)",
-                     "flops_per_solve": {"iop_and_update": model["iop_update_flops_per_solve"],
-                                         "exponentials": model["expm_flops_per_solve"]}},
+                     "note": "achieved = FP64 flops per solve (eq 41 summed over the substeps with nz = the "
+                             "operator's stored nonzeros, 2jN per update, (8+s) 2 (j+1)^3 per small exponential) "
+                             "/ event-timed solve; peak = FP64 FMA throughput measured in this run by "
+                             "kiops_probe_fp64 (burst, best of repeated calls), clocks sampled during the probe",
+                     "peak_source": "measured (kiops_probe_fp64)", "peak_clocks": probe_clocks,
+                     "flops_per_solve": {"iop_eq41": model["iop_flops_per_solve"],
+                                         "update": model["update_flops_per_solve"],
+                                         "exponentials": model["expm_flops_per_solve"],
+                                         "nz": model["nz"], "matvecs": st["matvecs"],
+                                         "substeps": st["substeps"]}},
         "expm_share_of_solve_time": expm_share,
         "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),

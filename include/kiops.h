@@ -289,6 +289,12 @@ kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* 
 /* info[0..5] = pending (not yet admitted), in flight, reserved workspace bytes, small teams, large teams,
  * blocks per large team. */
 kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]);
+/* Self-test of the server's recovery from a device-side wait that gave up (the paper has no counterpart):
+ * raises the server's abort word from the host, as such a wait does.  Running teams stop at their next
+ * check of the word and the kernel exits; requests they had claimed finish with KIOPS_ETIMEOUT (reported
+ * by kiops_poll), requests not yet claimed stay queued, and the next launch clears the word and serves
+ * them.  EINVAL without a server. */
+kiops_status kiops_server_selftest_abort(kiops_ctx* ctx);
 /* Stop the server after the queued work (waits for the kernel), free its memory. */
 kiops_status kiops_server_stop(kiops_ctx* ctx);
 
@@ -343,14 +349,21 @@ kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, d
  * KIOPS_ETIMEOUT when that happened as designed (the context stays usable), KIOPS_ECUDA otherwise. */
 kiops_status kiops_selftest_wait_timeout(kiops_ctx* ctx, double timeout_s);
 
+/* Measured FP64 throughput of the context's GPU in flop/s (the paper has no counterpart: the peak the
+ * FP64-bound phases of the solver are reported against).  Four blocks of 256 threads per SM each run eight
+ * independent chains of dependent FP64 fused multiply-adds (2 flops each); best of five timed launches
+ * after a warm-up, on the context's stream.  Allocates and frees a small result buffer. */
+kiops_status kiops_probe_fp64(kiops_ctx* ctx, double* flops_per_s);
+
 /* Size of the fixed device scratch used by kiops_solve_noalloc (bytes). */
 #define KIOPS_NOALLOC_SCRATCH_BYTES (32u << 20)
 
-/* kiops_solve without any memory allocation, for callers that cannot allocate: code that runs while a
- * stream is being captured into a CUDA graph (cudaMalloc is not allowed there), applications whose device
- * memory is owned by their own pool or allocator and must not be fragmented by a library, and embedded or
- * real-time hosts that forbid allocation after start-up.  (The paper has no counterpart: this is an
- * interface property, not part of the method.)
+/* kiops_solve without any memory allocation.  Some callers cannot let a library allocate device memory
+ * while they run: applications whose device memory is owned by their own pool or allocator (a cudaMalloc
+ * behind their back escapes their accounting, fragments their pool and synchronises the whole device),
+ * and real-time or embedded hosts that forbid allocation after start-up (cudaMalloc may block for an
+ * unbounded time).  This entry point serves them.  (The paper has no counterpart: it is an interface
+ * property, not part of the method.)
  *
  * Same arguments and result as kiops_solve with prec = KIOPS_FP64; the solve runs on one thread block.
  * Instead of the context's cudaMalloc'd workspace it uses one file-scope device array of
@@ -358,11 +371,11 @@ kiops_status kiops_selftest_wait_timeout(kiops_ctx* ctx, double timeout_s);
  * The caller still passes b and w.  Requests whose workspace (Krylov basis of (m_max+1) x (N+p) FP64
  * values, Hessenberg and exponential work matrices) does not fit are rejected with KIOPS_EINVAL and a
  * message giving the bytes needed; with m_max = 128 roughly N + p <= 30000 fits.
- * The first call on a device looks up the array's device address (set-up, once per device, with that
+ * Set-up: the first call on a device looks up the array's device address (once per device, with that
  * device current); make that first call before any stream capture.  Every call shares the one array and
  * it keeps the previous call's contents (the counters it needs are cleared on each call): calls whose
- * GPU work overlaps — from several streams, threads or contexts on the same device — race and give
- * undefined results.  The call waits for its stream before returning. */
+ * GPU work overlaps (from several streams, threads or contexts on the same device) race and give
+ * undefined results.  The call copies the stats back and waits for its stream before returning. */
 kiops_status kiops_solve_noalloc(kiops_ctx* ctx, const kiops_op* A, double tau, int p, const double* const* b,
                                  double tol, int m_init, int m_o, double* w, kiops_stats* stats);
 

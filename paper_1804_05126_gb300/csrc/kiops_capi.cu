@@ -1131,6 +1131,7 @@ struct MappedQueues {  // lives in mapped pinned host memory
 
 struct InFlight {
   int cls = 0, slot = -1;
+  unsigned int index = 0;  // queue index of the request in its class (claimed once head has passed it)
   size_t off = 0, bytes = 0;
   int64_t* stats_dev = nullptr;
 };
@@ -1148,6 +1149,7 @@ struct KiopsServer {
   cudaStream_t kstream = nullptr, cstream = nullptr;
   cudaEvent_t kdone = nullptr;
   bool launched = false;
+  bool exit_checked = false;  // the exited launch's abort word has been read
   // mapped host memory
   MappedQueues* q = nullptr;
   SolveArgs* slots_h[kServerClasses] = {};
@@ -1172,13 +1174,50 @@ namespace {
 kiops_status server_launch(kiops_ctx* ctx, KiopsServer* S) {
   void* fn = kiops_k::server_kernel();
   KCHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
-  // a new launch starts every team's barrier epochs at zero: clear the team counters and claim words
+  // a new launch starts every team's barrier epochs at zero: clear the team counters, the claim words and
+  // the abort word that follows them (raised by a wait of the previous launch that gave up)
   const int n_teams = S->sd.teams[0] + S->sd.teams[1];
-  KCHECK(ctx, cudaMemsetAsync(S->sd.team_ctr, 0, (size_t)n_teams * 64 * 4 * 2, S->kstream));
+  KCHECK(ctx, cudaMemsetAsync(S->sd.team_ctr, 0, (size_t)n_teams * 64 * 4 * 2 + 256, S->kstream));
   void* kargs[] = {(void*)&S->sd};
   KCHECK(ctx, cudaLaunchCooperativeKernel(fn, S->grid, kThreads, kargs, kDynSmem, S->kstream));
   KCHECK(ctx, cudaEventRecord(S->kdone, S->kstream));
   S->launched = true;
+  S->exit_checked = false;
+  return KIOPS_OK;
+}
+
+// Once per exited launch: if a device-side wait gave up (abort word raised), the teams left without
+// finishing the requests they had claimed.  Those tickets finish here with the abort status and give back
+// their slot and workspace; requests still queued (not claimed) run on the next launch.
+kiops_status server_check_exit(kiops_ctx* ctx, KiopsServer* S) {
+  if (!S->launched || S->exit_checked) return KIOPS_OK;
+  const cudaError_t e = cudaEventQuery(S->kdone);
+  if (e == cudaErrorNotReady) return KIOPS_OK;
+  if (e != cudaSuccess) return fail(ctx, KIOPS_ECUDA, "server kernel: %s", cudaGetErrorString(e));
+  S->exit_checked = true;
+  int ab = 0;
+  unsigned int heads[kServerClasses] = {};
+  KCHECK(ctx, cudaMemcpyAsync(&ab, S->sd.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, S->cstream));
+  for (int c = 0; c < kServerClasses; ++c)
+    KCHECK(ctx, cudaMemcpyAsync(heads + c, S->sd.head[c], sizeof(unsigned int), cudaMemcpyDeviceToHost, S->cstream));
+  KCHECK(ctx, cudaStreamSynchronize(S->cstream));
+  if (ab == 0) return KIOPS_OK;
+  std::vector<uint64_t> lost;
+  for (auto& kv : S->inflight) {
+    const InFlight& f = kv.second;
+    const bool claimed = (int)(heads[f.cls] - f.index) > 0;
+    const bool done = *(volatile unsigned long long*)(S->done_h[f.cls] + f.slot) == kv.first;
+    if (claimed && !done) lost.push_back(kv.first);
+  }
+  for (uint64_t t : lost) {
+    const InFlight f = S->inflight[t];
+    std::vector<int64_t> st(16, 0);
+    st[6] = ab;
+    S->finished[t] = st;
+    S->arena.release(f.off, f.bytes);
+    S->slot_busy[f.cls][f.slot] = 0;
+    S->inflight.erase(t);
+  }
   return KIOPS_OK;
 }
 
@@ -1186,6 +1225,8 @@ bool server_kernel_running(KiopsServer* S) { return S->launched && cudaEventQuer
 
 // Admit pending requests (budget and slot permitting), collect completions, relaunch an exited kernel.
 kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
+  kiops_status xs = server_check_exit(ctx, S);
+  if (xs) return xs;
   // completions
   std::vector<uint64_t> done_now;
   for (auto& kv : S->inflight) {
@@ -1224,6 +1265,7 @@ kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
     InFlight f;
     f.cls = c;
     f.slot = slot;
+    f.index = S->next_index[c];
     f.off = off;
     f.bytes = pd.P.L.total;
     f.stats_dev = pd.P.args.stats;
@@ -1428,6 +1470,45 @@ kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]) {
   return KIOPS_OK;
 }
 
+kiops_status kiops_server_selftest_abort(kiops_ctx* ctx) {
+  if (!ctx || !ctx->server) return KIOPS_EINVAL;
+  KiopsServer* S = ctx->server;
+  // a copy-engine write, so it lands while the server kernel occupies every SM
+  const int v = ST_ETIMEOUT;
+  KCHECK(ctx, cudaMemcpyAsync(S->sd.abort_flag, &v, sizeof(int), cudaMemcpyHostToDevice, S->cstream));
+  KCHECK(ctx, cudaStreamSynchronize(S->cstream));
+  return KIOPS_OK;
+}
+
+// ---- FP64 throughput probe -------------------------------------------------------------------------------
+kiops_status kiops_probe_fp64(kiops_ctx* ctx, double* flops_per_s) {
+  if (!ctx || !flops_per_s) return KIOPS_EINVAL;
+  *flops_per_s = 0.0;
+  const int blocks = 4 * ctx->sms, iters = 4096;
+  void* buf = nullptr;
+  KCHECK(ctx, cudaMalloc(&buf, (size_t)blocks * kiops_k::probe_threads() * sizeof(double)));
+  std::unique_ptr<void, cudaError_t (*)(void*)> guard(buf, cudaFree);
+  cudaEvent_t e0, e1;
+  KCHECK(ctx, cudaEventCreate(&e0));
+  KCHECK(ctx, cudaEventCreate(&e1));
+  KCHECK(ctx, kiops_k::launch_fp64_probe(blocks, iters, (double*)buf, ctx->stream));  // warm-up
+  const int reps = 5;
+  float best = 0.0f;
+  for (int r = 0; r < reps; ++r) {
+    KCHECK(ctx, cudaEventRecord(e0, ctx->stream));
+    KCHECK(ctx, kiops_k::launch_fp64_probe(blocks, iters, (double*)buf, ctx->stream));
+    KCHECK(ctx, cudaEventRecord(e1, ctx->stream));
+    KCHECK(ctx, cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    KCHECK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+    if (r == 0 || ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double flops = kiops_k::probe_flops_per_thread(iters) * (double)blocks * kiops_k::probe_threads();
+  *flops_per_s = best > 0.0f ? flops / (1e-3 * (double)best) : 0.0;
+  return KIOPS_OK;
+}
 
 // ---- Self-test of the bounded device-side waits ----------------------------------------------------------
 kiops_status kiops_selftest_wait_timeout(kiops_ctx* ctx, double timeout_s) {

@@ -158,6 +158,7 @@ _SIGS = {
     "kiops_poll": ([C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_int), C.POINTER(kiops_stats)], C.c_int),
     "kiops_server_info": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "kiops_server_stop": ([C.c_void_p], C.c_int),
+    "kiops_server_selftest_abort": ([C.c_void_p], C.c_int),
     "kiops_expm": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "kiops_solve_task1": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                            C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p), C.POINTER(kiops_stats)], C.c_int),
@@ -165,6 +166,7 @@ _SIGS = {
                              C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
     "kiops_pde_rhs": ([C.c_void_p, C.POINTER(kiops_pde), C.c_void_p, C.c_void_p], C.c_int),
     "kiops_selftest_wait_timeout": ([C.c_void_p, C.c_double], C.c_int),
+    "kiops_probe_fp64": ([C.c_void_p, C.POINTER(C.c_double)], C.c_int),
     "kiops_integrate": ([C.c_void_p, C.POINTER(kiops_pde), C.c_int, C.c_double, C.c_double, C.c_int64, C.c_double,
                          C.c_int, C.c_void_p, C.POINTER(kiops_integrate_stats)], C.c_int),
 }
@@ -309,6 +311,13 @@ def kiops_selftest_wait_timeout(ctx, timeout_s: float) -> int:
     return int(lib().kiops_selftest_wait_timeout(ctx, timeout_s))
 
 
+def kiops_probe_fp64(ctx) -> float:
+    """Measured FP64 FMA throughput of the context's GPU (flop/s)."""
+    v = C.c_double(0.0)
+    _check(ctx, lib().kiops_probe_fp64(ctx, C.byref(v)), "kiops_probe_fp64")
+    return v.value
+
+
 def kiops_pde_rhs(ctx, pde: kiops_pde, u_ptr, f_ptr) -> None:
     _check(ctx, lib().kiops_pde_rhs(ctx, C.byref(pde), u_ptr, f_ptr), "kiops_pde_rhs")
 
@@ -361,6 +370,11 @@ def kiops_server_info(ctx) -> dict:
     _check(ctx, lib().kiops_server_info(ctx, v), "kiops_server_info")
     return {"pending": v[0], "in_flight": v[1], "reserved_bytes": v[2], "small_teams": v[3], "large_teams": v[4],
             "large_team_blocks": v[5]}
+
+
+def kiops_server_selftest_abort(ctx) -> None:
+    """Raise the server's abort word from the host (recovery self-test; see include/kiops.h)."""
+    _check(ctx, lib().kiops_server_selftest_abort(ctx), "kiops_server_selftest_abort")
 
 
 def kiops_server_stop(ctx) -> None:

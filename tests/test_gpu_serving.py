@@ -1,5 +1,7 @@
 """Continuous-batching server on the GPU: results alone and in the mix, admission under a budget, a
-served stream checked against the oracle."""
+served stream checked against the oracle, recovery after a device-side wait gave up."""
+import time
+
 import numpy as np
 import pytest
 
@@ -76,3 +78,31 @@ def test_large_class_request(solver):
     res = serve.run_stream(solver, [(0.0, P)])
     ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
     assert np.linalg.norm(res["w"][0].cpu().numpy() - ref) <= 10 * P.tol * np.linalg.norm(ref)
+
+
+def test_server_recovers_after_an_abort():
+    """The abort word a device-side wait raises when it gives up (here raised from the host, no GPU fault):
+    the request the server had claimed reports KIOPS_ETIMEOUT instead of never finishing, and the next
+    launch clears the word and serves a later request correctly."""
+    time.sleep(2.5)  # the module server's kernel has left the GPU (idle limit 2 s), so ours starts at once
+    s = kiops.Solver(device=0)
+    s.server_start(hbm_budget_bytes=4e9, small_team_blocks=8, large_teams=0)
+    P = W.problem_adr2d(n=512, seed=3)
+    op = s.operator(P.op)
+    b = torch.as_tensor(P.b, device="cuda:0")
+    t, _ = s.submit(op, 0.1, b, P.tol)  # hundreds of milliseconds on one team of 8 blocks
+    time.sleep(0.05)  # claimed by then
+    kiops.kiops_server_selftest_abort(s.ctx)
+    with pytest.raises(kiops.KiopsError) as e:
+        t0 = time.time()
+        while not s.poll(t, 1.0)[0]:
+            assert time.time() - t0 < 60, "the claimed request never finished"
+    assert e.value.status == 4
+    assert s.server_info()["in_flight"] == 0
+    _, P2 = small_stream(count=1, seed=21)[0]
+    res = serve.run_stream(s, [(0.0, P2)])
+    ref, _, _ = oracle.kiops(P2.op, P2.tau, P2.b, P2.tol)
+    assert res["stats"][0]["status"] == 0
+    assert np.linalg.norm(res["w"][0].cpu().numpy() - ref) <= 10 * P2.tol * np.linalg.norm(ref)
+    s.server_stop()
+    s.close()

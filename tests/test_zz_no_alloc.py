@@ -1,8 +1,11 @@
-"""The allocation-free entry point kiops_solve_noalloc, checked on the GPU against kiops_solve.
+"""The allocation-free entry point kiops_solve_noalloc, checked on the GPU against kiops_solve and the oracle.
 
-Some callers cannot allocate device memory at solve time (a stream being captured into a CUDA graph,
-applications whose device memory belongs to their own allocator, hosts that forbid allocation after
-start-up); kiops_solve_noalloc serves them from a fixed device array instead of the context's workspace.
+Some callers cannot let a library allocate device memory while they run: applications whose device
+memory belongs to their own pool or allocator (a hidden cudaMalloc escapes their accounting and
+synchronises the device) and hosts that forbid allocation after start-up.  kiops_solve_noalloc serves
+them from a fixed device array instead of the context's workspace.  Each case makes two calls in a row
+(the array keeps the previous call's contents) and compares both with kiops_solve and with the FP64 CPU
+oracle of the method.
 This file is collected last so that a run stopping at the first failure has run every other test.
 """
 import numpy as np
@@ -14,6 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle  # noqa: E402
 from paper_1804_05126_gb300 import kiops, workloads as W  # noqa: E402
 
 
@@ -34,6 +38,7 @@ def test_noalloc_matches_kiops_solve_on_two_calls_in_a_row(solver, make):
     b = torch.as_tensor(P.b, device="cuda:0")
     w_ref, st_ref = solver.solve(op, P.tau, b, P.tol, m_init=P.m_init, m_o=P.m_o)
     ref = w_ref.cpu().numpy()
+    w_or, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o)
     ptrs = [b[k].data_ptr() for k in range(P.p + 1)]
     for call in range(2):
         w = torch.full((P.n,), float("nan"), dtype=torch.float64, device="cuda:0")
@@ -41,6 +46,7 @@ def test_noalloc_matches_kiops_solve_on_two_calls_in_a_row(solver, make):
         got = w.cpu().numpy()
         assert st["status"] == 0 and st["matvecs"] > 0
         assert np.linalg.norm(got - ref) <= 10 * P.tol * np.linalg.norm(ref), call
+        assert np.linalg.norm(got - w_or) <= 10 * P.tol * np.linalg.norm(w_or), call
 
 
 def test_noalloc_rejects_a_solve_larger_than_its_scratch(solver):
