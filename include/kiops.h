@@ -286,9 +286,9 @@ kiops_status kiops_server_start(kiops_ctx* ctx, const kiops_server_config* cfg);
 kiops_status kiops_submit(kiops_ctx* ctx, const kiops_request* req, uint64_t* ticket);
 /* Wait up to timeout_s (0 = just check) for a ticket; *done = 1 and stats filled once it has finished. */
 kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* done, kiops_stats* stats);
-/* info[0..5] = pending (not yet admitted), in flight, reserved workspace bytes, small teams, large teams,
- * blocks per large team. */
-kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]);
+/* info[0..7] = pending (not yet admitted), in flight, reserved workspace bytes, small teams, large teams,
+ * blocks per large team, requests the small and the large teams have claimed since the server started. */
+kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[8]);
 /* Self-test of the server's recovery from a device-side wait that gave up (the paper has no counterpart):
  * raises the server's abort word from the host, as such a wait does.  Running teams stop at their next
  * check of the word and the kernel exits; requests they had claimed finish with KIOPS_ETIMEOUT (reported
@@ -350,9 +350,10 @@ kiops_status kiops_integrate(kiops_ctx* ctx, const kiops_pde* pde, int scheme, d
 kiops_status kiops_selftest_wait_timeout(kiops_ctx* ctx, double timeout_s);
 
 /* Measured FP64 throughput of the context's GPU in flop/s (the paper has no counterpart: the peak the
- * FP64-bound phases of the solver are reported against).  Four blocks of 256 threads per SM each run eight
- * independent chains of dependent FP64 fused multiply-adds (2 flops each); best of five timed launches
- * after a warm-up, on the context's stream.  Allocates and frees a small result buffer. */
+ * FP64-bound phases of the solver are reported against).  Two or four blocks of 256 threads per SM, every
+ * thread running 8 or 16 independent chains of dependent FP64 fused multiply-adds (2 flops each); the best
+ * of three timed launches of each shape after a warm-up, on the context's stream.  Allocates and frees a
+ * small result buffer. */
 kiops_status kiops_probe_fp64(kiops_ctx* ctx, double* flops_per_s);
 
 /* Size of the fixed device scratch used by kiops_solve_noalloc (bytes). */

@@ -1224,10 +1224,8 @@ kiops_status server_check_exit(kiops_ctx* ctx, KiopsServer* S) {
 bool server_kernel_running(KiopsServer* S) { return S->launched && cudaEventQuery(S->kdone) == cudaErrorNotReady; }
 
 // Admit pending requests (budget and slot permitting), collect completions, relaunch an exited kernel.
-kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
-  kiops_status xs = server_check_exit(ctx, S);
-  if (xs) return xs;
-  // completions
+// Finished requests (completion word = ticket): stats back, slot and workspace free.
+kiops_status server_collect(kiops_ctx* ctx, KiopsServer* S) {
   std::vector<uint64_t> done_now;
   for (auto& kv : S->inflight) {
     const InFlight& f = kv.second;
@@ -1244,6 +1242,13 @@ kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
     S->slot_busy[f.cls][f.slot] = 0;
     S->inflight.erase(t);
   }
+  return KIOPS_OK;
+}
+
+kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
+  kiops_status xs = server_check_exit(ctx, S);
+  if (!xs) xs = server_collect(ctx, S);
+  if (xs) return xs;
   // admissions, in arrival order per class (a request that does not fit waits; later ones may pass it)
   bool enqueued = false;
   for (auto it = S->pending.begin(); it != S->pending.end();) {
@@ -1278,10 +1283,12 @@ kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
     it = S->pending.erase(it);
   }
   if ((enqueued || !S->inflight.empty()) && !server_kernel_running(S)) {
-    if (S->launched) {
-      cudaError_t e = cudaEventQuery(S->kdone);
-      if (e != cudaSuccess) return fail(ctx, KIOPS_ECUDA, "server kernel: %s", cudaGetErrorString(e));
-    }
+    // the kernel may have exited after the check at the top: collect what an abort left before the
+    // relaunch clears the abort word
+    kiops_status xs2 = server_check_exit(ctx, S);
+    if (!xs2) xs2 = server_collect(ctx, S);
+    if (xs2) return xs2;
+    if (S->inflight.empty()) return KIOPS_OK;
     kiops_status st = server_launch(ctx, S);
     if (st) return st;
   }
@@ -1456,7 +1463,7 @@ kiops_status kiops_server_stop(kiops_ctx* ctx) {
   return rc;
 }
 
-kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]) {
+kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[8]) {
   if (!ctx || !info || !ctx->server) return KIOPS_EINVAL;
   KiopsServer* S = ctx->server;
   size_t free_bytes = 0;
@@ -1467,6 +1474,12 @@ kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[6]) {
   info[3] = S->sd.teams[0];
   info[4] = S->sd.teams[1];
   info[5] = S->sd.team_blocks[1];
+  unsigned int heads[kServerClasses] = {};  // copy-engine reads: they proceed while the kernel runs
+  for (int c = 0; c < kServerClasses; ++c)
+    KCHECK(ctx, cudaMemcpyAsync(heads + c, S->sd.head[c], sizeof(unsigned int), cudaMemcpyDeviceToHost, S->cstream));
+  KCHECK(ctx, cudaStreamSynchronize(S->cstream));
+  info[6] = heads[0];
+  info[7] = heads[1];
   return KIOPS_OK;
 }
 
@@ -1484,29 +1497,32 @@ kiops_status kiops_server_selftest_abort(kiops_ctx* ctx) {
 kiops_status kiops_probe_fp64(kiops_ctx* ctx, double* flops_per_s) {
   if (!ctx || !flops_per_s) return KIOPS_EINVAL;
   *flops_per_s = 0.0;
-  const int blocks = 4 * ctx->sms, iters = 4096;
+  const int iters = 4096, max_blocks = 4 * ctx->sms;
   void* buf = nullptr;
-  KCHECK(ctx, cudaMalloc(&buf, (size_t)blocks * kiops_k::probe_threads() * sizeof(double)));
+  KCHECK(ctx, cudaMalloc(&buf, (size_t)max_blocks * kiops_k::probe_threads() * sizeof(double)));
   std::unique_ptr<void, cudaError_t (*)(void*)> guard(buf, cudaFree);
   cudaEvent_t e0, e1;
   KCHECK(ctx, cudaEventCreate(&e0));
   KCHECK(ctx, cudaEventCreate(&e1));
-  KCHECK(ctx, kiops_k::launch_fp64_probe(blocks, iters, (double*)buf, ctx->stream));  // warm-up
-  const int reps = 5;
-  float best = 0.0f;
-  for (int r = 0; r < reps; ++r) {
-    KCHECK(ctx, cudaEventRecord(e0, ctx->stream));
-    KCHECK(ctx, kiops_k::launch_fp64_probe(blocks, iters, (double*)buf, ctx->stream));
-    KCHECK(ctx, cudaEventRecord(e1, ctx->stream));
-    KCHECK(ctx, cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    KCHECK(ctx, cudaEventElapsedTime(&ms, e0, e1));
-    if (r == 0 || ms < best) best = ms;
-  }
+  double best = 0.0;
+  for (int chains : {8, 16})
+    for (int per_sm : {2, 4}) {
+      const int blocks = per_sm * ctx->sms;
+      KCHECK(ctx, kiops_k::launch_fp64_probe(chains, blocks, iters, (double*)buf, ctx->stream));  // warm-up
+      for (int r = 0; r < 3; ++r) {
+        KCHECK(ctx, cudaEventRecord(e0, ctx->stream));
+        KCHECK(ctx, kiops_k::launch_fp64_probe(chains, blocks, iters, (double*)buf, ctx->stream));
+        KCHECK(ctx, cudaEventRecord(e1, ctx->stream));
+        KCHECK(ctx, cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        KCHECK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        const double f = kiops_k::probe_flops_per_thread(chains, iters) * (double)blocks * kiops_k::probe_threads();
+        if (ms > 0.0f) best = std::max(best, f / (1e-3 * (double)ms));
+      }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  const double flops = kiops_k::probe_flops_per_thread(iters) * (double)blocks * kiops_k::probe_threads();
-  *flops_per_s = best > 0.0f ? flops / (1e-3 * (double)best) : 0.0;
+  *flops_per_s = best;
   return KIOPS_OK;
 }
 

@@ -2205,13 +2205,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_server_kernel(cons
       int claimed = -1;
       const long long t0 = global_ns();
       while (true) {
+        if (ld_volatile_int(sd.abort_flag)) break;  // a wait gave up: claim nothing more in this launch
         const unsigned int h = *(volatile unsigned int*)sd.head[cls];
         const unsigned int tl = ld_acquire_sys(sd.tail[cls]);
         if ((int)(tl - h) > 0) {
           if (atomicCAS(sd.head[cls], h, h + 1) == h) { claimed = (int)h; break; }
           continue;
         }
-        if (ld_acquire_sys_int(sd.stop) || ld_volatile_int(sd.abort_flag)) break;
+        if (ld_acquire_sys_int(sd.stop)) break;
         if (global_ns() - t0 > sd.idle_ns) break;
         __nanosleep(1000);
       }

@@ -38,8 +38,9 @@ cudaError_t launch_assemble(const PdeDev& P, const double* un, const double* U2,
 cudaError_t launch_axpy2(int64_t N, double* y, double a1, const double* x1, double a2, const double* x2, int sms,
                          cudaStream_t st);
 // FP64 FMA throughput probe (kiops_probe.cu): `blocks` blocks of probe_threads() threads, each thread
-// doing probe_flops_per_thread(iters) flops; out holds blocks * probe_threads() doubles.
+// running `chains` (8 or 16) FMA chains for probe_flops_per_thread(chains, iters) flops; out holds
+// blocks * probe_threads() doubles.
 int probe_threads();
-double probe_flops_per_thread(int iters);
-cudaError_t launch_fp64_probe(int blocks, int iters, double* out, cudaStream_t st);
+double probe_flops_per_thread(int chains, int iters);
+cudaError_t launch_fp64_probe(int chains, int blocks, int iters, double* out, cudaStream_t st);
 }  // namespace kiops_k

@@ -366,10 +366,10 @@ def kiops_poll(ctx, ticket: int, timeout_s: float = 0.0):
 
 
 def kiops_server_info(ctx) -> dict:
-    v = (C.c_int64 * 6)()
+    v = (C.c_int64 * 8)()
     _check(ctx, lib().kiops_server_info(ctx, v), "kiops_server_info")
     return {"pending": v[0], "in_flight": v[1], "reserved_bytes": v[2], "small_teams": v[3], "large_teams": v[4],
-            "large_team_blocks": v[5]}
+            "large_team_blocks": v[5], "claimed_small": v[6], "claimed_large": v[7]}
 
 
 def kiops_server_selftest_abort(ctx) -> None:

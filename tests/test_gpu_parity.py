@@ -300,15 +300,19 @@ def test_cost_model_costs_and_scenario_choice_match_oracle(make, scenario):
     w_ref, st_ref, tr_ref = oracle_solve(P, scenario=scenario)
     assert st["status"] == 0 and rel(w, w_ref) <= 10 * P.tol
     assert [(t["j"], t["accepted"], t["m_new"]) for t in tr] == [(t["j"], t["accepted"], t["m_new"]) for t in tr_ref]
-    # Within the first substep ||tau H~||_1 depends on the basis only and agrees to rounding.  Step sizes
-    # follow the error estimates through Algorithm 4 (eq 43's order estimate is a log-ratio of tiny estimates
-    # summed in different orders), so later substeps start from slightly different states and every
-    # quantity there, like the tau-dependent costs, agrees to ~1e-6 relative.
+    # Substep 0 starts from the same vector on both sides, so ||tau H~||_1 agrees to rounding.  A later
+    # substep starts from the previous accepted result, which differs between the two sides by up to the
+    # solve's error (10 tol relative), and so does its basis: ||tau H~||_1 there is held to 1e-5 (measured
+    # worst 3.2e-7 at tol 1e-8).  The new step size and the eq 40 costs depend on the iteration's omega only
+    # through eq 44 (a power 1/(q+1) of gamma/omega) and otherwise on integers, tau and the remaining
+    # interval, so they are held to 1e-12 plus twice the iteration's relative difference in omega (measured:
+    # equal to 1e-15 in every substep).
     for t, r in zip(tr, tr_ref):
-        if t["substep"] == 0:
-            assert t["hnorm"] == pytest.approx(r["hnorm"], rel=1e-10, abs=0.0), (t, r)
-        for k in ("cost_a", "cost_b", "tau_new", "hnorm"):
-            assert t[k] == pytest.approx(r[k], rel=1e-5, abs=0.0), (k, t, r)
+        d_om = abs(t["omega"] - r["omega"]) / r["omega"] if r["omega"] > 0 else 0.0
+        tol_h = 1e-10 if t["substep"] == 0 else 1e-5
+        assert t["hnorm"] == pytest.approx(r["hnorm"], rel=tol_h, abs=0.0), (t, r)
+        for k in ("cost_a", "cost_b", "tau_new"):
+            assert t[k] == pytest.approx(r[k], rel=1e-12 + 2 * d_om, abs=0.0), (k, t, r)
 
 
 def _adr3d_problem(n, bc, p, seed, tau=1e-3, tol=1e-9):

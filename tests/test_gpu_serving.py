@@ -84,14 +84,16 @@ def test_server_recovers_after_an_abort():
     """The abort word a device-side wait raises when it gives up (here raised from the host, no GPU fault):
     the request the server had claimed reports KIOPS_ETIMEOUT instead of never finishing, and the next
     launch clears the word and serves a later request correctly."""
-    time.sleep(2.5)  # the module server's kernel has left the GPU (idle limit 2 s), so ours starts at once
     s = kiops.Solver(device=0)
     s.server_start(hbm_budget_bytes=4e9, small_team_blocks=8, large_teams=0)
     P = W.problem_adr2d(n=512, seed=3)
     op = s.operator(P.op)
     b = torch.as_tensor(P.b, device="cuda:0")
-    t, _ = s.submit(op, 0.1, b, P.tol)  # hundreds of milliseconds on one team of 8 blocks
-    time.sleep(0.05)  # claimed by then
+    t, _ = s.submit(op, 0.1, b, P.tol)  # 1664 matvecs: far longer than the claim, on one team of 8 blocks
+    t0 = time.time()
+    while s.server_info()["claimed_small"] < 1:  # a team has taken the request
+        assert time.time() - t0 < 30, "the request was never claimed"
+        time.sleep(0.001)
     kiops.kiops_server_selftest_abort(s.ctx)
     with pytest.raises(kiops.KiopsError) as e:
         t0 = time.time()
