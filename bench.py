@@ -379,7 +379,7 @@ def measure_patterns(dev):
     return out
 
 
-STEP_PHASES = (2, 3, 4, 5, 11, 12, 13)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
+STEP_PHASES = (2, 3, 4, 5, 11, 12, 13, 14)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
 
 
 def measure_beyond_l2(dev):

@@ -95,6 +95,18 @@ typedef struct {
                               0 (default) = automatic: one block of 512 threads per SM for N <= 65536, one
                               block of 256 threads per SM for N <= 2^19, else two blocks of 256.  Other
                               engines and the FP32 basis use two blocks of 256 threads per SM. */
+  int tma;                 /* grid engine, 2D stencils whose grid has more tiles than blocks: stage each tile's
+                              operands in shared memory with bulk tensor copies (TMA), ahead of the tile being
+                              computed.  1 (default) = with an FP32 basis only (FP64 steps are bound by the FP64
+                              pipe and run faster with per-element loads), 2 = with either basis, 0 = never.
+                              Used where the row length and the plane size are multiples of 16 bytes. */
+  int tile_w, tile_h;      /* that path's tile shape (points; tile_w a multiple of 4); 0, 0 (default) =
+                              automatic.  A shape that does not fit the shared memory at the launch's block
+                              count is replaced by the automatic choice. */
+  int tma_stages;          /* that path's tiles in flight per block (2 to 6; 0 = 2) */
+  int tma_prefetch;        /* that path's L2 lookahead: tiles fetched into L2 (bulk prefetch, no shared memory)
+                              this many tiles before their shared-memory copy is issued; 0 = none, -1 (default)
+                              = automatic (tma_stages + 2) */
 } kiops_config;
 
 typedef struct {
@@ -111,7 +123,8 @@ typedef struct {
   /* SM cycles by phase when cfg.profile is set (rank-0 view): 0 setup, 1 start vector, 2 step matvec+dots
    * and block reduction, 3 step cross-block sum, 4 step coefficients, 5 step normalise, 6 expm powers,
    * 7 expm Horner, 8 expm squarings, 9 control, 10 update, 11 grid barrier waits, 12 tiled path:
-   * finalisation of v_j, 13 tiled path: A~ v_j and dots; other entries 0. */
+   * finalisation of v_j, 13 tiled path: A~ v_j and dots, 14 tiled path with bulk tensor copies: waits for a
+   * tile's copies; other entries 0. */
   int64_t phase_cycles[16];
 } kiops_stats;
 

@@ -4,7 +4,9 @@
 // (the whole GPU works on one solve), the CTA engine launches one block per request of a batch.  The
 // host only validates arguments, lays out the workspace, uploads the argument block and reads back the
 // statistics; every step of Algorithm 1 runs in the kernel of kiops_device.cuh.
+#include <cuda.h>  // tensor-map types (the encoder is reached through the runtime's driver entry point)
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -251,7 +253,153 @@ struct Prepared {
   Layout L;
   char* base;
   size_t dyn_smem = kDynSmem;  // dynamic shared memory of the launch
+  size_t tma_b = 0, tma_f = 0;  // TMA path: workspace offsets of the staged copies of B (FP64) and the fields
+  TmaMaps maps{};               // TMA path: tensor maps (a kernel parameter)
 };
+
+// ---- TMA path of the several-tiles 2D step (grid engine) --------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tile shape, stages and shared-memory layout of the TMA path, if it applies and keeps `blocks` blocks
+// co-resident; the workspace grows by the tensor maps and the staged copies of B (FP64) and the fields.
+bool setup_tma(kiops_ctx* ctx, void* fn, int blocks, int threads, Prepared& P) {
+  SolveArgs& a = P.args;
+  // automatic (tma = 1): FP32 basis only.  FP64 steps are bound by the FP64 pipe, and the staged path measured
+  // slower there (2048^2 ADR 190 -> 202 us per step, 1024^2 Gray-Scott 8.9 -> 11.9 ms per solve)
+  if (!a.fused || ctx->cfg.tma <= 0 || a.op.kind != OP_ST2D || (ctx->cfg.tma == 1 && !a.prec)) return false;
+  if ((int64_t)a.tile_gx * a.tile_gy <= blocks) return false;  // one tile per block: the shared-memory extras
+  const size_t es = a.prec ? 4 : 8;
+  const int64_t nx = a.op.nx, ny = a.op.ny, npts = nx * ny;
+  const int ns = a.op.nspecies, p = a.p;
+  if ((nx * (int64_t)es) % 16 != 0 || (npts * (int64_t)es) % 16 != 0 || nx > (1 << 30) || ny > (1 << 30)) return false;
+  if (!tensor_map_encoder()) return false;
+  int nf = 0, fidx[2][2] = {{-1, -1}, {-1, -1}};
+  for (int sp = 0; sp < ns; ++sp)
+    for (int q = 0; q < ns; ++q)
+      if (a.op.diag[sp][q]) fidx[sp][q] = nf++;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device) != cudaSuccess) return false;
+  const int S = ctx->cfg.tma_stages >= 3 && ctx->cfg.tma_stages <= 6 ? ctx->cfg.tma_stages : 2;
+  const int pad = (int)(16 / es);
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  // candidates: the configured shape, then the automatic order (wide rows first)
+  // automatic shapes, measured on 2048^2 Gray-Scott (FP32 basis): 32 x 16 best; every shape gives each thread
+  // at least one 16-byte item of own points
+  const int auto_shapes[][2] = {{32, 16}, {64, 8}, {128, 4}, {16, 32}, {64, 4}, {32, 8}};
+  std::vector<std::pair<int, int>> cand;
+  if (ctx->cfg.tile_w > 0 && ctx->cfg.tile_h > 0) cand.push_back({ctx->cfg.tile_w, ctx->cfg.tile_h});
+  for (auto& sh : auto_shapes) cand.push_back({sh[0], sh[1]});
+  for (auto [tw, th] : cand) {
+    if (tw < 4 || tw % 4 != 0 || th < 1 || tw > 248 || th > 254) continue;
+    const int bw = tw + 2 * pad, bh = th + 2;
+    const int64_t gx = (nx + tw - 1) / tw, gy = (ny + th - 1) / th;
+    if (gx * gy <= blocks || gx * gy > INT32_MAX) continue;
+    const size_t box = up((size_t)bw * bh * ns * es);
+    const size_t off_f = box, off_b = off_f + (size_t)a.m_o * box;
+    const size_t off_d = off_b + up((size_t)p * ns * tw * th * es);
+    const size_t stage = up(off_d + up((size_t)nf * tw * th * es));
+    const size_t bar_off = std::max((size_t)S * stage, up(kDynSmem));
+    const size_t dyn = bar_off + 64 + 128;  // barriers, alignment slack
+    if (dyn > (size_t)optin) continue;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) continue;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess) continue;
+    if ((int64_t)per_sm * ctx->sms < blocks) continue;
+    a.tma_on = 1;
+    a.tma_stages = S;
+    a.tma_prefetch = ctx->cfg.tma_prefetch < 0 ? S + 2 : std::min(ctx->cfg.tma_prefetch, 64);
+    a.tma_pad = pad;
+    a.tma_bw = bw;
+    a.tma_bh = bh;
+    a.tma_nf = nf;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int q = 0; q < 2; ++q) a.tma_fidx[sp][q] = fidx[sp][q];
+    a.tma_stage_bytes = (int)stage;
+    a.tma_box_bytes = (int)box;
+    a.tma_off_f = (int)off_f;
+    a.tma_off_b = (int)off_b;
+    a.tma_off_d = (int)off_d;
+    a.tma_bar_off = (int)bar_off;
+    a.tile_w = tw;
+    a.tile_h = th;
+    a.tile_gx = (int)gx;
+    a.tile_gy = (int)gy;
+    P.dyn_smem = dyn;
+    Layout& L = P.L;
+    P.tma_b = align_up(L.total, 256);
+    P.tma_f = align_up(P.tma_b + (a.prec ? 0 : (size_t)p * a.ldv * 8), 256);
+    L.total = align_up(P.tma_f + (size_t)nf * npts * es, 256);
+    return true;
+  }
+  cudaGetLastError();
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+  return false;
+}
+
+// The four tensor maps of the TMA path (basis, raw ring, B columns, coupling fields) for the bound
+// workspace, into P.maps (passed to the kernel as a grid-constant parameter).
+kiops_status encode_tma_maps(kiops_ctx* ctx, Prepared& P) {
+  SolveArgs& a = P.args;
+  a.tma_b = a.prec ? (void*)a.bf : (void*)(P.base + P.tma_b);
+  a.tma_f = P.base + P.tma_f;
+  std::memset(&P.maps, 0, sizeof(P.maps));
+  static_assert(sizeof(CUtensorMap) == 128 && sizeof(TmaMaps) == 512, "tensor map size");
+  CUtensorMap* m = (CUtensorMap*)P.maps.m;
+  auto enc = tensor_map_encoder();
+  const CUtensorMapDataType dt = a.prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t es = a.prec ? 4 : 8;
+  const cuuint64_t nx = (cuuint64_t)a.op.nx, ny = (cuuint64_t)a.op.ny, ns = (cuuint64_t)a.op.nspecies;
+  const cuuint32_t one[4] = {1, 1, 1, 1};
+  auto check = [&](CUresult r, const char* what) -> kiops_status {
+    if (r != CUDA_SUCCESS) return fail(ctx, KIOPS_ECUDA, "tensor map of the %s: error %d", what, (int)r);
+    return KIOPS_OK;
+  };
+  {  // halo'd boxes of the basis and of the raw ring
+    const cuuint64_t st[3] = {nx * es, nx * ny * es, (cuuint64_t)a.ldv * es};
+    const cuuint32_t box[4] = {(cuuint32_t)a.tma_bw, (cuuint32_t)a.tma_bh, (cuuint32_t)ns, 1};
+    const cuuint64_t dv[4] = {nx, ny, ns, (cuuint64_t)a.m_max + 1};
+    kiops_status r = check(enc(&m[0], dt, 4, a.V, dv, st, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE), "basis");
+    if (r) return r;
+    const cuuint64_t dr[4] = {nx, ny, ns, 2};
+    r = check(enc(&m[1], dt, 4, a.raw, dr, st, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE), "raw vectors");
+    if (r) return r;
+  }
+  if (a.p > 0) {  // own-point box of the p B columns
+    const cuuint64_t st[3] = {nx * es, nx * ny * es, (cuuint64_t)a.ldv * es};
+    const cuuint32_t box[4] = {(cuuint32_t)a.tile_w, (cuuint32_t)a.tile_h, (cuuint32_t)ns, (cuuint32_t)a.p};
+    const cuuint64_t d[4] = {nx, ny, ns, (cuuint64_t)a.p};
+    kiops_status r = check(enc(&m[2], dt, 4, a.tma_b, d, st, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE), "B columns");
+    if (r) return r;
+  }
+  if (a.tma_nf > 0) {  // own-point box of the coupling fields
+    const cuuint64_t st[2] = {nx * es, nx * ny * es};
+    const cuuint32_t box[3] = {(cuuint32_t)a.tile_w, (cuuint32_t)a.tile_h, (cuuint32_t)a.tma_nf};
+    const cuuint64_t d[3] = {nx, ny, (cuuint64_t)a.tma_nf};
+    kiops_status r = check(enc(&m[3], dt, 3, a.tma_f, d, st, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE), "coupling fields");
+    if (r) return r;
+  }
+  return KIOPS_OK;
+}
 
 // Grid engine, tiled path: shared-memory extras of the fused phase, all placed over the exponential's
 // region (which invalidates them).  Ring: finalised tiles of the last m_o + 1 basis vectors; stage: the
@@ -458,7 +606,12 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
       P.args.wout[l] = wout[l];
     }
   }
-  if (engine == KIOPS_ENGINE_GRID) enable_fused_smem(ctx, fn, blocks, P, threads);
+  void* fn_tma = (A->d.kind == OP_ST2D && threads == kThreads) ? kiops_k::solve_kernel_tma(fp32) : nullptr;
+  if (engine == KIOPS_ENGINE_GRID && fn_tma && prepare_kernel(ctx, fn_tma) == KIOPS_OK &&
+      setup_tma(ctx, fn_tma, blocks, threads, P))
+    fn = fn_tma;  // the instantiation with the bulk-tensor-copy path
+  else if (engine == KIOPS_ENGINE_GRID)
+    enable_fused_smem(ctx, fn, blocks, P, threads);
   st = ensure_workspace(ctx, P.L.total);
   if (st) return st;
   bind(P, (char*)ctx->ws);
@@ -467,13 +620,17 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   st = ensure_pinned(ctx, sizeof(SolveArgs) + 512 + tr_bytes);
   if (st) return st;
   char* hp = (char*)ctx->host_pinned;
+  if (P.args.tma_on) {
+    st = encode_tma_maps(ctx, P);
+    if (st) return st;
+  }
   std::memcpy(hp, &P.args, sizeof(SolveArgs));
   KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
   KCHECK(ctx, cudaMemsetAsync(P.base + P.L.trace_len, 0, 8, ctx->stream));
   if (ctx->cfg.profile) KCHECK(ctx, cudaMemsetAsync(P.base + P.L.prof, 0, 16 * 8, ctx->stream));
   KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, hp, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
   const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
-  void* kargs[] = {(void*)&dargs};
+  void* kargs[] = {(void*)&dargs, (void*)&P.maps};
   KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, threads, kargs, P.dyn_smem, ctx->stream));
   int64_t* hs = (int64_t*)(hp + sizeof(SolveArgs) + 0);
   KCHECK(ctx, cudaMemcpyAsync(hs, P.base + P.L.stats, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -559,6 +716,11 @@ kiops_status kiops_config_default(kiops_config* cfg) {
   cfg->fused_smem = -1;
   cfg->scenario = 0;
   cfg->block_threads = 0;
+  cfg->tma = 1;
+  cfg->tile_w = 0;
+  cfg->tile_h = 0;
+  cfg->tma_stages = 0;
+  cfg->tma_prefetch = -1;
   return KIOPS_OK;
 }
 
@@ -650,6 +812,9 @@ kiops_status kiops_workspace_size(kiops_ctx* ctx, const kiops_op* A, int p, int 
   int64_t ldv;
   Layout L = layout(A->d.n, p, ctx->cfg.m_max, std::min(m_o, ctx->cfg.m_max + 1), fp32, blocks, max_r(ctx->tt), 0, &ldv);
   *bytes = L.total;
+  if (A->d.kind == OP_ST2D)  // the bulk-tensor-copy path's staged B columns (FP64) and coupling fields
+    *bytes += align_up((size_t)p * ldv * 8, 256) +
+              align_up((size_t)A->d.nspecies * A->d.nspecies * A->d.nx * A->d.ny * (fp32 ? 4 : 8), 256) + 512;
   return KIOPS_OK;
 }
 
@@ -1006,7 +1171,7 @@ kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f) {
   KCHECK(ctx, cudaMemsetAsync(P.base + P.L.bar, 0, 256 + 16 * 8 + 256, ctx->stream));
   KCHECK(ctx, cudaMemcpyAsync(P.base + P.L.args, ctx->host_pinned, sizeof(SolveArgs), cudaMemcpyHostToDevice, ctx->stream));
   const SolveArgs* dargs = (const SolveArgs*)(P.base + P.L.args);
-  void* kargs[] = {(void*)&dargs};
+  void* kargs[] = {(void*)&dargs, (void*)&P.maps};
   KCHECK(ctx, cudaLaunchCooperativeKernel(fn, blocks, kThreads, kargs, kDynSmem, ctx->stream));
   KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
   int flag = 0;

@@ -149,6 +149,21 @@ struct SolveArgs {
   int expm_n;
   const double* expm_in;
   double* expm_out;
+  // several-tiles 2D path with bulk tensor (TMA) staging of each tile's operands (grid engine only), see
+  // fused_st2d_tma.  The tile shape is tile_w x tile_h; halo'd operands are copied as boxes of tma_bw x
+  // tma_bh points per species starting at (x0 - tma_pad, y0 - 1), so that the box's x coordinate stays
+  // 16-byte aligned; own-point operands as tile_w x tile_h boxes.
+  int tma_on;
+  int tma_stages;            // tiles in flight per block (shared-memory stages)
+  int tma_prefetch;          // issue(k) also fetches tile k + tma_prefetch into L2 (0: none; > tma_stages)
+  int tma_pad;               // 16 bytes of elements (4 FP32, 2 FP64)
+  int tma_bw, tma_bh;
+  int tma_nf;                // coupling-field planes staged per tile
+  int tma_fidx[2][2];        // plane of the coupling field (s, q) among the staged ones, -1 if none
+  int tma_stage_bytes, tma_box_bytes, tma_off_f, tma_off_b, tma_off_d, tma_bar_off;
+  const void* tmaps;         // the kernel parameter's tensor maps (basis, raw ring, B columns, coupling fields)
+  void* tma_b;               // B columns b_{p-t} at t * ldv in the basis precision (FP32: bf; FP64: a copy)
+  void* tma_f;               // coupling fields in the basis precision, tma_nf planes of nx * ny points
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -286,6 +301,8 @@ struct Ctl {
   float wff[kWarps][kRegK][2];  // FP32 basis: per-warp float-float sums of the step's dots
   long long prof[16];           // cycles by phase (rank 0, thread 0) when profiling
   long long prof_last;
+  unsigned int tma_seq;         // TMA path: tile loads this block has issued and consumed (barrier phases)
+  int tma_init;                 // TMA path: the stage barriers are initialised
 };
 
 // Phase profiling: thread 0 of rank 0 charges the cycles since the previous tick to a category.
@@ -616,6 +633,64 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---- bulk tensor copies (TMA) completed through shared-memory barriers --------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// the initialised barriers become visible to the copy engine's (async) proxy
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the barrier phase of the given parity to complete; false after timeout_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = global_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (((++spins) & 63u) == 0u && global_ns() - t0 > timeout_ns) return false;
+  return true;
+}
+// generic-proxy accesses of shared memory are ordered before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// global data written by other blocks before a gpu-scope barrier becomes visible to this block's bulk copies
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int x, int y, int z, int w, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+// the box of a 4D / 3D tensor map into L2 only (no shared memory, no completion to wait for)
+__device__ __forceinline__ void tma_prefetch_4d(const void* map, int x, int y, int z, int w) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(map), "r"(x), "r"(y),
+               "r"(z), "r"(w)
+               : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const void* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(map), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ T diag_val(const SolveArgs& a, int sp, int q, uint32_t pt) {
@@ -998,7 +1073,314 @@ __device__ __forceinline__ void fused_st2d_tiles(const SolveArgs& a, Ctl& c, int
   }
 }
 
+// 16 bytes of basis-precision values (4 FP32 or 2 FP64): the unit of work of the TMA path's loops.
 template <typename T>
+struct alignas(16) Vec16 {
+  static constexpr int W = 16 / (int)sizeof(T);
+  T e[16 / sizeof(T)];
+};
+template <typename T>
+__device__ __forceinline__ Vec16<T> ld16(const T* p) {
+  return *(const Vec16<T>*)p;
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const Vec16<T>& v) {
+  *(Vec16<T>*)p = v;
+}
+// 16-byte store to global memory (cached in L2 only: the next step reads it through the copy engine)
+__device__ __forceinline__ void stg16(float* p, const Vec16<float>& v) {
+  __stcg((float4*)p, make_float4(v.e[0], v.e[1], v.e[2], v.e[3]));
+}
+__device__ __forceinline__ void stg16(double* p, const Vec16<double>& v) {
+  __stcg((double2*)p, make_double2(v.e[0], v.e[1]));
+}
+
+// Fused step on grids with more tiles than blocks, operands staged by bulk tensor copies (TMA).  Block `rank`
+// takes tiles rank, rank + nblk, ... in turn; one thread issues each tile's copies into one of tma_stages
+// shared-memory stages (completed through that stage's barrier), tma_stages tiles ahead of the tile being
+// computed, so the copies of the next tiles overlap the finalisation and products of this one.  Per tile:
+//   halo'd boxes (tile + one-point halo, widened in x to a 16-byte aligned start): the vector v_j is built
+//   from (raw x_j, or v_j itself on the first step of a substep) and the window vectors of its finalisation
+//   (which contain the dot window of step j);
+//   own-point boxes: the B columns and the coupling fields.
+// Points outside the grid arrive as zeros from the copy, which is the Dirichlet value; for periodic and
+// reflected boundaries those halo points are read from global memory at their mapped index instead.
+// The loops take 16 bytes of consecutive points per item (tile widths are multiples of that): 128-bit
+// shared-memory loads and global stores, coefficients and B-block weights held in registers.  Per element
+// the arithmetic and its order are those of fused_st2d_tiles; the elements are accumulated in another order.
+template <typename T>
+__device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0,
+                                               int nwin, T* V, size_t ldv, double* smem, DotAcc<T>& acc,
+                                               bool prof_on) {
+  constexpr int W = Vec16<T>::W;
+  const OpDesc& op = a.op;
+  const int nx = (int)op.nx, ny = (int)op.ny;
+  const uint32_t npts = (uint32_t)nx * (uint32_t)ny;
+  const int ns = op.nspecies;
+  const int p = a.p;
+  const int tid = threadIdx.x;
+  const int bc = op.bc;
+  T* raw = (T*)a.raw;
+  const bool pend = c.fin_pending != 0;
+  const T* src = pend ? raw + (size_t)((j - 1) & 1) * ldv : V + (size_t)(j - 1) * ldv;  // v_j before finalising
+  T* vj = V + (size_t)(j - 1) * ldv;
+  T* xo = raw + (size_t)(j & 1) * ldv;  // raw x_{j+1}
+  const int fnw = pend ? c.fin_nwin : 0;
+  const T fh0 = fnw > 0 ? T(c.fin_h[0]) : T(0), fh1 = fnw > 1 ? T(c.fin_h[1]) : T(0),
+          fh2 = fnw > 2 ? T(c.fin_h[2]) : T(0);
+  const T frs = pend ? T(c.fin_rs) : T(1);
+  // window boxes: the finalisation window (pending) or the dot window below v_j (first step)
+  const int fbase = pend ? c.fin_i0 : i0;
+  const int nfb = pend ? fnw : nwin - 1;
+  const T* f0 = V + (size_t)(fbase - 1) * ldv;
+  const T* f1 = V + (size_t)(fbase + (nfb > 1 ? 1 : 0) - 1) * ldv;
+  const T* f2 = V + (size_t)(fbase + (nfb > 2 ? 2 : 0) - 1) * ldv;
+  const int wslot0 = i0 - fbase, wslot1 = i0 + 1 - fbase;  // window entries i0, i0 + 1 (when below j)
+  // loop invariants in registers (the shared-memory stores of the finalisation go through generic pointers,
+  // so values read from shared memory inside the loops would be read again after each store)
+  T cfr[2][5], ntr[4];
+  int fo_s[2], ft_s[2];
+  for (int sp = 0; sp < 2; ++sp) {
+    const T* cf = coef_ptr<T>(op, sp < ns ? sp : 0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) cfr[sp][k] = cf[k];
+    fo_s[sp] = sp < ns ? a.tma_fidx[sp][sp] : -1;
+    ft_s[sp] = ns == 2 ? a.tma_fidx[sp][1 - sp] : -1;
+  }
+  {
+    const T* nt = ntail_ptr<T>(c);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) ntr[t] = t < p ? nt[t] : T(0);
+  }
+  const T* ntp = ntail_ptr<T>(c);
+  const int S = a.tma_stages, A = a.tma_pad, BW = a.tma_bw, BH = a.tma_bh;  // A == W
+  const int TW = a.tile_w, TH = a.tile_h;
+  const int bplane = BW * BH, bsz = ns * bplane;     // elements of one halo'd box (all species)
+  const int fst = a.tma_box_bytes / (int)sizeof(T);  // elements between window boxes (128-byte aligned)
+  const int oplane = TW * TH;
+  const int gxn = a.tile_gx, ntiles = a.tile_gx * a.tile_gy;
+  const int K = rank < ntiles ? (ntiles - rank + nblk - 1) / nblk : 0;
+  const int nwin_l = nwin, i0_l = i0, j_l = j;
+  // stages and barriers from the first 128-byte aligned shared address (the launch reserves the slack)
+  char* sm = (char*)smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+  uint64_t* bars = (uint64_t*)(sm + a.tma_bar_off);
+  const char* maps = (const char*)a.tmaps;  // 128 bytes each: basis, raw ring, B columns, fields
+  const int tma_nf = a.tma_nf, off_f = a.tma_off_f, off_b = a.tma_off_b, off_d = a.tma_off_d;
+  const int stage_bytes = a.tma_stage_bytes;
+  const long long timeout_ns = a.timeout_ns;
+  const unsigned expect = (unsigned)(bsz * (int)sizeof(T) * (1 + nfb)) +
+                          (p > 0 ? (unsigned)(p * ns * oplane * (int)sizeof(T)) : 0u) +
+                          (tma_nf > 0 ? (unsigned)(tma_nf * oplane * (int)sizeof(T)) : 0u);
+  if (tid == 0 && !c.tma_init) {
+    for (int s = 0; s < S; ++s) mbar_init(bars + s, 1);
+    mbar_init_fence();
+    c.tma_init = 1;
+  }
+  // raw x_j and v_j - 1 were written by every block before the barrier that opened this step
+  fence_proxy_async_all();
+  __syncthreads();
+  const unsigned q0 = c.tma_seq;
+  const int PF = a.tma_prefetch;
+  auto prefetch = [&](int k) {  // thread 0: this block's k-th tile of the step into L2
+    const int tile = rank + k * nblk;
+    const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
+    if (pend) tma_prefetch_4d(maps + 128, x0 - A, y0 - 1, 0, (j_l - 1) & 1);
+    else tma_prefetch_4d(maps, x0 - A, y0 - 1, 0, j_l - 1);
+    for (int u = 0; u < nfb; ++u) tma_prefetch_4d(maps, x0 - A, y0 - 1, 0, fbase + u - 1);
+    if (p > 0) tma_prefetch_4d(maps + 256, x0, y0, 0, 0);
+    if (tma_nf > 0) tma_prefetch_3d(maps + 384, x0, y0, 0);
+  };
+  auto issue = [&](int k) {  // thread 0: the copies of this block's k-th tile of the step
+    if (k + PF < K) prefetch(k + PF);
+    const int tile = rank + k * nblk;
+    const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
+    char* base = sm + (size_t)st * stage_bytes;
+    uint64_t* bar = bars + st;
+    const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
+    mbar_arrive_expect_tx(bar, expect);
+    if (pend) tma_load_4d(base, maps + 128, x0 - A, y0 - 1, 0, (j_l - 1) & 1, bar);
+    else tma_load_4d(base, maps, x0 - A, y0 - 1, 0, j_l - 1, bar);
+    for (int u = 0; u < nfb; ++u)
+      tma_load_4d(base + off_f + (size_t)u * fst * sizeof(T), maps, x0 - A, y0 - 1, 0, fbase + u - 1, bar);
+    if (p > 0) tma_load_4d(base + off_b, maps + 256, x0, y0, 0, 0, bar);
+    if (tma_nf > 0) tma_load_3d(base + off_d, maps + 384, x0, y0, 0, bar);
+  };
+  if (tid == 0) {
+    for (int k = S; k < K && k < PF; ++k) prefetch(k);  // later tiles are prefetched by issue(k - PF)
+    for (int k = 0; k < K && k < S; ++k) issue(k);
+  }
+  int done = 0;
+  for (int k = 0; k < K; ++k) {
+    const int tile = rank + k * nblk;
+    const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
+    const unsigned par = ((q0 + (unsigned)k) / (unsigned)S) & 1u;
+    char* base = sm + (size_t)st * stage_bytes;
+    const bool ok = mbar_wait(bars + st, par, timeout_ns);
+    KIOPS_TICK(14);
+    T* sb = (T*)base;
+    const T* fb = (const T*)(base + off_f);
+    const T* bb = (const T*)(base + off_b);
+    const T* db = (const T*)(base + off_d);
+    const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
+    const int tw = min(TW, nx - x0), th = min(TH, ny - y0);  // tw is a multiple of W
+    const int tv = tw / W;                                     // own vectors per row
+    const bool edge = bc != 0 && (x0 == 0 || y0 == 0 || x0 + tw == nx || y0 + th == ny);
+    // v_j = (x_j - sum h v) / s over the tile and its halo, in place in the source box: box rows 0..th+1,
+    // vectors 0..tv+1 of each row (box vector c covers the points x0 - W + c W ...)
+    if (ok) {
+      const int rv = tv + 2, tot = ns * (th + 2) * rv;
+      TileWalk wk(tid, rv, th + 2);
+      for (int e = tid; e < tot; e += kThreads, wk.next()) {
+        const int sp = wk.s, hy = wk.y, cv = wk.x;
+        const int bi = sp * bplane + hy * BW + cv * W;
+        const int gy = y0 - 1 + hy, gxv = x0 - W + cv * W;
+        const bool own = hy >= 1 && hy <= th && cv >= 1 && cv <= tv;
+        Vec16<T> v = ld16(sb + bi);
+        if (pend) {
+          Vec16<T> g0 = ld16(fb + bi), g1, g2;
+          if (fnw > 1) g1 = ld16(fb + fst + bi);
+          if (fnw > 2) g2 = ld16(fb + 2 * fst + bi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            T x = fma(-fh0, g0.e[u], v.e[u]);
+            if (fnw > 1) x = fma(-fh1, g1.e[u], x);
+            if (fnw > 2) x = fma(-fh2, g2.e[u], x);
+            v.e[u] = x * frs;
+          }
+        }
+        if (edge && (gy < 0 || gy >= ny || gxv < 0 || gxv + W > nx)) {
+          // periodic or reflected halo points outside the grid: the mapped point from global memory
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const int gx = gxv + u;
+            if (gx < x0 - 1 || gx > x0 + tw || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) continue;
+            const int mx = (int)bc_index(bc, gx, nx), my = (int)bc_index(bc, gy, ny);
+            const size_t r = (size_t)sp * npts + (uint32_t)my * nx + (uint32_t)mx;
+            T x = src[r];
+            if (pend) {
+              x = fma(-fh0, f0[r], x);
+              if (fnw > 1) x = fma(-fh1, f1[r], x);
+              if (fnw > 2) x = fma(-fh2, f2[r], x);
+              x = x * frs;
+            }
+            v.e[u] = x;
+          }
+        }
+        st16(sb + bi, v);
+        if (pend && own) stg16(vj + (size_t)sp * npts + (uint32_t)gy * nx + (uint32_t)gxv, v);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      // a copy that never completed: raise the abort flag (the step's barrier then stops every block)
+      if (tid == 0 && a.abort_flag) atomicExch(a.abort_flag, ST_ETIMEOUT);
+      break;
+    }
+    done = k + 1;
+    KIOPS_TICK(12);
+    // A~ v_j on the tile's own points and the step's dots, every operand from the stage
+    {
+      const int tot = ns * th * tv;
+      TileWalk wk(tid, tv, th);
+      for (int e = tid; e < tot; e += kThreads, wk.next()) {
+        const int sp = wk.s, ly = wk.y, cv = wk.x;
+        const int bi = sp * bplane + (ly + 1) * BW + W + cv * W;
+        const int pi = ly * TW + cv * W;
+        const int fo = sp ? fo_s[1] : fo_s[0], ft = sp ? ft_s[1] : ft_s[0];
+        const T c0 = sp ? cfr[1][0] : cfr[0][0], c1 = sp ? cfr[1][1] : cfr[0][1], c2 = sp ? cfr[1][2] : cfr[0][2];
+        const T c3 = sp ? cfr[1][3] : cfr[0][3], c4 = sp ? cfr[1][4] : cfr[0][4];
+        // each operand vector is read right before its terms are added (short live ranges); per element the
+        // terms are added in the order of fused_st2d_tiles
+        const Vec16<T> ctr = ld16(sb + bi);
+        Vec16<T> out;
+        {
+          Vec16<T> dow;
+          if (fo >= 0) dow = ld16(db + fo * oplane + pi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = (fo >= 0 ? c0 + dow.e[u] : c0) * ctr.e[u];
+        }
+        {
+          const T wl = sb[bi - 1], er = sb[bi + W];
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(c1, u == 0 ? wl : ctr.e[u == 0 ? 0 : u - 1], out.e[u]);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(c2, u == W - 1 ? er : ctr.e[u == W - 1 ? 0 : u + 1], out.e[u]);
+        }
+        {
+          const Vec16<T> up = ld16(sb + bi - BW);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(c3, up.e[u], out.e[u]);
+        }
+        {
+          const Vec16<T> dn = ld16(sb + bi + BW);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(c4, dn.e[u], out.e[u]);
+        }
+        if (ft >= 0) {
+          const Vec16<T> oth = ld16(sb + bi + (1 - 2 * sp) * bplane), dth = ld16(db + ft * oplane + pi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(dth.e[u], oth.e[u], out.e[u]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < p) {
+            const Vec16<T> bv = ld16(bb + (t * ns + sp) * oplane + pi);
+#pragma unroll
+            for (int u = 0; u < W; ++u) out.e[u] = fma(ntr[t], bv.e[u], out.e[u]);
+          }
+        for (int t = 4; t < p; ++t) {
+          const Vec16<T> bv = ld16(bb + (t * ns + sp) * oplane + pi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(ntp[t], bv.e[u], out.e[u]);
+        }
+        stg16(xo + (size_t)sp * npts + (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + cv * W), out);
+        {  // the step's dots
+          Vec16<T> g;
+          if (i0_l != j_l) g = ld16(fb + wslot0 * fst + bi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const T v0 = (i0_l == j_l) ? ctr.e[u] : g.e[u];
+            acc.add(0, v0, out.e[u]);
+            acc.add(kChunk, ctr.e[u], v0);
+          }
+        }
+        if (nwin_l > 1) {
+          Vec16<T> g;
+          if (i0_l + 1 != j_l) g = ld16(fb + wslot1 * fst + bi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const T v1 = (i0_l + 1 == j_l) ? ctr.e[u] : g.e[u];
+            acc.add(1, v1, out.e[u]);
+            acc.add(kChunk + 1, ctr.e[u], v1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          if (nwin_l > 2) {  // i0 + 2 == j
+            acc.add(2, ctr.e[u], out.e[u]);
+            acc.add(kChunk + 2, ctr.e[u], ctr.e[u]);
+          }
+          acc.add(2 * kChunk, out.e[u], out.e[u]);
+        }
+      }
+    }
+    KIOPS_TICK(13);
+    fence_proxy_async_smem();  // this stage's shared-memory accesses come before the next copies into it
+    __syncthreads();
+    if (tid == 0 && k + S < K) issue(k + S);
+  }
+  // copies issued but not consumed (only after a copy timed out): wait for them, bounded, before the
+  // stages are reused
+  for (int k = done; k < K && k < done + S; ++k) {
+    const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
+    mbar_wait(bars + st, ((q0 + (unsigned)k) / (unsigned)S) & 1u, timeout_ns);
+  }
+  __syncthreads();
+  if (tid == 0) c.tma_seq = q0 + (unsigned)K;
+}
+
+// TMA: the kernel instantiation that contains the bulk-tensor-copy path (kept out of the other
+// instantiations, whose register allocation it would otherwise share).
+template <typename T, bool TMA>
 __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0, int nwin, bool lead,
                                  T* V, size_t ldv, double* smem, DotAcc<T>& acc, bool prof_on) {
   const OpDesc& op = a.op;
@@ -1028,7 +1410,9 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
   const int nr = a.ring_n;
   const int ring_valid_from = nr > 0 ? max(c.ring_lo, j - nr + 1) : (1 << 30);
   const int ntiles = a.tile_gx * a.tile_gy;
-  if (ntiles > nblk) {
+  if (TMA && ntiles > nblk && a.tma_on) {
+    if constexpr (TMA) fused_st2d_tma<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
+  } else if (ntiles > nblk) {
     fused_st2d_tiles<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
   } else {
     // one tile per block, with the shared-memory extras
@@ -1215,11 +1599,18 @@ __device__ void fused_prefetch(const SolveArgs& a, int rank, int jn, double* sme
 // ------------------------------------------------------------------------------------------------
 // The solver kernel.
 // ------------------------------------------------------------------------------------------------
-template <typename T, int KIND, class Team>
+template <typename T, int KIND, class Team, bool TMA = false>
 __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn);
 
-template <typename T, int KIND, bool GRID>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_solve_kernel(const SolveArgs* __restrict__ all) {
+// Tensor maps of the TMA path, passed by value as a grid-constant kernel parameter (128 bytes each, 64-byte
+// aligned): basis, raw ring, B columns, coupling fields.
+struct TmaMaps {
+  alignas(64) unsigned char m[4][128];
+};
+
+template <typename T, int KIND, bool GRID, bool TMA = false>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_solve_kernel(const SolveArgs* __restrict__ all,
+                                                                           const __grid_constant__ TmaMaps tmaps) {
   extern __shared__ double smem_dyn[];
   __shared__ Ctl c;
   // The argument block is copied to shared memory: gpu-scope acquires at every barrier invalidate L1,
@@ -1230,10 +1621,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_solve_kernel(const
     const int words = (int)(sizeof(SolveArgs) / sizeof(int));
     for (int i = threadIdx.x; i < words; i += kThreads) ((int*)&sa)[i] = ((const int*)src)[i];
     __syncthreads();
+    if (threadIdx.x == 0) sa.tmaps = &tmaps;  // generic address of the parameter (the bulk copies read it)
+    __syncthreads();
   }
   if (GRID) {
     GridTeam team{(int)blockIdx.x, (int)gridDim.x, sa.bar, sa.abort_flag, sa.timeout_ns, 0u};
-    solve_body<T, KIND, GridTeam>(sa, team, c, smem_dyn);
+    solve_body<T, KIND, GridTeam, TMA>(sa, team, c, smem_dyn);
   } else {
     CtaTeam team;
     solve_body<T, KIND, CtaTeam>(sa, team, c, smem_dyn);
@@ -1451,7 +1844,7 @@ __device__ void combine_rows(Ctl& c, const T* V, size_t ldv, int j, const double
   }
 }
 
-template <typename T, int KIND, class Team>
+template <typename T, int KIND, class Team, bool TMA>
 __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn) {
   const int tid = threadIdx.x;
   const int64_t N = a.N;
@@ -1480,6 +1873,8 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     c.pre_j = 0;
     c.cache_ok = 0;
     c.tbl_ok = 0;
+    c.tma_seq = 0;
+    c.tma_init = 0;
   }
   __syncthreads();
 
@@ -1517,6 +1912,23 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
               for (int64_t pt = q0 + tid; pt < q1; pt += kThreads)
                 a.df[(size_t)(sp * ns + q) * npts + pt] = (float)__ldg(a.op.diag[sp][q] + pt);
       }
+    }
+    if (TMA && KIND == OP_ST2D && a.tma_on) {  // TMA path: B columns (FP64 basis) and coupling fields as staged
+      if constexpr (sizeof(T) == 8) {
+        double* tb = (double*)a.tma_b;
+        for (int t = 0; t < p; ++t)
+          for (int64_t r = r0 + tid; r < r1; r += kThreads) tb[(size_t)t * a.ldv + r] = __ldg(a.b[p - t] + r);
+      }
+      const int ns = a.op.nspecies;
+      const int64_t npts = a.op.nx * a.op.ny;
+      const int64_t pchunk = (npts + team.size - 1) / team.size;
+      const int64_t q0 = (int64_t)team.rank * pchunk, q1 = q0 + pchunk < npts ? q0 + pchunk : npts;
+      T* tf = (T*)a.tma_f;
+      for (int sp = 0; sp < ns; ++sp)
+        for (int q = 0; q < ns; ++q)
+          if (a.tma_fidx[sp][q] >= 0)
+            for (int64_t pt = q0 + tid; pt < q1; pt += kThreads)
+              tf[(size_t)a.tma_fidx[sp][q] * npts + pt] = (T)__ldg(a.op.diag[sp][q] + pt);
     }
     if (p > 0) {
       if (!finish_reduce<Team>(team, c, a.partials, parity, p)) goto stop;
@@ -1630,7 +2042,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       if (fused) {
         DotAcc<T> dacc;
         dacc.zero();
-        fused_st2d_phase<T>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+        fused_st2d_phase<T, TMA>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
         __syncthreads();
         if (tid == 0) {
           c.ring_lo = (c.ring_lo <= j - 1) ? c.ring_lo : j;  // v_j is now in the ring

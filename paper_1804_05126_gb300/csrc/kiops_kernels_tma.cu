@@ -1,0 +1,13 @@
+// Instantiations of the grid-engine kernel for 2D stencils with the bulk-tensor-copy (TMA) several-tiles
+// path, in their own translation unit (compiled in parallel with the others).
+#include "kiops_device.cuh"
+#include "kiops_kernels.h"
+
+using namespace kiops_dev;
+
+namespace kiops_k {
+void* solve_kernel_tma(bool fp32) {
+  if (fp32) return (void*)kiops_solve_kernel<float, OP_ST2D, true, true>;
+  return (void*)kiops_solve_kernel<double, OP_ST2D, true, true>;
+}
+}  // namespace kiops_k

@@ -35,7 +35,8 @@ class kiops_config(C.Structure):
                 ("max_iterations", C.c_int64), ("timeout_s", C.c_double), ("engine", C.c_int),
                 ("grid_blocks", C.c_int), ("profile", C.c_int), ("fuse_stencil", C.c_int),
                 ("batch_team_blocks", C.c_int), ("fused_smem", C.c_int), ("scenario", C.c_int),
-                ("block_threads", C.c_int)]
+                ("block_threads", C.c_int), ("tma", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int),
+                ("tma_stages", C.c_int), ("tma_prefetch", C.c_int)]
 
 
 class kiops_stats(C.Structure):
@@ -461,7 +462,9 @@ class Solver:
     def __init__(self, device: int = 0, stream=None, m_min: int = 10, m_max: int = 128, normalize_B: bool = True,
                  breakdown_tol: float = 1e-12, max_substeps: int = 10**6, max_iterations: int = 10**5,
                  timeout_s: float = 10.0, engine: int = ENGINE_AUTO, grid_blocks: int = 0, profile: bool = False,
-                 fuse_stencil: bool = True, fused_smem: int = -1, scenario: int = 0, block_threads: int = 0):
+                 fuse_stencil: bool = True, fused_smem: int = -1, scenario: int = 0, block_threads: int = 0,
+                 tma: int = 1, tile: tuple[int, int] | None = None, tma_stages: int = 0,
+                 tma_prefetch: int = -1):
         import torch
         self.device = torch.device("cuda", device)
         cfg = kiops_config_default()
@@ -474,6 +477,10 @@ class Solver:
         cfg.fused_smem = int(fused_smem)
         cfg.scenario = int(scenario)
         cfg.block_threads = int(block_threads)
+        cfg.tma = int(tma)
+        cfg.tile_w, cfg.tile_h = (int(tile[0]), int(tile[1])) if tile else (0, 0)
+        cfg.tma_stages = int(tma_stages)
+        cfg.tma_prefetch = int(tma_prefetch)
         self.cfg = cfg
         self.ctx = kiops_create(cfg)
 

@@ -412,6 +412,36 @@ def test_fused_path_with_several_tiles_per_block(make, blocks):
         assert rel(w, wu) <= 1e-9
 
 
+@pytest.mark.parametrize("tile,stages", [(None, 2), ((32, 16), 3), ((16, 8), 2)])
+@pytest.mark.parametrize("m_o", [2, 3])
+@pytest.mark.parametrize("make", [
+    lambda: W.problem_adr2d(n=152, seed=26),                                            # Dirichlet
+    lambda: W.problem_gray_scott(n=96, seed=10, precision="fp64", tol=1e-8, tau=1.0),   # periodic, 2 species
+    lambda: _neumann_adr_problem(132, 27),                                              # reflecting
+    lambda: W.problem_gray_scott(n=200, seed=11, precision="fp32_basis", tol=1e-6, tau=1.0)])
+def test_tma_staged_several_tiles_path(make, m_o, tile, stages):
+    """The several-tiles step with each tile's operands staged by bulk tensor copies (TMA): 3 blocks (each
+    grid is too large for one tile per block), ragged edge tiles (tile shapes that do not divide the grid),
+    the three boundary treatments, both precisions, orthogonalisation lengths 2 and 3 and 2 or 3 tiles in
+    flight, forced on for both precisions (tma = 2).  Against the per-element several-tiles path (tma = 0): same
+    decisions and the same result up to rounding; against the oracle within 10 tol."""
+    P = make()
+    s = kiops.Solver(device=0, grid_blocks=3, tile=tile, tma_stages=stages, tma=2)
+    w, st, tr = gpu_solve(s, P, trace=True, m_o=m_o)
+    s.close()
+    u = kiops.Solver(device=0, grid_blocks=3, tma=0)
+    wu, stu, tru = gpu_solve(u, P, trace=True, m_o=m_o)
+    u.close()
+    w_ref, st_ref, tr_ref = oracle_solve(P, m_o=m_o)
+    assert st["status"] == 0 and stu["status"] == 0
+    assert rel(w, w_ref) <= 10 * P.tol
+    if P.precision == "fp64":
+        assert [(t["j"], t["accepted"]) for t in tr] == [(t["j"], t["accepted"]) for t in tr_ref]
+        assert rel(w, wu) <= 1e-9
+    else:
+        assert rel(w, wu) <= P.tol
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32_basis", 1e-6)])
 def test_2048_grid_several_tiles_vs_dst_closed_form(solver, precision, tol):
     """Full-size pin of the several-tiles path: 2048^2 Dirichlet diffusion + shift (N = 4.2 M, 4 or 2 tiles
