@@ -324,9 +324,17 @@ def measure_patterns(dev):
         dt, (w, st) = timed(lambda: s.solve(op, P.tau, b, P.tol, precision=prec))
         res[prec] = (dt, w.clone(), st)
     rel = float((res["fp32_basis"][1] - res["fp64"][1]).norm() / res["fp64"][1].norm())
+    # the error of each result against the FP64 oracle (its OpenMP build on the host cores, not timed here)
+    import oracle
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    w_ref, st_ref, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o, parallel=True)
+    ref_n = float(np.linalg.norm(w_ref))
+    err = {prec: float(np.linalg.norm(res[prec][1].cpu().numpy() - w_ref) / ref_n) for prec in res}
     out["mixed_precision_gray_scott_1024"] = {
         "fp32_basis_ms": 1e3 * res["fp32_basis"][0], "fp64_ms": 1e3 * res["fp64"][0],
         "speedup": res["fp64"][0] / res["fp32_basis"][0], "rel_err_vs_fp64": rel, "tol": P.tol,
+        "rel_err_vs_oracle": {"fp32_basis": err["fp32_basis"], "fp64": err["fp64"]},
+        "oracle_matvecs": st_ref["matvecs"],
         "matvecs_fp32": res["fp32_basis"][2]["matvecs"], "matvecs_fp64": res["fp64"][2]["matvecs"]}
     s.close()
     # served: Poisson stream (2000/s) of the 3D ADR request mix with n in 16..64
@@ -346,6 +354,7 @@ def measure_patterns(dev):
         "note": "half the requests FP32 basis (tol 1e-6), half FP64 (tol 1e-10); latency = completion - arrival"}
     srv.close()
     seq.close()
+    out["served_config5"] = measure_served_config5(dev)
 
     # integrators (section 4): the paper's 400 x 400 ADR problem over t in [0, 0.1], h = 0.0025 (40 steps)
     integ = kiops.Solver(device=dev.index)
@@ -379,6 +388,60 @@ def measure_patterns(dev):
     return out
 
 
+def measure_served_config5(dev, count=48):
+    """The served request mix at its stated sizes (3D ADR, n in 16..160, N up to 4.1 M; half FP32 basis at tol
+    1e-6, half FP64 at tol 1e-10) on a bounded number of requests: the saturated service rate (all requests
+    queued at once), p50/p99 latency for Poisson arrivals at 3/4 of that rate (the sustainable rate measured here)
+    and at the stated 2000/s (where the queue grows), plain single-instance FP64 solves of the same requests,
+    and the FP32-basis results' error against the FP64 oracle on the smaller requests."""
+    import torch
+
+    from paper_1804_05126_gb300 import kiops, serve
+    import oracle
+
+    base = W.request_stream(count, seed=1005, n_range=(16, 160))
+    srv = kiops.Solver(device=dev.index)
+    srv.server_start(hbm_budget_bytes=120e9)
+    serve.run_stream(srv, [(0.0, P) for _, P in base[:4]])  # warm-up
+    burst = serve.run_stream(srv, [(0.0, P) for _, P in base])
+    rate = burst["solves_per_s"]
+    sus_rate = 0.75 * rate
+    rng = np.random.default_rng(7)
+    arrivals = np.cumsum(rng.exponential(1.0 / sus_rate, count))
+    sus = serve.run_stream(srv, [(float(t), P) for t, (_, P) in zip(arrivals, base)])
+    fast = serve.run_stream(srv, base)  # the stated 2000/s arrivals
+    srv.server_stop()
+    # error of the FP32-basis results against the FP64 oracle on the requests with n <= 40
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    errs = []
+    for (_, P), w in zip(base, burst["w"]):
+        if P.precision == "fp32_basis" and P.meta["n"] <= 40:
+            ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o, parallel=True)
+            errs.append(float(np.linalg.norm(w.cpu().numpy() - ref) / np.linalg.norm(ref)))
+    srv.close()
+    seq = kiops.Solver(device=dev.index)
+    ops = [seq.operator(P.op) for _, P in base]
+    bs = [torch.as_tensor(P.b, device=dev) for _, P in base]
+    seq.solve(ops[0], base[0][1].tau, bs[0], base[0][1].tol, precision="fp64")
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i, (_, P) in enumerate(base):
+        seq.solve(ops[i], P.tau, bs[i], P.tol, precision="fp64")
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    seq.close()
+    return {"requests": count, "n_range": [16, 160],
+            "saturated": {"solves_per_s": rate, "p50_ms": burst["p50_ms"], "p99_ms": burst["p99_ms"]},
+            "sustainable": {"arrival_rate_per_s": sus_rate, "solves_per_s": sus["solves_per_s"],
+                            "p50_ms": sus["p50_ms"], "p99_ms": sus["p99_ms"]},
+            "at_2000_per_s": {"solves_per_s": fast["solves_per_s"], "p50_ms": fast["p50_ms"], "p99_ms": fast["p99_ms"]},
+            "single_instance_fp64_solves_per_s": count / t_seq,
+            "fp32_basis_rel_err_vs_oracle": {"requests": len(errs), "max": max(errs) if errs else None,
+                                             "tol": 1e-6},
+            "note": ("sustainable = 3/4 of the saturated rate; 2000/s exceeds the service rate, so its latency is "
+                     "queueing; latency = completion - arrival")}
+
+
 STEP_PHASES = (2, 3, 4, 5, 11, 12, 13, 14)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
 
 
@@ -392,7 +455,7 @@ def measure_beyond_l2(dev):
 
     import torch
 
-    from paper_1804_05126_gb300 import kiops
+    from paper_1804_05126_gb300 import kiops, tune
 
     hbm = peaks().get("hbm_gbs", 6768.1)
     cases = [("gray_scott_2048_fp32_basis", W.problem_gray_scott(n=2048), "fp32_basis", 4, 2),
@@ -403,6 +466,9 @@ def measure_beyond_l2(dev):
         prof = kiops.Solver(device=dev.index, profile=True)
         op, pop = sol.operator(P.op), prof.operator(P.op)
         b = torch.as_tensor(P.b, device=dev)
+        # launch shape (tile shape of the 2D step, block size) picked by the autotuner on this solve
+        best, tuning = tune.tune_solve(sol, op, P.tau, b, P.tol, precision=prec)
+        prof.configure(**best)
         sol.solve(op, P.tau, b, P.tol, precision=prec)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 3
@@ -421,7 +487,8 @@ def measure_beyond_l2(dev):
         gbs = bytes_step / (step_us * 1e-6) / 1e9
         res[name] = {"N": P.n, "p": P.p, "ms_per_solve": ms, "matvecs": st["matvecs"], "substeps": st["substeps"],
                      "step_us": step_us, "step_share_of_solve": share, "bytes_per_step": bytes_step,
-                     "step_gbs": gbs, "step_hbm_frac": gbs / hbm, "grid_blocks": st["grid_blocks"]}
+                     "step_gbs": gbs, "step_hbm_frac": gbs / hbm, "grid_blocks": st["grid_blocks"],
+                     "tuned_launch_shape": best, "tuning_ms_per_solve": tuning}
         sol.close()
         prof.close()
     res["note"] = ("step_hbm_frac: algorithmic step bytes / step time / measured copy bandwidth; the FP64 case "

@@ -267,6 +267,13 @@ kiops_status kiops_solve_batch(kiops_ctx* ctx, int count, const kiops_request* r
 /* Set cfg.batch_team_blocks of a live context (used by the batch autotuner). */
 kiops_status kiops_set_batch_team_blocks(kiops_ctx* ctx, int team_blocks);
 
+/* The configuration of a live context, and a new one for the solves that follow (used by the autotuner of
+ * the engine's launch shapes).  The device and the stream cannot change (EINVAL); a context that runs a server
+ * keeps its configuration (EBUSY).  Results depend on the shape settings (tile_w, tile_h, block_threads,
+ * grid_blocks, tma) only through the order in which partial sums are added. */
+kiops_status kiops_get_config(const kiops_ctx* ctx, kiops_config* cfg);
+kiops_status kiops_set_config(kiops_ctx* ctx, const kiops_config* cfg);
+
 /* Dense exponential F = exp(A) of an n x n row-major FP64 matrix (device pointers), n <= KIOPS_MAX_M + 1,
  * computed by the same on-device scaling-and-squaring code the solver uses for exp(tau H~). */
 kiops_status kiops_expm(kiops_ctx* ctx, int n, const double* a, double* f);
@@ -286,8 +293,8 @@ typedef struct {
   double hbm_budget_bytes;      /* admission budget for request workspaces, allocated at start (120e9) */
   int queue_slots;              /* request slots per class (512) */
   int small_team_blocks;        /* blocks per small team (8) */
-  int large_team_blocks;        /* blocks per large team (0 = half of the co-resident blocks) */
-  int large_teams;              /* number of large teams (1; 0 = every request is small) */
+  int large_team_blocks;        /* blocks per large team (0 = the large teams share half of the co-resident blocks) */
+  int large_teams;              /* number of large teams (2; 0 = every request is small) */
   double large_work_threshold;  /* estimated work above which a request is large (2e8) */
   double idle_timeout_s;        /* the kernel exits after this long without work; must be < cfg.timeout_s (2) */
 } kiops_server_config;

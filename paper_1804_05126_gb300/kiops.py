@@ -153,6 +153,8 @@ _SIGS = {
                           C.c_int, C.c_int, C.c_void_p, C.POINTER(kiops_stats)], C.c_int),
     "kiops_solve_batch": ([C.c_void_p, C.c_int, C.POINTER(kiops_request), C.POINTER(kiops_stats)], C.c_int),
     "kiops_set_batch_team_blocks": ([C.c_void_p, C.c_int], C.c_int),
+    "kiops_get_config": ([C.c_void_p, C.POINTER(kiops_config)], C.c_int),
+    "kiops_set_config": ([C.c_void_p, C.POINTER(kiops_config)], C.c_int),
     "kiops_server_config_default": ([C.POINTER(kiops_server_config)], C.c_int),
     "kiops_server_start": ([C.c_void_p, C.POINTER(kiops_server_config)], C.c_int),
     "kiops_submit": ([C.c_void_p, C.POINTER(kiops_request), C.POINTER(C.c_uint64)], C.c_int),
@@ -339,6 +341,16 @@ def kiops_solve_noalloc(ctx, op, tau, p, b_ptrs, tol, m_init, m_o, w_ptr) -> dic
     return st.as_dict()
 
 
+def kiops_get_config(ctx) -> kiops_config:
+    cfg = kiops_config()
+    _check(ctx, lib().kiops_get_config(ctx, C.byref(cfg)), "kiops_get_config")
+    return cfg
+
+
+def kiops_set_config(ctx, cfg: kiops_config) -> None:
+    _check(ctx, lib().kiops_set_config(ctx, C.byref(cfg)), "kiops_set_config")
+
+
 def kiops_set_batch_team_blocks(ctx, team_blocks: int) -> None:
     _check(ctx, lib().kiops_set_batch_team_blocks(ctx, team_blocks), "kiops_set_batch_team_blocks")
 
@@ -483,6 +495,17 @@ class Solver:
         cfg.tma_prefetch = int(tma_prefetch)
         self.cfg = cfg
         self.ctx = kiops_create(cfg)
+
+    def configure(self, **fields) -> dict:
+        """Change fields of the live context's configuration (e.g. tile_w, tile_h, tma, tma_stages, fused_smem,
+        block_threads, grid_blocks); returns the previous values of those fields."""
+        cfg = kiops_get_config(self.ctx)
+        old = {k: getattr(cfg, k) for k in fields}
+        for k, v in fields.items():
+            setattr(cfg, k, v)
+        kiops_set_config(self.ctx, cfg)
+        self.cfg = cfg
+        return old
 
     def operator(self, desc: dict) -> Operator:
         return Operator(self, desc)
