@@ -297,6 +297,11 @@ typedef struct {
   int large_teams;              /* number of large teams (2; 0 = every request is small) */
   double large_work_threshold;  /* estimated work above which a request is large (2e8) */
   double idle_timeout_s;        /* the kernel exits after this long without work; must be < cfg.timeout_s (2) */
+  double solo_min_unknowns;     /* requests with at least this many unknowns run alone on the whole GPU (the grid
+                                   engine of kiops_solve) between launches of the server kernel: the server stops
+                                   admitting, lets the requests in flight finish, runs them in arrival order and
+                                   resumes.  A team's share of the GPU is slower for such sizes.  0 = never
+                                   (default 1e6) */
 } kiops_server_config;
 
 kiops_status kiops_server_config_default(kiops_server_config* cfg);
@@ -304,7 +309,8 @@ kiops_status kiops_server_start(kiops_ctx* ctx, const kiops_server_config* cfg);
 /* Queue one request (same fields as kiops_solve; tau > 0).  b and w are borrowed until kiops_poll reports
  * it done.  *ticket identifies it.  Errors: EINVAL, ENOMEM if it cannot fit the budget even alone. */
 kiops_status kiops_submit(kiops_ctx* ctx, const kiops_request* req, uint64_t* ticket);
-/* Wait up to timeout_s (0 = just check) for a ticket; *done = 1 and stats filled once it has finished. */
+/* Wait up to timeout_s (0 = just check) for a ticket; *done = 1 and stats filled once it has finished.  Requests
+ * that run alone (solo_min_unknowns) are run inside this call, so one call can take as long as such a solve. */
 kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* done, kiops_stats* stats);
 /* info[0..7] = pending (not yet admitted), in flight, reserved workspace bytes, small teams, large teams,
  * blocks per large team, requests the small and the large teams have claimed since the server started. */

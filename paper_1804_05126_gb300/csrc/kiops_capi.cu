@@ -1326,6 +1326,12 @@ struct Pending {
   Prepared P;
 };
 
+struct SoloReq {  // a request that runs alone on the whole GPU (server_config.solo_min_unknowns)
+  uint64_t ticket;
+  kiops_request r;
+  std::vector<const double*> b;  // copy of the caller's b[0..p]
+};
+
 }  // namespace
 
 struct KiopsServer {
@@ -1348,6 +1354,7 @@ struct KiopsServer {
   unsigned int next_index[kServerClasses] = {};
   uint64_t next_ticket = 1;
   std::deque<Pending> pending;
+  std::deque<SoloReq> solo;  // waiting to run alone; while any waits, nothing is admitted and the kernel drains
   std::unordered_map<uint64_t, InFlight> inflight;
   std::unordered_map<uint64_t, std::vector<int64_t>> finished;  // ticket -> 16 stats words
   int grid = 0;
@@ -1429,10 +1436,41 @@ kiops_status server_collect(kiops_ctx* ctx, KiopsServer* S) {
   return KIOPS_OK;
 }
 
-kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S) {
+// Requests that run alone: with the server kernel gone (it drains its queues and exits once the stop word is
+// up) and nothing in flight, run the oldest on the whole GPU with the grid engine, synchronously.
+kiops_status server_run_solo(kiops_ctx* ctx, KiopsServer* S) {
+  __atomic_store_n(&S->q->stop[0], 1, __ATOMIC_RELEASE);  // the kernel exits when its queues are empty
+  while (!S->solo.empty() && S->inflight.empty() && !server_kernel_running(S)) {
+    kiops_status xs = server_check_exit(ctx, S);
+    if (xs) return xs;
+    SoloReq q = S->solo.front();
+    S->solo.pop_front();
+    kiops_stats st{};
+    const kiops_status rc = run_single(ctx, q.r.A, q.r.tau, q.r.p, q.b.data(), q.r.tol, q.r.m_init, q.r.m_o,
+                                       q.r.prec, q.r.w, &st, nullptr, 0, nullptr);
+    std::vector<int64_t> w(16, 0);
+    w[0] = st.substeps; w[1] = st.rejected; w[2] = st.matvecs; w[3] = st.iterations; w[4] = st.expm_calls;
+    w[5] = st.m_last; w[6] = rc;
+    std::memcpy(&w[10], &st.err_est, sizeof(double));
+    S->finished[q.ticket] = w;
+  }
+  if (S->solo.empty()) __atomic_store_n(&S->q->stop[0], 0, __ATOMIC_RELEASE);
+  return KIOPS_OK;
+}
+
+kiops_status server_pump(kiops_ctx* ctx, KiopsServer* S, bool allow_solo = false) {
   kiops_status xs = server_check_exit(ctx, S);
   if (!xs) xs = server_collect(ctx, S);
   if (xs) return xs;
+  if (!S->solo.empty()) {  // drain, then run alone (only from kiops_poll: it blocks for the solve)
+    if (!allow_solo) {
+      __atomic_store_n(&S->q->stop[0], 1, __ATOMIC_RELEASE);
+      return KIOPS_OK;
+    }
+    xs = server_run_solo(ctx, S);
+    if (xs) return xs;
+    if (!S->solo.empty()) return KIOPS_OK;  // still draining
+  }
   // admissions, in arrival order per class (a request that does not fit waits; later ones may pass it)
   bool enqueued = false;
   for (auto it = S->pending.begin(); it != S->pending.end();) {
@@ -1495,6 +1533,7 @@ kiops_status kiops_server_config_default(kiops_server_config* cfg) {
   cfg->large_teams = 2;  // measured on the 3D request mix with n <= 64: 415 (one team) -> 555 solves/s
   cfg->large_work_threshold = 2e8;
   cfg->idle_timeout_s = 2.0;
+  cfg->solo_min_unknowns = 1e6;
   return KIOPS_OK;
 }
 
@@ -1589,6 +1628,18 @@ kiops_status kiops_submit(kiops_ctx* ctx, const kiops_request* r, uint64_t* tick
   if (!S) return fail(ctx, KIOPS_EINVAL, "no server: call kiops_server_start first");
   if (!r->A || !r->b || !r->w) return fail(ctx, KIOPS_EINVAL, "NULL operator, b or w");
   if (!(r->tau > 0.0)) return fail(ctx, KIOPS_EINVAL, "served requests need tau > 0");
+  if (S->cfg.solo_min_unknowns > 0 && (double)r->A->d.n >= S->cfg.solo_min_unknowns) {
+    Prepared P;  // validates the request as kiops_solve does
+    kiops_status st = prepare(ctx, r->A, r->tau, r->p, r->b, r->tol, r->m_init, r->m_o, r->prec, r->w, 1, 0, P);
+    if (st) return st;
+    SoloReq q;
+    q.ticket = S->next_ticket++;
+    q.r = *r;
+    q.b.assign(r->b, r->b + r->p + 1);
+    S->solo.push_back(q);
+    *ticket = q.ticket;
+    return server_pump(ctx, S);
+  }
   const int cls = (S->cfg.large_teams > 0 && estimate_work(ctx, *r) > S->cfg.large_work_threshold) ? 1 : 0;
   Pending pd;
   pd.ticket = S->next_ticket++;
@@ -1610,7 +1661,7 @@ kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* 
   *done = 0;
   auto t0 = std::chrono::steady_clock::now();
   while (true) {
-    kiops_status st = server_pump(ctx, S);
+    kiops_status st = server_pump(ctx, S, true);
     if (st) return st;
     auto it = S->finished.find(ticket);
     if (it != S->finished.end()) {
@@ -1625,7 +1676,8 @@ kiops_status kiops_poll(kiops_ctx* ctx, uint64_t ticket, double timeout_s, int* 
       return KIOPS_OK;
     }
     const bool known = S->inflight.count(ticket) ||
-                       std::any_of(S->pending.begin(), S->pending.end(), [&](const Pending& p) { return p.ticket == ticket; });
+                       std::any_of(S->pending.begin(), S->pending.end(), [&](const Pending& p) { return p.ticket == ticket; }) ||
+                       std::any_of(S->solo.begin(), S->solo.end(), [&](const SoloReq& q) { return q.ticket == ticket; });
     if (!known) return fail(ctx, KIOPS_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (el >= timeout_s) return KIOPS_OK;
@@ -1654,7 +1706,7 @@ kiops_status kiops_server_info(kiops_ctx* ctx, int64_t info[8]) {
   KiopsServer* S = ctx->server;
   size_t free_bytes = 0;
   for (auto& kv : S->arena.free_) free_bytes += kv.second;
-  info[0] = (int64_t)S->pending.size();
+  info[0] = (int64_t)(S->pending.size() + S->solo.size());
   info[1] = (int64_t)S->inflight.size();
   info[2] = (int64_t)(S->arena.bytes - free_bytes);
   info[3] = S->sd.teams[0];

@@ -82,7 +82,7 @@ class kiops_stencil3d_desc(C.Structure):
 class kiops_server_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_double), ("queue_slots", C.c_int), ("small_team_blocks", C.c_int),
                 ("large_team_blocks", C.c_int), ("large_teams", C.c_int), ("large_work_threshold", C.c_double),
-                ("idle_timeout_s", C.c_double)]
+                ("idle_timeout_s", C.c_double), ("solo_min_unknowns", C.c_double)]
 
 
 class kiops_request(C.Structure):

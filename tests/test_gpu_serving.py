@@ -108,3 +108,27 @@ def test_server_recovers_after_an_abort():
     assert np.linalg.norm(res["w"][0].cpu().numpy() - ref) <= 10 * P2.tol * np.linalg.norm(ref)
     s.server_stop()
     s.close()
+
+
+def test_large_requests_run_alone_between_launches():
+    """Requests with at least solo_min_unknowns unknowns run alone on the whole GPU between launches of the
+    server kernel (the server drains, runs them, resumes): in a mix with smaller requests each of them equals
+    kiops_solve of the same request bit for bit (same kernel and grid), and the smaller ones match the oracle."""
+    s = kiops.Solver(device=0)
+    s.server_start(hbm_budget_bytes=4e9, solo_min_unknowns=30000)
+    stream = small_stream(count=10, seed=31, n_range=(16, 40))
+    big = [P.n >= 30000 for _, P in stream]
+    assert any(big) and not all(big)
+    res = serve.run_stream(s, stream)
+    s.server_stop()
+    for ((_, P), w, st), alone in zip(zip(stream, res["w"], res["stats"]), big):
+        assert st["status"] == 0
+        if alone:
+            op = s.operator(P.op)
+            w_direct, _ = s.solve(op, P.tau, torch.as_tensor(P.b, device="cuda:0"), P.tol, P.m_init, P.m_o,
+                                  precision=P.precision)
+            assert torch.equal(w, w_direct), P.name
+        else:
+            ref, _, _ = oracle.kiops(P.op, P.tau, P.b, P.tol)
+            assert np.linalg.norm(w.cpu().numpy() - ref) <= 10 * P.tol * np.linalg.norm(ref), P.name
+    s.close()
