@@ -327,7 +327,9 @@ def measure_patterns(dev):
     # the error of each result against the FP64 oracle (its OpenMP build on the host cores, not timed here)
     import oracle
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    t_or = time.perf_counter()
     w_ref, st_ref, _ = oracle.kiops(P.op, P.tau, P.b, P.tol, m_init=P.m_init, m_o=P.m_o, parallel=True)
+    t_or = time.perf_counter() - t_or
     ref_n = float(np.linalg.norm(w_ref))
     err = {prec: float(np.linalg.norm(res[prec][1].cpu().numpy() - w_ref) / ref_n) for prec in res}
     out["mixed_precision_gray_scott_1024"] = {
@@ -335,6 +337,8 @@ def measure_patterns(dev):
         "speedup": res["fp64"][0] / res["fp32_basis"][0], "rel_err_vs_fp64": rel, "tol": P.tol,
         "rel_err_vs_oracle": {"fp32_basis": err["fp32_basis"], "fp64": err["fp64"]},
         "oracle_matvecs": st_ref["matvecs"],
+        "cpu_oracle_fp64": {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count() or 1,
+                            "sample": "one complete FP64 solve of this workload by the OpenMP build of the oracle"},
         "matvecs_fp32": res["fp32_basis"][2]["matvecs"], "matvecs_fp64": res["fp64"][2]["matvecs"]}
     s.close()
     # served: Poisson stream (2000/s) of the 3D ADR request mix with n in 16..64
