@@ -112,7 +112,7 @@ typedef struct {
 typedef struct {
   int64_t substeps;        /* accepted substeps */
   int64_t rejected;        /* rejected iterations */
-  int64_t matvecs;         /* applications of A~ (Algorithm 2 line 4), basis extensions included */
+  int64_t matvecs;         /* applications of A~ (Algorithm 2), basis extensions included */
   int64_t iterations;      /* accepted + rejected */
   int64_t expm_calls;      /* small dense exponentials (one per iteration) */
   int m_last;              /* Krylov dimension suggested for the next call (warm start, section 3.6) */
@@ -187,7 +187,7 @@ typedef struct {
   double* w;               /* device, N */
 } kiops_request;
 
-/* Defaults: m_min 10, m_max 128, normalize_B 1, breakdown_tol 1e-12 (Algorithm 1 line 1, section 3.7). */
+/* Defaults: m_min 10, m_max 128, normalize_B 1, breakdown_tol 1e-12 (Algorithm 1, section 3.7). */
 kiops_status kiops_config_default(kiops_config* cfg);
 
 /* Constants of the method as implemented: out[0..5] = delta (eq 39), gamma (eq 44), gamma_max
@@ -206,7 +206,7 @@ kiops_status kiops_attach_workspace(kiops_ctx* ctx, void* dptr, size_t bytes);
 kiops_status kiops_workspace_size(kiops_ctx* ctx, const kiops_op* A, int p, int m_o, kiops_precision prec,
                                   size_t* bytes);
 
-/* Operators (the matrix A of eq 12, applied matrix-free, Algorithm 2 lines 4-6).
+/* Operators (the matrix A of eq 12, applied matrix-free, Algorithm 2).
  * CSR: n x n, rowptr[n+1], colind[nnz] (int32), vals[nnz] (FP64), all device pointers, borrowed. */
 kiops_status kiops_op_csr(kiops_ctx* ctx, kiops_op** op, int64_t n, int64_t nnz, const int32_t* rowptr,
                           const int32_t* colind, const double* vals);
@@ -223,7 +223,7 @@ kiops_status kiops_op_apply(kiops_ctx* ctx, const kiops_op* A, const double* x, 
  *   p       0..KIOPS_MAX_P
  *   b       host array of p+1 DEVICE pointers b_0..b_p, each N FP64 values (natural order)
  *   tol     > 0, absolute tolerance of eq 39
- *   m_init  >= 1, first Krylov dimension (clipped to [m_min, m_max], Algorithm 1 line 3)
+ *   m_init  >= 1, first Krylov dimension (clipped to [m_min, m_max], Algorithm 1)
  *   m_o     >= 1, orthogonalisation length (2 = the paper's IOP; >= m_max = full Arnoldi)
  *   prec    KIOPS_FP64 or KIOPS_FP32_BASIS
  *   w       DEVICE output of N FP64 values (may alias b[0])
@@ -238,12 +238,12 @@ kiops_status kiops_solve_traced(kiops_ctx* ctx, const kiops_op* A, double tau, i
                                 kiops_stats* stats, kiops_trace_rec* trace, int64_t trace_cap,
                                 int64_t* trace_len);
 
-/* Task I (Algorithm 1 lines 31-36 with Algorithm 3): one adaptive run to T[n_times-1] that also returns
+/* Task I (Algorithm 1 with Algorithm 3): one adaptive run to T[n_times-1] that also returns
  *   w[l] = (1/T[l])^p * sum_k T[l]^k phi_k(T[l] A) b_k,   l = 0..n_times-1,
  * i.e. phi_p(T[l] A) b_p for every l when b_0..b_{p-1} are zero (the use the paper makes of it in
  * exponential integrators).  T: host array of increasing positive times (n_times <= KIOPS_MAX_TIMES);
  * w: host array of n_times DEVICE output pointers (N FP64 values each).  Outputs strictly inside an
- * accepted substep come from exp((T[l] - T_now) H_j) on that substep's basis (Algorithm 3 line 14);
+ * accepted substep come from exp((T[l] - T_now) H_j) on that substep's basis (Algorithm 3);
  * the substep sizes are not shortened to hit them. */
 kiops_status kiops_solve_task1(kiops_ctx* ctx, const kiops_op* A, const double* T, int n_times, int p,
                                const double* const* b, double tol, int m_init, int m_o, kiops_precision prec,

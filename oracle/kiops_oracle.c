@@ -22,8 +22,8 @@
  *   section 3.3.1 ([47] = Higham 2005)             diagonal Pade approximant with scaling and squaring
  *
  * Readings of passages that are ambiguous or garbled (each is also a switch or a documented choice):
- *   R1  H~ used in the exponential has a zero last row (eq 37), not the slice H(1:j+1,1:j+1) of
- *       Algorithm 1 line 18; opts.literal_last_row=1 selects the literal slice instead.
+ *   R1  H~ used in the exponential has a zero last row (eq 37), not the slice H(1:j+1,1:j+1) that
+ *       Algorithm 1 exponentiates; opts.literal_last_row=1 selects the literal slice instead.
  *   R2  eq 43 is applied as (q+1) = log(eps/eps_old) / log(tau/tau_old), the inverse of the printed
  *       ratio, so that it matches its own error model err ~ C tau^(q+1); q+1 = m/4 otherwise.
  *   R3  kappa (eq 45) and the order estimate (eq 43) are reset at each new substep and updated only
@@ -32,19 +32,19 @@
  *       to [m_min, m_max] (eq 46 and the text after it).
  *   R5  "remaining interval" is T_end - (T_now + tau) after an accepted step, T_end - T_now after a
  *       rejected one; a new substep starts with tau = min(tau, T_end - T_now).
- *   R6  happy breakdown when ||x|| <= breakdown_tol * ||A~ v_j|| (Algorithm 2 line 12).
+ *   R6  happy breakdown when ||x|| <= breakdown_tol * ||A~ v_j|| (the breakdown test of Algorithm 2).
  *   R7  ||B||_1 is the matrix 1-norm (largest column sum); nu = mu = 1 when it is 0 or p = 0.
- *   R8  Task I: the intermediate outputs of Algorithm 3 line 15 use beta (line 14) as their scale.
+ *   R16 Task I: the intermediate outputs of Algorithm 3 use beta, the substep's start-vector norm, as scale.
  *   R9  Cost model (eqs 40-42), evaluated after every iteration that did not break down.  Scenario A
  *       keeps m and takes tau_A from eq 44 (gamma = 0.9 after an accepted iteration, 0.6 after a
- *       rejected one, clipped as in Algorithm 4 lines 9-16); scenario B keeps tau and takes m_B from
+ *       rejected one, clipped as in Algorithm 4's m = m_max branch); scenario B keeps tau and takes m_B from
  *       eq 46 as in R4.  t_end - t_now is the remaining interval of R5 (cost 0 when none is left).
  *       nz(A~) in eq 41 counts the operator's stored nonzeros only (the B block is the separate
  *       (2p-1)N + p term): CSR nnz, 5 (2D) or 7 (3D) per unknown for a stencil plus one per unknown
  *       and coupling field, n^2 dense.  N_mult in eq 42 is the multiplication count of [47] for a
  *       matrix of the 1-norm of tau H~ (scaled by tau_A/tau for scenario A): pi_m = 2, 3, 4, 5, 6
  *       for Pade degrees 3, 5, 7, 9, 13 plus the s squarings.  With opts.scenario = 1 the cheaper
- *       scenario replaces Algorithm 4's choice in its line 18 branch (ties keep scenario B).
+ *       scenario replaces Algorithm 4's choice in its branch that varies m (ties keep scenario B).
  *       The cost values have no printed counterpart in the paper: parity unpinned (they are checked only
  *       against the paper's statement that scenario B is almost always the cheaper completion, and the
  *       cheaper-scenario mode against the exact dense exponential).
@@ -330,7 +330,7 @@ double oracle_n_mult(double x) { return n_mult(x); }
 double oracle_op_nonzeros(const oracle_op* A) { return op_nonzeros(A); }
 
 /* ------------------------------------------------------------------------------------------------
- * Augmented matrix-vector product (Algorithm 2 lines 4-6; Theorem 1 with B = [b_p, ..., b_1]).
+ * Augmented matrix-vector product (Algorithm 2; Theorem 1 with B = [b_p, ..., b_1]).
  * x has N + p entries: x[0:N] the state, x[N+t] (t = 0..p-1) the tail; tail row t pairs with
  * column t of B, which is b_{p-t}.  nu scales B (section 3.7).
  * ---------------------------------------------------------------------------------------------- */
@@ -422,11 +422,10 @@ int oracle_iop(const oracle_op* A, int p, const double* b_flat, const double* v_
  *                kappa = (omega/omega_old)^(1/(m_old - m)) when m changed and tau did not (kappa <= 1 or
  *                non-finite -> 2); q+1 = log(eps/eps_old)/log(tau/tau_old) when tau changed and m did not
  *                (<= 0 or non-finite -> m/4, section 3.6.1's q = m/4 - 1)
- *   lines 4-8    breakdown: tau_new = min(tau, remaining), m_new = m
- *   lines 9-13   j == m_max and rejected: m_new = j, tau_new = tau (gamma_max/omega)^(1/(q+1)) clipped to
- *                [tau/5, remaining]
- *   line 15      j == m_max and accepted: eq 44 with gamma = 0.9, clipped to [tau/5, 5 tau] and remaining
- *   line 18      otherwise: tau kept, m_new from eq 46 (R4)
+ *   breakdown    tau_new = min(tau, remaining), m_new = m
+ *   j == m_max   rejected: m_new = j, tau_new = tau (gamma_max/omega)^(1/(q+1)) clipped to [tau/5, remaining];
+ *                accepted: eq 44 with gamma = 0.9, clipped to [tau/5, 5 tau] and remaining
+ *   otherwise    tau kept, m_new from eq 46 (R4)
  * "remaining" is R5's: T_end - (T_now + tau) after an accepted iteration, T_end - T_now after a rejected one.
  * ---------------------------------------------------------------------------------------------- */
 typedef struct {
@@ -447,13 +446,13 @@ typedef struct {
 
 void oracle_alg4(oracle_alg4_state* st, int new_substep, int j, int m, int m_min, int m_max, double tau,
                  double t_now, double T_end, double tol, double eps, int breakdown, oracle_alg4_out* out) {
-  const double delta = 1.4, gamma = 0.9, gamma_max = 0.6; /* section 3.5, Algorithm 4 lines 2-3 */
+  const double delta = 1.4, gamma = 0.9, gamma_max = 0.6; /* section 3.5, Algorithm 4 */
   if (new_substep) {
     st->have_prev = 0; st->prev_j = 0;
     st->prev_tau = st->prev_omega = st->prev_eps = 0.0;
     st->kappa = 2.0; st->qp1_est = 0.0;
   }
-  const double omega = breakdown ? 0.0 : T_end * eps / (tau * tol); /* eq 39; line 5 */
+  const double omega = breakdown ? 0.0 : T_end * eps / (tau * tol); /* eq 39; 0 on a breakdown */
   const int accepted = omega <= delta;
   const double remaining = T_end - (accepted ? t_now + tau : t_now);
   if (!accepted && st->have_prev) { /* R3 */
@@ -468,10 +467,10 @@ void oracle_alg4(oracle_alg4_state* st, int new_substep, int j, int m, int m_min
   const double qp1 = st->qp1_est > 0.0 ? st->qp1_est : (double)j / 4.0; /* section 3.6.1: q = m/4 - 1 */
   double tau_new;
   int m_new;
-  if (breakdown) { /* lines 4-8 */
+  if (breakdown) { /* tau and m kept */
     tau_new = tau < remaining ? tau : remaining;
     m_new = m;
-  } else if (j == m_max) { /* lines 9-16 */
+  } else if (j == m_max) { /* tau varies */
     if (omega > delta) {
       m_new = j;
       tau_new = tau * pow(gamma_max / omega, 1.0 / qp1);
@@ -484,7 +483,7 @@ void oracle_alg4(oracle_alg4_state* st, int new_substep, int j, int m, int m_min
       if (tau_new < tau / 5.0) tau_new = tau / 5.0;
       if (tau_new > remaining) tau_new = remaining;
     }
-  } else { /* line 18: section 3.6.2, eq 46, R4 */
+  } else { /* m varies: section 3.6.2, eq 46, R4 */
     tau_new = tau;
     double mn = (double)m + log(omega / gamma) / log(st->kappa);
     double lo = floor(0.75 * (double)m), hi = ceil(4.0 * (double)m / 3.0);
@@ -495,7 +494,7 @@ void oracle_alg4(oracle_alg4_state* st, int new_substep, int j, int m, int m_min
     if (mn > m_max) mn = m_max;
     m_new = (int)mn;
   }
-  if (!accepted) { /* lines 26-28 keep the basis; this iteration becomes the "old" one (R3) */
+  if (!accepted) { /* a rejection keeps the basis; this iteration becomes the "old" one (R3) */
     st->have_prev = 1; st->prev_j = j; st->prev_tau = tau; st->prev_omega = omega; st->prev_eps = eps;
   }
   out->omega = omega; out->accepted = accepted; out->kappa = st->kappa; out->qp1 = qp1;
@@ -505,19 +504,19 @@ void oracle_alg4(oracle_alg4_state* st, int new_substep, int j, int m, int m_min
 /* ------------------------------------------------------------------------------------------------
  * Algorithm 1 with Algorithms 2-4.
  *   T, n_steps  output times T(1) < ... < T(end) (Task II: one time)
- *   task1       Task I: outputs at every T(l), scaled by (1/T(l))^p (Algorithm 1 lines 31-35)
+ *   task1       Task I: outputs at every T(l), scaled by (1/T(l))^p (Algorithm 1)
  *   b_flat      (p+1) vectors b_0..b_p of length N, contiguous, natural order
  *   W           n_steps columns of N entries (column l: the result at T(l))
  *   stats       [substeps, rejected, matvecs, m_last, iterations]
- * Reading R8: the intermediate outputs of Algorithm 3 line 15 are scaled by beta, the norm of the
- * substep's start vector (line 14); the printed ||w(:,l)|| would read a column line 15 has overwritten.
+ * Reading R16: the intermediate outputs of Algorithm 3 are scaled by beta, the norm of the
+ * substep's start vector; the printed ||w(:,l)|| would read a column the previous output has overwritten.
  * ---------------------------------------------------------------------------------------------- */
 static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task1, int p, const double* b_flat,
                       double tol, int m_init, const oracle_opts* o, double* W, int64_t* stats,
                       oracle_trace* trace, int64_t trace_cap, int64_t* trace_len) {
   const double T_end = T[n_steps - 1];
-  int ell = 0;  /* current output column (Algorithm 1 line 6) */
-  const double gamma = 0.9, gamma_max = 0.6; /* Algorithm 4 line 2 (scenario A of the cost model, R9) */
+  int ell = 0;  /* current output column (Algorithm 1) */
+  const double gamma = 0.9, gamma_max = 0.6; /* Algorithm 4 (scenario A of the cost model, R9) */
   int64_t N = A->n, M = N + p;
   int m_min = o->m_min, m_max = o->m_max, m_o = o->m_o;
   const double* b[8];
@@ -529,7 +528,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
   for (int k = 0; k <= p; ++k) b[k] = b_flat + (size_t)k * N;
   if (trace_len) *trace_len = 0;
   for (int k = 0; k < 5; ++k) stats[k] = 0;
-  memcpy(W, b[0], (size_t)N * sizeof(double)); /* Algorithm 1 line 8 */
+  memcpy(W, b[0], (size_t)N * sizeof(double)); /* Algorithm 1: w = b_0 */
   if (T_end == 0.0) { stats[3] = m_init; return ORACLE_OK; }
 
   /* section 3.7, eqs 48-49 */
@@ -556,7 +555,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
   double* F = (double*)malloc((size_t)nmax * nmax * sizeof(double));
   if (!V || !h || !x || !ht || !F) { free(V); free(h); free(x); free(ht); free(F); return ORACLE_ENOMEM; }
 
-  int m = m_min > (m_init < m_max ? m_init : m_max) ? m_min : (m_init < m_max ? m_init : m_max); /* line 3 */
+  int m = m_min > (m_init < m_max ? m_init : m_max) ? m_min : (m_init < m_max ? m_init : m_max); /* m_init clipped to [m_min, m_max] */
   double tau = T_end, t_now = 0.0, beta = 0.0;
   int j = 0, rc = ORACLE_OK;
   int64_t substeps = 0, rejected = 0, matvecs = 0, iters = 0;
@@ -564,12 +563,12 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
   oracle_alg4_state a4;
   int new_sub = 1;
 
-  while (t_now < T_end) { /* line 9 */
+  while (t_now < T_end) {
     if (iters >= o->max_iterations || substeps >= o->max_substeps) { rc = ORACLE_ENOTCONV; break; }
-    if (j == 0) { /* lines 10-15 */
+    if (j == 0) { /* new substep: start vector */
       if (tau > T_end - t_now) tau = T_end - t_now; /* R5 */
       memcpy(V, W + (size_t)ell * N, (size_t)N * sizeof(double));
-      for (int t = 0; t < p; ++t) { /* line 13 (corrigendum), eq 47, times mu */
+      for (int t = 0; t < p; ++t) { /* tail (corrigendum), eq 47, times mu */
         int e = p - 1 - t;
         double v = 1.0;
         for (int i = 1; i <= e; ++i) v *= t_now / (double)i;
@@ -582,13 +581,13 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
       }
       double inv = 1.0 / beta;
 #pragma omp parallel for
-      for (int64_t r = 0; r < M; ++r) V[r] *= inv; /* line 14 */
+      for (int64_t r = 0; r < M; ++r) V[r] *= inv; /* V_1 = [w; tail] / beta */
       memset(h, 0, (size_t)ldh * ldh * sizeof(double));
       new_sub = 1;
     }
-    int breakdown = iop(A, p, b, nu, V, h, ldh, &j, m, m_o, o->breakdown_tol, x, &matvecs); /* line 16 */
+    int breakdown = iop(A, p, b, nu, V, h, ldh, &j, m, m_o, o->breakdown_tol, x, &matvecs); /* Algorithm 2 */
 
-    /* lines 17-18 with eq 37 (R1): H~ = [[H_j, e_1], [0, 0]] */
+    /* the exponential, eq 37 (R1): H~ = [[H_j, e_1], [0, 0]] */
     int n = j + 1;
     for (int r = 0; r < n; ++r)
       for (int c = 0; c < n; ++c) ht[r * n + c] = 0.0;
@@ -600,10 +599,10 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
     const double hnorm = norm1(n, ht); /* ||tau H~||_1, for the cost model (R9) */
     if (oracle_expm(n, ht, F) != ORACLE_OK) { rc = ORACLE_ENOTCONV; break; }
 
-    /* line 19: eqs 36, 38 */
+    /* eqs 36, 38 */
     double eps = 0.0;
     if (!breakdown) eps = beta * h[j * ldh + (j - 1)] * fabs(F[(j - 1) * n + j]);
-    /* lines 20-22: eq 39 and Algorithm 4 */
+    /* eq 39 and Algorithm 4 */
     oracle_alg4_out d;
     oracle_alg4(&a4, new_sub, j, m, m_min, m_max, tau, t_now, T_end, tol, eps, breakdown, &d);
     new_sub = 0;
@@ -613,7 +612,7 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
     double tau_new = d.tau_new;
     int m_new = d.m_new;
 
-    /* R9: eq 40 for both scenarios; opts.scenario = 1 takes the cheaper one in the line 18 branch */
+    /* R9: eq 40 for both scenarios; opts.scenario = 1 takes the cheaper one where Algorithm 4 varies m */
     double cost_a = 0.0, cost_b = 0.0;
     if (!breakdown) {
       double tau_a = tau * pow((accepted ? gamma : gamma_max) / omega, 1.0 / qp1);
@@ -645,23 +644,23 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
     }
     iters++;
 
-    if (accepted) { /* lines 22-25, Algorithm 3 */
-      if (task1) { /* Algorithm 3 lines 4-19: outputs strictly inside this substep */
+    if (accepted) { /* accepted: Algorithm 3 */
+      if (task1) { /* Algorithm 3: outputs strictly inside this substep */
         int n_tau = 0;
         for (int k = ell; k < n_steps; ++k)
           if (fabs(T[k]) < fabs(t_now + tau)) n_tau++;
         if (n_tau > 0) {
-          memcpy(W + (size_t)(ell + n_tau) * N, W + (size_t)ell * N, (size_t)N * sizeof(double)); /* line 11 */
+          memcpy(W + (size_t)(ell + n_tau) * N, W + (size_t)ell * N, (size_t)N * sizeof(double)); /* running state carried to the next column */
           double* h2 = (double*)malloc((size_t)j * j * sizeof(double));
           double* F2 = (double*)malloc((size_t)j * j * sizeof(double));
           if (!h2 || !F2) { free(h2); free(F2); rc = ORACLE_ENOMEM; break; }
           for (int k = 0; k < n_tau; ++k) {
-            const double tt = T[ell + k] - t_now; /* line 13 */
+            const double tt = T[ell + k] - t_now;
             for (int r = 0; r < j; ++r)
               for (int cc = 0; cc < j; ++cc) h2[r * j + cc] = tt * h[r * ldh + cc];
-            if (oracle_expm(j, h2, F2) != ORACLE_OK) { rc = ORACLE_ENOTCONV; break; } /* line 14 */
+            if (oracle_expm(j, h2, F2) != ORACLE_OK) { rc = ORACLE_ENOTCONV; break; } /* exp((T(k) - T_now) H_j) */
             double* wk = W + (size_t)(ell + k) * N;
-            for (int64_t r = 0; r < N; ++r) { /* line 15 */
+            for (int64_t r = 0; r < N; ++r) { /* beta V F(:, 1), R16 */
               double sacc = 0.0;
               for (int cc = 0; cc < j; ++cc) sacc += V[(size_t)cc * M + r] * F2[cc * j + 0];
               wk[r] = beta * sacc;
@@ -670,10 +669,10 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
           free(h2);
           free(F2);
           if (rc != ORACLE_OK) break;
-          ell += n_tau; /* line 17 */
+          ell += n_tau;
         }
       }
-      double* wl = W + (size_t)ell * N; /* the last line of Algorithm 3: w = beta V(1:N,1:j) F(1:j,1) */
+      double* wl = W + (size_t)ell * N; /* Algorithm 3, the Task II update: w = beta V(1:N,1:j) F(1:j,1) */
 #pragma omp parallel for
       for (int64_t r = 0; r < N; ++r) {
         double s = 0.0;
@@ -684,13 +683,13 @@ static int kiops_core(const oracle_op* A, const double* T, int n_steps, int task
       else t_now = t_next;
       j = 0;
       substeps++;
-    } else { /* lines 26-28: keep the basis */
+    } else { /* rejected: keep the basis */
       rejected++;
     }
     tau = tau_new;
     m = m_new;
   }
-  if (task1 && rc == ORACLE_OK) /* Algorithm 1 lines 31-35 */
+  if (task1 && rc == ORACLE_OK) /* Algorithm 1: outputs scaled by (1/T(l))^p */
     for (int l = 0; l < n_steps; ++l) {
       double sc = 1.0;
       for (int k = 0; k < p; ++k) sc *= 1.0 / T[l];
@@ -708,7 +707,7 @@ int oracle_kiops(const oracle_op* A, double T_end, int p, const double* b_flat, 
   return kiops_core(A, &T_end, 1, 0, p, b_flat, tol, m_init, o, w_out, stats, trace, trace_cap, trace_len);
 }
 
-/* Task I: W(:, l) = (1/T(l))^p e^{T(l) A~} v (top N entries), l = 1..n_steps (Algorithm 1 lines 31-36). */
+/* Task I: W(:, l) = (1/T(l))^p e^{T(l) A~} v (top N entries), l = 1..n_steps (Algorithm 1). */
 int oracle_kiops_task1(const oracle_op* A, const double* T, int n_steps, int p, const double* b_flat, double tol,
                        int m_init, const oracle_opts* o, double* W, int64_t* stats, oracle_trace* trace,
                        int64_t trace_cap, int64_t* trace_len) {

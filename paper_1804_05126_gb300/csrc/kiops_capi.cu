@@ -557,7 +557,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   if (!ctx) return KIOPS_EINVAL;
   if (trace_len) *trace_len = 0;
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  if (tau == 0.0 && A && b && w && b[0]) {  // w = b_0, no work (Algorithm 1 lines 8-9)
+  if (tau == 0.0 && A && b && w && b[0]) {  // w = b_0, no work (Algorithm 1)
     if (w != b[0]) KCHECK(ctx, cudaMemcpyAsync(w, b[0], (size_t)A->d.n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
     if (stats) stats->m_last = std::max(ctx->cfg.m_min, std::min(m_init, ctx->cfg.m_max));

@@ -1,9 +1,9 @@
 // Device side of the KIOPS solver for GB300 (sm_103a).
 //
 // One kernel template runs Algorithm 1 (Task II) of Gaudreault, Rainwater & Tokman (JCP 372, 2018)
-// end to end on the device: setup (section 3.7), start vector (Algorithm 1 lines 10-15), IOP steps
+// end to end on the device: setup (section 3.7), start vector (Algorithm 1), IOP steps
 // (Algorithm 2), the small exponential of tau H~ (eqs 37-38), the estimate and acceptance (eqs 36, 39),
-// Algorithm 4 with sections 3.6.1-3.6.2, and the update w = beta V F(:,1) (Algorithm 3, Task II line).
+// Algorithm 4 with sections 3.6.1-3.6.2, and the update w = beta V F(:,1) (Algorithm 3, Task II).
 //
 // Two execution "teams" share that code:
 //   GridTeam  one persistent cooperative launch spreads every vector phase over all blocks of the GPU;
@@ -290,7 +290,7 @@ struct Ctl {
   int cache_ok;                 // fused path: the B / coupling cache is filled
   int tbl_ok;                   // fused path: the halo index table is filled
   double vtail[kGramRing][kMaxP];  // fused path: tail of v_k (basis precision) in row k % kGramRing
-  int ell;                      // Task I: next output index (Algorithm 1 line 6)
+  int ell;                      // Task I: next output index (Algorithm 1)
   double ntail[kMaxP];          // nu * tail (the B-block weights of the step)
   float ntail_f[kMaxP];         // the same weights rounded to FP32 (FP32 basis)
   double gram[kGramRing][kGramRing];  // row i % kGramRing: <v_i, v_{i-o}>, o = 0..m_o-1 (m_o <= kGramRing)
@@ -456,7 +456,7 @@ __device__ __forceinline__ bool finish_reduce_hook(Team& team, Ctl& c, double* p
 }
 
 // ------------------------------------------------------------------------------------------------
-// Operators: row r of A x (matrix-free; Algorithm 2 lines 4-6 apply A to the first N entries).
+// Operators: row r of A x (matrix-free; Algorithm 2 applies A to the first N entries).
 // ------------------------------------------------------------------------------------------------
 // Index just outside [0, n) under the operator's boundary rule; returns -1 where the value is 0.
 __device__ __forceinline__ int64_t bc_index(int bc, int64_t i, int64_t n) {
@@ -1639,7 +1639,7 @@ template <class Team>
 __device__ __noinline__ bool expm_phase(const SolveArgs& a, Team& team, Ctl& c, int& parity, double* smem_dyn,
                                         bool aug = true, double scale = 0.0) {
   // aug: exp(tau H~) of size j+1 (eqs 37-38), F(:,1) and F(j, j+1) into fvec.  !aug: exp(scale H_j) of
-  // size j (Algorithm 3 line 14), its first column into fvec.
+  // size j (Algorithm 3), its first column into fvec.
   const bool prof_on = a.prof != nullptr && team.rank == 0;
   const int n = a.expm_only ? a.expm_n : (aug ? c.j + 1 : c.j);
   const size_t ldm = (size_t)(a.m_max + 1) * (a.m_max + 1);
@@ -1883,7 +1883,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
     return;
   }
 
-  // ---- setup (section 3.7): ||B||_1 = max_k sum_i |b_k,i|; w = b_0 (Algorithm 1 line 8)
+  // ---- setup (section 3.7): ||B||_1 = max_k sum_i |b_k,i|; w = b_0 (Algorithm 1)
   {
     double acc[kRegK];
     for (int base = 1; base <= p; base += kRegK) {
@@ -1947,7 +1947,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         c.nu = ldexp(1.0, -e);
         c.mu = ldexp(1.0, e);
       }
-      // Algorithm 1 lines 2-5
+      // Algorithm 1: first tau and m
       int m = a.m_init < a.m_max ? a.m_init : a.m_max;
       c.m = m > a.m_min ? m : a.m_min;
       c.tau = a.T_end;
@@ -1958,14 +1958,14 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
   }
 
   KIOPS_TICK(0);
-  while (c.t_now < a.T_end) {  // Algorithm 1 line 9
+  while (c.t_now < a.T_end) {  // Algorithm 1
     if (c.iters >= a.max_iters || c.substeps >= a.max_substeps) {
       if (tid == 0) c.status = ST_ENOTCONV;
       __syncthreads();
       break;
     }
     if (c.j == 0) {
-      // ---- new substep: tail (line 13 + corrigendum, eq 47, times mu), beta = ||[w; tail]||, V_1
+      // ---- new substep: tail (corrigendum, eq 47, times mu), beta = ||[w; tail]||, V_1
       if (tid == 0) {
         if (c.tau > a.T_end - c.t_now) c.tau = a.T_end - c.t_now;
         for (int t = 0; t < p; ++t) {
@@ -2000,7 +2000,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         break;
       }
       {
-        const double ib = 1.0 / c.beta;  // Algorithm 1 line 14
+        const double ib = 1.0 / c.beta;  // Algorithm 1
         for (int64_t r = r0 + tid; r < r1; r += kThreads) V[r] = (T)(a.w[r] * ib);
         if (lead && tid < p) V[N + tid] = (T)(c.tail[tid] * ib);
       }
@@ -2193,7 +2193,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         if (!finish_reduce_hook<Team>(team, c, a.partials, parity, Ktot, prof_on, prefetch)) goto stop;
       }
       KIOPS_TICK(3);
-      // ---- MGS coefficients from CGS dots and the Gram entries (Algorithm 2 lines 7-10):
+      // ---- MGS coefficients from CGS dots and the Gram entries (Algorithm 2):
       // h_i = <v_i, x> - sum_{k<i} h_k <v_i, v_k>;  ||x - sum h_i v_i||^2 expanded over the window
       if (tid == 0) {
         const double nx2 = c.red[nwin];
@@ -2286,7 +2286,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
           if (lead)
             for (int u = 0; u < c.nwin; ++u) a.H[(size_t)(c.i0 + u - 1) * ldh + (j - 1)] = c.hcoef[u];
           c.j = j;
-          if (c.s * c.s <= a.bd_tol * a.bd_tol * nx2_pre) {  // happy breakdown (Algorithm 2 lines 12-15)
+          if (c.s * c.s <= a.bd_tol * a.bd_tol * nx2_pre) {  // happy breakdown (Algorithm 2)
             c.breakdown = 1;
             c.sub[j] = 0.0;
           } else {
@@ -2307,7 +2307,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       KIOPS_TICK(4);
       if (c.breakdown) break;
       if (fused) continue;  // v_{j+1} is finalised by the next step's tiles (or stays pending)
-      // ---- v_{j+1} = (1/s) (x - sum_i h_i v_i) in MGS order (lines 9, 16-17)
+      // ---- v_{j+1} = (1/s) (x - sum_i h_i v_i) in MGS order (Algorithm 2)
       if (nwin <= kChunk) {
         const T h0 = T(c.hcoef[0]), h1 = nwin > 1 ? T(c.hcoef[1]) : T(0), h2 = nwin > 2 ? T(c.hcoef[2]) : T(0);
         const T rsT = T(c.rs);
@@ -2355,10 +2355,10 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       KIOPS_TICK(5);
     }
 
-    // ---- Algorithm 1 lines 17-18: F = exp(tau H~)
+    // ---- Algorithm 1: F = exp(tau H~)
     if (!expm_phase<Team>(a, team, c, parity, smem_dyn)) goto stop;
 
-    // ---- lines 19-22: estimate (eq 36), omega (eq 39), Algorithm 4 (sections 3.6.1, 3.6.2)
+    // ---- estimate (eq 36), omega (eq 39), Algorithm 4 (sections 3.6.1, 3.6.2)
     if (tid == 0) {
       const double delta = 1.4, gamma = 0.9, gamma_max = 0.6;
       const int j = c.j;
@@ -2473,7 +2473,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       for (int k = tid; k < j; k += kThreads) c.hcoef[k] = a.fvec[k];
       __syncthreads();
       const double beta = c.beta;
-      if (a.n_times > 0) {  // Task I: outputs T(k) < T_now + tau (Algorithm 3 lines 4-18)
+      if (a.n_times > 0) {  // Task I: outputs T(k) < T_now + tau (Algorithm 3)
         while (c.ell < a.n_times - 1 && fabs(a.times[c.ell]) < fabs(c.t_sub + c.tau_sub)) {
           if (!expm_phase<Team>(a, team, c, parity, smem_dyn, false, a.times[c.ell] - c.t_sub)) goto stop;
           for (int k = tid; k < j; k += kThreads) c.yint[k] = a.fvec[k];
@@ -2490,7 +2490,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       KIOPS_TICK(10);
     }
   }
-  if (a.n_times > 0 && c.status == ST_OK) {  // Task I: w(:, l) *= (1/T(l))^p (Algorithm 1 lines 31-35)
+  if (a.n_times > 0 && c.status == ST_OK) {  // Task I: w(:, l) *= (1/T(l))^p (Algorithm 1)
     for (int l = 0; l < a.n_times; ++l) {
       double sc = 1.0;
       for (int k = 0; k < p; ++k) sc *= 1.0 / a.times[l];

@@ -43,7 +43,7 @@ SCEN = _scenarios()
 def test_golden_file_covers_every_branch_of_algorithm_4():
     rows = [(s, r) for s in SCEN for r in s["rows"]]
     assert len(SCEN) == 5 and len(rows) == 14
-    assert any(r[0][6] for _, r in rows)                                          # breakdown (lines 4-8)
+    assert any(r[0][6] for _, r in rows)                                          # breakdown
     assert any(r[0][1] == s["m_max"] and not r[1][1] for s, r in rows)            # m_max, rejected (9-13)
     assert any(r[0][1] == s["m_max"] and r[1][1] and not r[0][6] for s, r in rows)  # m_max, accepted (15)
     assert any(r[0][1] < s["m_max"] and not r[0][6] for s, r in rows)              # vary m (18)

@@ -331,7 +331,7 @@ def test_matvec_count_equals_basis_growth():
     assert st["matvecs"] == sum(last_j.values())
 
 
-# ---------------------------------------------------------------- Task I (Algorithm 1 lines 31-35, Algorithm 3)
+# ---------------------------------------------------------------- Task I (Algorithm 1 with Algorithm 3)
 def test_task1_single_phi_at_several_times_vs_dst():
     """Task I with b = [0, 0, b_2]: W[l] = phi_2(T_l A) b_2, checked against the DST-I closed form."""
     n, tol = 120, 1e-10
@@ -355,7 +355,7 @@ def test_task1_general_combination_vs_dense_expm():
     b = rng.standard_normal((p + 1, n))
     T = [0.003, 0.007, 0.0071, 0.02]
     Wt, st = oracle.kiops_task1({"kind": "dense", "n": n, "a": a}, T, b, tol, m_max=16, m_min=5)
-    assert st["status"] == 0  # one substep: the first three outputs come from Algorithm 3 lines 4-18
+    assert st["status"] == 0  # one substep: the first three outputs come from Algorithm 3, inside the substep
     for l, t in enumerate(T):
         assert err_ok(Wt[l], exact_dense(a, b, t) / t**p, tol / t**p), l
 
