@@ -106,7 +106,10 @@ typedef struct {
   int tma_stages;          /* that path's tiles in flight per block (2 to 6; 0 = 2) */
   int tma_prefetch;        /* that path's L2 lookahead: tiles fetched into L2 (bulk prefetch, no shared memory)
                               this many tiles before their shared-memory copy is issued; 0 = none, -1 (default)
-                              = automatic (tma_stages + 2) */
+                              = automatic (none: measured slower with it) */
+  int tma_fixed;           /* that path with an FP32 basis, 32 x 16 tiles, two species and p = 3 on a grid of
+                              whole tiles: 1 (default) = run the kernel compiled for exactly that configuration
+                              (constant loop bounds and offsets), 0 = the general one */
 } kiops_config;
 
 typedef struct {
@@ -126,6 +129,11 @@ typedef struct {
    * finalisation of v_j, 13 tiled path: A~ v_j and dots, 14 tiled path with bulk tensor copies: waits for a
    * tile's copies; other entries 0. */
   int64_t phase_cycles[16];
+  /* 2D stencils on the grid engine: how the Krylov step ran.  tile_path 0 = not tiled (or one tile per
+   * block), 1 = several tiles per block with per-element loads, 2 = several tiles per block staged by bulk
+   * tensor copies, 3 = as 2 with the kernel compiled for 32 x 16 tiles, two species and p = 3; tile_w,
+   * tile_h = the tile shape of paths 1 to 3 (0 otherwise). */
+  int tile_path, tile_w, tile_h;
 } kiops_stats;
 
 /* One record per iteration (accepted or rejected) when a trace buffer is given. */

@@ -13,7 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkiops.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["kiops_kernels_f64.cu", "kiops_kernels_f64_wide.cu", "kiops_kernels_f32.cu", "kiops_server.cu",
-           "kiops_capi.cu", "kiops_integrate.cu", "kiops_probe.cu", "kiops_kernels_tma.cu"]
+           "kiops_capi.cu", "kiops_integrate.cu", "kiops_probe.cu", "kiops_kernels_tma.cu",
+           "kiops_kernels_tma_fixed.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -320,7 +320,9 @@ bool setup_tma(kiops_ctx* ctx, void* fn, int blocks, int threads, Prepared& P) {
     if ((int64_t)per_sm * ctx->sms < blocks) continue;
     a.tma_on = 1;
     a.tma_stages = S;
-    a.tma_prefetch = ctx->cfg.tma_prefetch < 0 ? S + 2 : std::min(ctx->cfg.tma_prefetch, 64);
+    // L2 prefetch ahead of the staged copies: off unless asked for (2048^2 Gray-Scott FP32: 117 us per step
+    // without, 122 us with 2 tiles beyond the stages)
+    a.tma_prefetch = ctx->cfg.tma_prefetch < 0 ? 0 : std::min(ctx->cfg.tma_prefetch, 64);
     a.tma_pad = pad;
     a.tma_bw = bw;
     a.tma_bh = bh;
@@ -546,6 +548,7 @@ void fill_stats(kiops_stats* st, const int64_t* s, const double* sd, int engine,
   st->engine = engine;
   st->grid_blocks = blocks;
   st->err_est = sd[0];
+  st->tile_path = st->tile_w = st->tile_h = 0;
 }
 
 // One solve on the grid engine (or a single-block CTA launch).
@@ -608,9 +611,21 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   }
   void* fn_tma = (A->d.kind == OP_ST2D && threads == kThreads) ? kiops_k::solve_kernel_tma(fp32) : nullptr;
   if (engine == KIOPS_ENGINE_GRID && fn_tma && prepare_kernel(ctx, fn_tma) == KIOPS_OK &&
-      setup_tma(ctx, fn_tma, blocks, threads, P))
+      setup_tma(ctx, fn_tma, blocks, threads, P)) {
     fn = fn_tma;  // the instantiation with the bulk-tensor-copy path
-  else if (engine == KIOPS_ENGINE_GRID)
+    // the instantiation compiled for 32 x 16 tiles, two species and p = 3, on a grid of whole tiles
+    const SolveArgs& sa = P.args;
+    if (fp32 && ctx->cfg.tma_fixed != 0 && sa.tile_w == 32 && sa.tile_h == 16 && sa.op.nspecies == 2 && sa.p == 3 &&
+        sa.op.nx % 32 == 0 && sa.op.ny % 16 == 0) {
+      void* fx = kiops_k::solve_kernel_tma_fixed();
+      int per_sm = 0;
+      if (cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.dyn_smem) == cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fx, threads, P.dyn_smem) == cudaSuccess &&
+          (int64_t)per_sm * ctx->sms >= blocks)
+        fn = fx;
+      cudaGetLastError();
+    }
+  } else if (engine == KIOPS_ENGINE_GRID)
     enable_fused_smem(ctx, fn, blocks, P, threads);
   st = ensure_workspace(ctx, P.L.total);
   if (st) return st;
@@ -665,6 +680,11 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   const double* hsd = (const double*)(hs + 10);
   fill_stats(stats, hs, hsd, engine, blocks);
   if (stats && ctx->cfg.profile) std::memcpy(stats->phase_cycles, hprof, 16 * 8);
+  if (stats && P.args.fused && (int64_t)P.args.tile_gx * P.args.tile_gy > blocks) {
+    stats->tile_path = !P.args.tma_on ? 1 : (fn == fn_tma ? 2 : 3);
+    stats->tile_w = P.args.tile_w;
+    stats->tile_h = P.args.tile_h;
+  }
   const int dst = (int)hs[6];
   if (dst == ST_ETIMEOUT) return fail(ctx, KIOPS_ETIMEOUT, "a device-side wait exceeded %.3g s", ctx->cfg.timeout_s);
   if (dst == ST_ENOTCONV)
@@ -721,6 +741,7 @@ kiops_status kiops_config_default(kiops_config* cfg) {
   cfg->tile_h = 0;
   cfg->tma_stages = 0;
   cfg->tma_prefetch = -1;
+  cfg->tma_fixed = 1;
   return KIOPS_OK;
 }
 

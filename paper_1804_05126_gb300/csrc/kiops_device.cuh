@@ -32,6 +32,9 @@ namespace KIOPS_DEV_NS {
 #endif
 constexpr int kThreads = KIOPS_THREADS;  // threads per block (256 or 512)
 constexpr int kWarps = kThreads / 32;
+// Kernel variants of the 2D several-tiles path with bulk tensor copies: none, any tile shape / species
+// count / p, or compiled for 32 x 16 tiles, two species and p = 3 (grids that are whole multiples of it).
+constexpr int kTmaNone = 0, kTmaGeneral = 1, kTmaFixed = 2;
 // blocks per SM the register budget is sized for (two of 256 threads or one of 512: 128 registers a thread)
 constexpr int kMinBlocks = kThreads <= 256 ? 2 : 1;
 constexpr int kMaxM = 256;                 // largest m_max
@@ -1104,25 +1107,30 @@ __device__ __forceinline__ void stg16(double* p, const Vec16<double>& v) {
 //   (which contain the dot window of step j);
 //   own-point boxes: the B columns and the coupling fields.
 // Points outside the grid arrive as zeros from the copy, which is the Dirichlet value; for periodic and
-// reflected boundaries those halo points are read from global memory at their mapped index instead.
+// reflected boundaries the halo points the stencil reads there (one row above or below the tile, one column
+// left or right of it) are finalised from global memory at their mapped index, in a separate pass over the
+// edge tiles only (so that the main loops carry no boundary test).
 // The loops take 16 bytes of consecutive points per item (tile widths are multiples of that): 128-bit
 // shared-memory loads and global stores, coefficients and B-block weights held in registers.  Per element
 // the arithmetic and its order are those of fused_st2d_tiles; the elements are accumulated in another order.
-template <typename T>
+// CTW, CTH, CNS, CP > 0 (CP >= 0) fix the tile shape, the species count and p at compile time (an
+// instantiation for grids that are whole multiples of the tile): the loop bounds, the shared-memory offsets
+// and the B-block loop are then constants.  0 (CP = -1): taken from the arguments.
+template <typename T, int CTW = 0, int CTH = 0, int CNS = 0, int CP = -1>
 __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0,
                                                int nwin, T* V, size_t ldv, double* smem, DotAcc<T>& acc,
                                                bool prof_on) {
   constexpr int W = Vec16<T>::W;
+  constexpr bool kFixed = CTW > 0 && CTH > 0 && CNS > 0;
   const OpDesc& op = a.op;
   const int nx = (int)op.nx, ny = (int)op.ny;
   const uint32_t npts = (uint32_t)nx * (uint32_t)ny;
-  const int ns = op.nspecies;
-  const int p = a.p;
+  const int ns = CNS > 0 ? CNS : op.nspecies;
+  const int p = CP >= 0 ? CP : a.p;
   const int tid = threadIdx.x;
   const int bc = op.bc;
   T* raw = (T*)a.raw;
   const bool pend = c.fin_pending != 0;
-  const T* src = pend ? raw + (size_t)((j - 1) & 1) * ldv : V + (size_t)(j - 1) * ldv;  // v_j before finalising
   T* vj = V + (size_t)(j - 1) * ldv;
   T* xo = raw + (size_t)(j & 1) * ldv;  // raw x_{j+1}
   const int fnw = pend ? c.fin_nwin : 0;
@@ -1132,9 +1140,6 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
   // window boxes: the finalisation window (pending) or the dot window below v_j (first step)
   const int fbase = pend ? c.fin_i0 : i0;
   const int nfb = pend ? fnw : nwin - 1;
-  const T* f0 = V + (size_t)(fbase - 1) * ldv;
-  const T* f1 = V + (size_t)(fbase + (nfb > 1 ? 1 : 0) - 1) * ldv;
-  const T* f2 = V + (size_t)(fbase + (nfb > 2 ? 2 : 0) - 1) * ldv;
   const int wslot0 = i0 - fbase, wslot1 = i0 + 1 - fbase;  // window entries i0, i0 + 1 (when below j)
   // loop invariants in registers (the shared-memory stores of the finalisation go through generic pointers,
   // so values read from shared memory inside the loops would be read again after each store)
@@ -1153,10 +1158,12 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     for (int t = 0; t < 4; ++t) ntr[t] = t < p ? nt[t] : T(0);
   }
   const T* ntp = ntail_ptr<T>(c);
-  const int S = a.tma_stages, A = a.tma_pad, BW = a.tma_bw, BH = a.tma_bh;  // A == W
-  const int TW = a.tile_w, TH = a.tile_h;
-  const int bplane = BW * BH, bsz = ns * bplane;     // elements of one halo'd box (all species)
-  const int fst = a.tma_box_bytes / (int)sizeof(T);  // elements between window boxes (128-byte aligned)
+  const int S = a.tma_stages, A = W;
+  const int TW = kFixed ? CTW : a.tile_w, TH = kFixed ? CTH : a.tile_h;
+  const int BW = kFixed ? CTW + 2 * W : a.tma_bw, BH = kFixed ? CTH + 2 : a.tma_bh;
+  const int bplane = BW * BH, bsz = ns * bplane;  // elements of one halo'd box (all species)
+  // elements between window boxes (box bytes rounded up to 128)
+  const int fst = kFixed ? (bsz * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T) : a.tma_box_bytes / (int)sizeof(T);
   const int oplane = TW * TH;
   const int gxn = a.tile_gx, ntiles = a.tile_gx * a.tile_gy;
   const int K = rank < ntiles ? (ntiles - rank + nblk - 1) / nblk : 0;
@@ -1222,7 +1229,7 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     const T* bb = (const T*)(base + off_b);
     const T* db = (const T*)(base + off_d);
     const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
-    const int tw = min(TW, nx - x0), th = min(TH, ny - y0);  // tw is a multiple of W
+    const int tw = kFixed ? TW : min(TW, nx - x0), th = kFixed ? TH : min(TH, ny - y0);  // tw: a multiple of W
     const int tv = tw / W;                                     // own vectors per row
     const bool edge = bc != 0 && (x0 == 0 || y0 == 0 || x0 + tw == nx || y0 + th == ny);
     // v_j = (x_j - sum h v) / s over the tile and its halo, in place in the source box: box rows 0..th+1,
@@ -1248,26 +1255,47 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
             v.e[u] = x * frs;
           }
         }
-        if (edge && (gy < 0 || gy >= ny || gxv < 0 || gxv + W > nx)) {
-          // periodic or reflected halo points outside the grid: the mapped point from global memory
-#pragma unroll
-          for (int u = 0; u < W; ++u) {
-            const int gx = gxv + u;
-            if (gx < x0 - 1 || gx > x0 + tw || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) continue;
-            const int mx = (int)bc_index(bc, gx, nx), my = (int)bc_index(bc, gy, ny);
-            const size_t r = (size_t)sp * npts + (uint32_t)my * nx + (uint32_t)mx;
-            T x = src[r];
-            if (pend) {
-              x = fma(-fh0, f0[r], x);
-              if (fnw > 1) x = fma(-fh1, f1[r], x);
-              if (fnw > 2) x = fma(-fh2, f2[r], x);
-              x = x * frs;
-            }
-            v.e[u] = x;
-          }
-        }
         st16(sb + bi, v);
         if (pend && own) stg16(vj + (size_t)sp * npts + (uint32_t)gy * nx + (uint32_t)gxv, v);
+      }
+    }
+    if (edge) {  // uniform over the block
+      // periodic or reflected grid, tile on its edge: the halo points outside the grid that the stencil
+      // reads (the row above / below the tile, the column left / right of it; no corners) from global
+      // memory at their mapped index, finalised, over the values the loop above derived from the copy's
+      // zero fill
+      __syncthreads();
+      if (ok) {
+        const int ntop = y0 == 0 ? tw : 0, nbot = y0 + th == ny ? tw : 0;
+        const int nlft = x0 == 0 ? th : 0, nrgt = x0 + tw == nx ? th : 0;
+        const int L = ntop + nbot + nlft + nrgt;
+        const T* src = pend ? raw + (size_t)((j_l - 1) & 1) * ldv : V + (size_t)(j_l - 1) * ldv;
+        const T* f0 = V + (size_t)(fbase - 1) * ldv;  // the finalisation window, consecutive columns
+        for (int e = tid; e < ns * L; e += kThreads) {
+          const int sp = e / L;
+          int q = e - sp * L, hy, hx;  // box row, box column (points)
+          if (q < ntop) {
+            hy = 0, hx = W + q;
+          } else if ((q -= ntop) < nbot) {
+            hy = th + 1, hx = W + q;
+          } else if ((q -= nbot) < nlft) {
+            hy = 1 + q, hx = W - 1;
+          } else {
+            q -= nlft;
+            hy = 1 + q, hx = W + tw;
+          }
+          const int gx = x0 - W + hx, gy = y0 - 1 + hy;
+          const int mx = (int)bc_index(bc, gx, nx), my = (int)bc_index(bc, gy, ny);
+          const size_t r = (size_t)sp * npts + (uint32_t)my * nx + (uint32_t)mx;
+          T x = src[r];
+          if (pend) {
+            x = fma(-fh0, f0[r], x);
+            if (fnw > 1) x = fma(-fh1, f0[r + ldv], x);
+            if (fnw > 2) x = fma(-fh2, f0[r + 2 * ldv], x);
+            x = x * frs;
+          }
+          sb[sp * bplane + hy * BW + hx] = x;
+        }
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -1327,11 +1355,12 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
 #pragma unroll
             for (int u = 0; u < W; ++u) out.e[u] = fma(ntr[t], bv.e[u], out.e[u]);
           }
-        for (int t = 4; t < p; ++t) {
-          const Vec16<T> bv = ld16(bb + (t * ns + sp) * oplane + pi);
+        if (CP < 0 || CP > 4)
+          for (int t = 4; t < p; ++t) {
+            const Vec16<T> bv = ld16(bb + (t * ns + sp) * oplane + pi);
 #pragma unroll
-          for (int u = 0; u < W; ++u) out.e[u] = fma(ntp[t], bv.e[u], out.e[u]);
-        }
+            for (int u = 0; u < W; ++u) out.e[u] = fma(ntp[t], bv.e[u], out.e[u]);
+          }
         stg16(xo + (size_t)sp * npts + (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + cv * W), out);
         {  // the step's dots
           Vec16<T> g;
@@ -1380,7 +1409,7 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
 
 // TMA: the kernel instantiation that contains the bulk-tensor-copy path (kept out of the other
 // instantiations, whose register allocation it would otherwise share).
-template <typename T, bool TMA>
+template <typename T, int TMA>
 __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0, int nwin, bool lead,
                                  T* V, size_t ldv, double* smem, DotAcc<T>& acc, bool prof_on) {
   const OpDesc& op = a.op;
@@ -1410,8 +1439,11 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
   const int nr = a.ring_n;
   const int ring_valid_from = nr > 0 ? max(c.ring_lo, j - nr + 1) : (1 << 30);
   const int ntiles = a.tile_gx * a.tile_gy;
-  if (TMA && ntiles > nblk && a.tma_on) {
-    if constexpr (TMA) fused_st2d_tma<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
+  if (TMA != 0 && ntiles > nblk && a.tma_on) {
+    if constexpr (TMA == kTmaFixed)  // 32 x 16 tiles, two species, p = 3 (grids of whole tiles)
+      fused_st2d_tma<T, 32, 16, 2, 3>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
+    else if constexpr (TMA != 0)
+      fused_st2d_tma<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
   } else if (ntiles > nblk) {
     fused_st2d_tiles<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
   } else {
@@ -1599,7 +1631,7 @@ __device__ void fused_prefetch(const SolveArgs& a, int rank, int jn, double* sme
 // ------------------------------------------------------------------------------------------------
 // The solver kernel.
 // ------------------------------------------------------------------------------------------------
-template <typename T, int KIND, class Team, bool TMA = false>
+template <typename T, int KIND, class Team, int TMA = 0>
 __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn);
 
 // Tensor maps of the TMA path, passed by value as a grid-constant kernel parameter (128 bytes each, 64-byte
@@ -1608,7 +1640,7 @@ struct TmaMaps {
   alignas(64) unsigned char m[4][128];
 };
 
-template <typename T, int KIND, bool GRID, bool TMA = false>
+template <typename T, int KIND, bool GRID, int TMA = 0>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) kiops_solve_kernel(const SolveArgs* __restrict__ all,
                                                                            const __grid_constant__ TmaMaps tmaps) {
   extern __shared__ double smem_dyn[];
@@ -1844,7 +1876,7 @@ __device__ void combine_rows(Ctl& c, const T* V, size_t ldv, int j, const double
   }
 }
 
-template <typename T, int KIND, class Team, bool TMA>
+template <typename T, int KIND, class Team, int TMA>
 __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_dyn) {
   const int tid = threadIdx.x;
   const int64_t N = a.N;
@@ -1913,7 +1945,7 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
                 a.df[(size_t)(sp * ns + q) * npts + pt] = (float)__ldg(a.op.diag[sp][q] + pt);
       }
     }
-    if (TMA && KIND == OP_ST2D && a.tma_on) {  // TMA path: B columns (FP64 basis) and coupling fields as staged
+    if (TMA != 0 && KIND == OP_ST2D && a.tma_on) {  // TMA path: B columns (FP64 basis) and coupling fields as staged
       if constexpr (sizeof(T) == 8) {
         double* tb = (double*)a.tma_b;
         for (int t = 0; t < p; ++t)

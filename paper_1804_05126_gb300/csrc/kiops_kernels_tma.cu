@@ -7,7 +7,7 @@ using namespace kiops_dev;
 
 namespace kiops_k {
 void* solve_kernel_tma(bool fp32) {
-  if (fp32) return (void*)kiops_solve_kernel<float, OP_ST2D, true, true>;
-  return (void*)kiops_solve_kernel<double, OP_ST2D, true, true>;
+  if (fp32) return (void*)kiops_solve_kernel<float, OP_ST2D, true, kTmaGeneral>;
+  return (void*)kiops_solve_kernel<double, OP_ST2D, true, kTmaGeneral>;
 }
 }  // namespace kiops_k

@@ -1,0 +1,11 @@
+// The grid-engine kernel for 2D stencils with the bulk-tensor-copy several-tiles path compiled for one
+// configuration: 32 x 16 tiles, two species, p = 3, FP32 basis (loop bounds, shared-memory offsets and the
+// B-block loop are constants).  Used for grids that are whole multiples of the tile.
+#include "kiops_device.cuh"
+#include "kiops_kernels.h"
+
+using namespace kiops_dev;
+
+namespace kiops_k {
+void* solve_kernel_tma_fixed() { return (void*)kiops_solve_kernel<float, OP_ST2D, true, kTmaFixed>; }
+}  // namespace kiops_k

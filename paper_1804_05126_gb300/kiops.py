@@ -36,14 +36,15 @@ class kiops_config(C.Structure):
                 ("grid_blocks", C.c_int), ("profile", C.c_int), ("fuse_stencil", C.c_int),
                 ("batch_team_blocks", C.c_int), ("fused_smem", C.c_int), ("scenario", C.c_int),
                 ("block_threads", C.c_int), ("tma", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int),
-                ("tma_stages", C.c_int), ("tma_prefetch", C.c_int)]
+                ("tma_stages", C.c_int), ("tma_prefetch", C.c_int), ("tma_fixed", C.c_int)]
 
 
 class kiops_stats(C.Structure):
     _fields_ = [("substeps", C.c_int64), ("rejected", C.c_int64), ("matvecs", C.c_int64),
                 ("iterations", C.c_int64), ("expm_calls", C.c_int64), ("m_last", C.c_int), ("engine", C.c_int),
                 ("grid_blocks", C.c_int), ("status", C.c_int), ("err_est", C.c_double),
-                ("phase_cycles", C.c_int64 * 16)]
+                ("phase_cycles", C.c_int64 * 16), ("tile_path", C.c_int), ("tile_w", C.c_int),
+                ("tile_h", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -476,7 +477,7 @@ class Solver:
                  timeout_s: float = 10.0, engine: int = ENGINE_AUTO, grid_blocks: int = 0, profile: bool = False,
                  fuse_stencil: bool = True, fused_smem: int = -1, scenario: int = 0, block_threads: int = 0,
                  tma: int = 1, tile: tuple[int, int] | None = None, tma_stages: int = 0,
-                 tma_prefetch: int = -1):
+                 tma_prefetch: int = -1, tma_fixed: int = 1):
         import torch
         self.device = torch.device("cuda", device)
         cfg = kiops_config_default()
@@ -493,6 +494,7 @@ class Solver:
         cfg.tile_w, cfg.tile_h = (int(tile[0]), int(tile[1])) if tile else (0, 0)
         cfg.tma_stages = int(tma_stages)
         cfg.tma_prefetch = int(tma_prefetch)
+        cfg.tma_fixed = int(tma_fixed)
         self.cfg = cfg
         self.ctx = kiops_create(cfg)
 

@@ -442,6 +442,32 @@ def test_tma_staged_several_tiles_path(make, m_o, tile, stages):
         assert rel(w, wu) <= P.tol
 
 
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("m_o", [2, 3])
+def test_tma_fixed_shape_kernel(bc, m_o):
+    """The staged several-tiles kernel compiled for 32 x 16 tiles, two species and p = 3 (FP32 basis, a grid
+    of whole tiles): a 192^2 two-species grid over 3 blocks (72 tiles, edge tiles on all four sides, whose
+    out-of-grid halo the edge pass fills) with each boundary treatment.  The statistics show which kernel
+    ran; against the general staged kernel (tma_fixed = 0): same per-element arithmetic and order, so the
+    same bits; against the per-element path (tma = 0) within tol and against the oracle within 10 tol."""
+    P = W.problem_gray_scott(n=192, seed=12, precision="fp32_basis", tol=1e-6, tau=1.0)
+    P.op = dict(P.op, bc=bc)
+    out = {}
+    for name, kw in (("fixed", {}), ("general", dict(tma_fixed=0)), ("element", dict(tma=0))):
+        s = kiops.Solver(device=0, grid_blocks=3, **kw)
+        out[name] = gpu_solve(s, P, m_o=m_o)
+        s.close()
+    (wf, sf), (wg, sg), (we, se) = out["fixed"], out["general"], out["element"]
+    assert (sf["tile_path"], sf["tile_w"], sf["tile_h"]) == (3, 32, 16)
+    assert (sg["tile_path"], sg["tile_w"], sg["tile_h"]) == (2, 32, 16)
+    assert se["tile_path"] == 1
+    assert sf["status"] == sg["status"] == se["status"] == 0
+    assert np.array_equal(wf, wg) and sf["matvecs"] == sg["matvecs"]
+    assert rel(wf, we) <= P.tol
+    w_ref, _, _ = oracle_solve(P, m_o=m_o)
+    assert rel(wf, w_ref) <= 10 * P.tol
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32_basis", 1e-6)])
 def test_2048_grid_several_tiles_vs_dst_closed_form(solver, precision, tol):
     """Full-size pin of the several-tiles path: 2048^2 Dirichlet diffusion + shift (N = 4.2 M, 4 or 2 tiles
