@@ -446,7 +446,7 @@ def measure_served_config5(dev, count=48):
                      "queueing; latency = completion - arrival")}
 
 
-STEP_PHASES = (2, 3, 4, 5, 11, 12, 13, 14)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
+STEP_PHASES = (2, 3, 4, 5, 11, 12, 13, 14, 15)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
 
 
 def measure_beyond_l2(dev):

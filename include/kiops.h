@@ -127,7 +127,8 @@ typedef struct {
    * and block reduction, 3 step cross-block sum, 4 step coefficients, 5 step normalise, 6 expm powers,
    * 7 expm Horner, 8 expm squarings, 9 control, 10 update, 11 grid barrier waits, 12 tiled path:
    * finalisation of v_j, 13 tiled path: A~ v_j and dots, 14 tiled path with bulk tensor copies: waits for a
-   * tile's copies; other entries 0. */
+   * tile's copies (and the issue of the next ones), 15 that path: the block barrier that ends a tile (waits
+   * for the block's last products); other entries 0. */
   int64_t phase_cycles[16];
   /* 2D stencils on the grid engine: how the Krylov step ran.  tile_path 0 = not tiled (or one tile per
    * block), 1 = several tiles per block with per-element loads, 2 = several tiles per block staged by bulk

@@ -275,7 +275,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // Tile shape, stages and shared-memory layout of the TMA path, if it applies and keeps `blocks` blocks
 // co-resident; the workspace grows by the tensor maps and the staged copies of B (FP64) and the fields.
-bool setup_tma(kiops_ctx* ctx, void* fn, int blocks, int threads, Prepared& P) {
+// fn: the general instantiation; fn_fixed (or null): the one compiled for 32 x 16 tiles, two species and
+// p = 3 (same stage layout).  On success *use_fixed tells which to launch.
+bool setup_tma(kiops_ctx* ctx, void* fn, void* fn_fixed, int blocks, int threads, Prepared& P, bool* use_fixed) {
   SolveArgs& a = P.args;
   // automatic (tma = 1): FP32 basis only.  FP64 steps are bound by the FP64 pipe, and the staged path measured
   // slower there (2048^2 ADR 190 -> 202 us per step, 1024^2 Gray-Scott 8.9 -> 11.9 ms per solve)
@@ -302,7 +304,13 @@ bool setup_tma(kiops_ctx* ctx, void* fn, int blocks, int threads, Prepared& P) {
   std::vector<std::pair<int, int>> cand;
   if (ctx->cfg.tile_w > 0 && ctx->cfg.tile_h > 0) cand.push_back({ctx->cfg.tile_w, ctx->cfg.tile_h});
   for (auto& sh : auto_shapes) cand.push_back({sh[0], sh[1]});
-  for (auto [tw, th] : cand) {
+  for (auto [tw, th] : cand)
+  for (int variant = 0; variant < 2; ++variant) {  // the fixed-shape kernel first, where it applies
+    const bool fixed = variant == 0;
+    if (fixed && !(fn_fixed && es == 4 && tw == 32 && th == 16 && ns == 2 && p == 3 && nx % 32 == 0 && ny % 16 == 0))
+      continue;
+    void* f = fixed ? fn_fixed : fn;
+    const int Sv = S;
     if (tw < 4 || tw % 4 != 0 || th < 1 || tw > 248 || th > 254) continue;
     const int bw = tw + 2 * pad, bh = th + 2;
     const int64_t gx = (nx + tw - 1) / tw, gy = (ny + th - 1) / th;
@@ -311,15 +319,17 @@ bool setup_tma(kiops_ctx* ctx, void* fn, int blocks, int threads, Prepared& P) {
     const size_t off_f = box, off_b = off_f + (size_t)a.m_o * box;
     const size_t off_d = off_b + up((size_t)p * ns * tw * th * es);
     const size_t stage = up(off_d + up((size_t)nf * tw * th * es));
-    const size_t bar_off = std::max((size_t)S * stage, up(kDynSmem));
-    const size_t dyn = bar_off + 64 + 128;  // barriers, alignment slack
+    const size_t bar_off = std::max((size_t)Sv * stage, up(kDynSmem));
+    const size_t side_off = bar_off + 64;                       // after the stage barriers (<= 6)
+    const size_t dyn = side_off + (size_t)threads * 4 * es + 128;  // landing slots, alignment slack
     if (dyn > (size_t)optin) continue;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) continue;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) continue;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess) continue;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, dyn) != cudaSuccess) continue;
     if ((int64_t)per_sm * ctx->sms < blocks) continue;
+    *use_fixed = fixed;
     a.tma_on = 1;
-    a.tma_stages = S;
+    a.tma_stages = Sv;
     // L2 prefetch ahead of the staged copies: off unless asked for (2048^2 Gray-Scott FP32: 117 us per step
     // without, 122 us with 2 tiles beyond the stages)
     a.tma_prefetch = ctx->cfg.tma_prefetch < 0 ? 0 : std::min(ctx->cfg.tma_prefetch, 64);
@@ -335,6 +345,7 @@ bool setup_tma(kiops_ctx* ctx, void* fn, int blocks, int threads, Prepared& P) {
     a.tma_off_b = (int)off_b;
     a.tma_off_d = (int)off_d;
     a.tma_bar_off = (int)bar_off;
+    a.tma_side_off = (int)side_off;
     a.tile_w = tw;
     a.tile_h = th;
     a.tile_gx = (int)gx;
@@ -610,21 +621,13 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
     }
   }
   void* fn_tma = (A->d.kind == OP_ST2D && threads == kThreads) ? kiops_k::solve_kernel_tma(fp32) : nullptr;
+  // the instantiation compiled for 32 x 16 tiles, two species and p = 3 (FP32 basis, grid of whole tiles)
+  void* fn_fixed = fn_tma && fp32 && ctx->cfg.tma_fixed != 0 ? kiops_k::solve_kernel_tma_fixed() : nullptr;
+  bool use_fixed = false;
   if (engine == KIOPS_ENGINE_GRID && fn_tma && prepare_kernel(ctx, fn_tma) == KIOPS_OK &&
-      setup_tma(ctx, fn_tma, blocks, threads, P)) {
-    fn = fn_tma;  // the instantiation with the bulk-tensor-copy path
-    // the instantiation compiled for 32 x 16 tiles, two species and p = 3, on a grid of whole tiles
-    const SolveArgs& sa = P.args;
-    if (fp32 && ctx->cfg.tma_fixed != 0 && sa.tile_w == 32 && sa.tile_h == 16 && sa.op.nspecies == 2 && sa.p == 3 &&
-        sa.op.nx % 32 == 0 && sa.op.ny % 16 == 0) {
-      void* fx = kiops_k::solve_kernel_tma_fixed();
-      int per_sm = 0;
-      if (cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.dyn_smem) == cudaSuccess &&
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fx, threads, P.dyn_smem) == cudaSuccess &&
-          (int64_t)per_sm * ctx->sms >= blocks)
-        fn = fx;
-      cudaGetLastError();
-    }
+      (!fn_fixed || prepare_kernel(ctx, fn_fixed) == KIOPS_OK) &&
+      setup_tma(ctx, fn_tma, fn_fixed, blocks, threads, P, &use_fixed)) {
+    fn = use_fixed ? fn_fixed : fn_tma;  // an instantiation with the bulk-tensor-copy path
   } else if (engine == KIOPS_ENGINE_GRID)
     enable_fused_smem(ctx, fn, blocks, P, threads);
   st = ensure_workspace(ctx, P.L.total);

@@ -164,6 +164,7 @@ struct SolveArgs {
   int tma_nf;                // coupling-field planes staged per tile
   int tma_fidx[2][2];        // plane of the coupling field (s, q) among the staged ones, -1 if none
   int tma_stage_bytes, tma_box_bytes, tma_off_f, tma_off_b, tma_off_d, tma_bar_off;
+  int tma_side_off;          // kThreads x 4 elements: per-thread landing slots of an edge tile's wrapped halo
   const void* tmaps;         // the kernel parameter's tensor maps (basis, raw ring, B columns, coupling fields)
   void* tma_b;               // B columns b_{p-t} at t * ldv in the basis precision (FP32: bf; FP64: a copy)
   void* tma_f;               // coupling fields in the basis precision, tma_nf planes of nx * ny points
@@ -1171,6 +1172,7 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
   // stages and barriers from the first 128-byte aligned shared address (the launch reserves the slack)
   char* sm = (char*)smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
   uint64_t* bars = (uint64_t*)(sm + a.tma_bar_off);
+  char* sm_side = sm + a.tma_side_off;
   const char* maps = (const char*)a.tmaps;  // 128 bytes each: basis, raw ring, B columns, fields
   const int tma_nf = a.tma_nf, off_f = a.tma_off_f, off_b = a.tma_off_b, off_d = a.tma_off_d;
   const int stage_bytes = a.tma_stage_bytes;
@@ -1222,16 +1224,56 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
     const unsigned par = ((q0 + (unsigned)k) / (unsigned)S) & 1u;
     char* base = sm + (size_t)st * stage_bytes;
+    const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
+    const int tw = kFixed ? TW : min(TW, nx - x0), th = kFixed ? TH : min(TH, ny - y0);  // tw: a multiple of W
+    const int tv = tw / W;                                     // own vectors per row
+    const bool edge = bc != 0 && (x0 == 0 || y0 == 0 || x0 + tw == nx || y0 + th == ny);
+    // Edge tile of a periodic or reflected grid: the halo points outside the grid that the stencil reads
+    // (the row above / below the tile, the column left / right of it; no corners), point e of
+    // ns * L in species-major order.  Their values are those at the mapped index: inside this box
+    // (reflection: one or two points inside the edge) or elsewhere in the grid (periodic wrap).
+    const int ntop = y0 == 0 ? tw : 0, nbot = y0 + th == ny ? tw : 0;
+    const int nlft = x0 == 0 ? th : 0, nrgt = x0 + tw == nx ? th : 0;
+    const int L = edge ? ntop + nbot + nlft + nrgt : 0;
+    // point e: species, box row, box column (points), and the mapped point's row-major offset in a plane and
+    // box coordinates
+    auto halo_point = [&](int e, int& sp, int& hy, int& hx, size_t& r, int& mbx, int& mby) {
+      sp = e / L;
+      int q = e - sp * L;
+      if (q < ntop) {
+        hy = 0, hx = W + q;
+      } else if ((q -= ntop) < nbot) {
+        hy = th + 1, hx = W + q;
+      } else if ((q -= nbot) < nlft) {
+        hy = 1 + q, hx = W - 1;
+      } else {
+        q -= nlft;
+        hy = 1 + q, hx = W + tw;
+      }
+      const int mx = (int)bc_index(bc, x0 - W + hx, nx), my = (int)bc_index(bc, y0 - 1 + hy, ny);
+      r = (size_t)sp * npts + (uint32_t)my * nx + (uint32_t)mx;
+      mbx = mx - (x0 - W), mby = my - (y0 - 1);
+    };
+    auto in_box = [&](int mbx, int mby) { return mbx >= 0 && mbx < tw + 2 * W && mby >= 0 && mby < th + 2; };
+    T* side = (T*)(sm_side) + tid * 4;  // this thread's landing slots: x_j (or v_j), then the window
+    if (edge && tid < ns * L) {
+      // the first point of this thread lying outside the box: its sources copied into the landing slots
+      // now, so that the global-memory latency overlaps the wait for the tile and its finalisation
+      int sp, hy, hx, mbx, mby;
+      size_t r;
+      halo_point(tid, sp, hy, hx, r, mbx, mby);
+      if (!in_box(mbx, mby)) {
+        cp_async_elem(side, (pend ? raw + (size_t)((j_l - 1) & 1) * ldv : V + (size_t)(j_l - 1) * ldv) + r);
+        const T* f0 = V + (size_t)(fbase - 1) * ldv + r;
+        for (int u = 0; u < fnw; ++u) cp_async_elem(side + 1 + u, f0 + (size_t)u * ldv);
+      }
+    }
     const bool ok = mbar_wait(bars + st, par, timeout_ns);
     KIOPS_TICK(14);
     T* sb = (T*)base;
     const T* fb = (const T*)(base + off_f);
     const T* bb = (const T*)(base + off_b);
     const T* db = (const T*)(base + off_d);
-    const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
-    const int tw = kFixed ? TW : min(TW, nx - x0), th = kFixed ? TH : min(TH, ny - y0);  // tw: a multiple of W
-    const int tv = tw / W;                                     // own vectors per row
-    const bool edge = bc != 0 && (x0 == 0 || y0 == 0 || x0 + tw == nx || y0 + th == ny);
     // v_j = (x_j - sum h v) / s over the tile and its halo, in place in the source box: box rows 0..th+1,
     // vectors 0..tv+1 of each row (box vector c covers the points x0 - W + c W ...)
     if (ok) {
@@ -1260,39 +1302,30 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
       }
     }
     if (edge) {  // uniform over the block
-      // periodic or reflected grid, tile on its edge: the halo points outside the grid that the stencil
-      // reads (the row above / below the tile, the column left / right of it; no corners) from global
-      // memory at their mapped index, finalised, over the values the loop above derived from the copy's
-      // zero fill
+      // the halo points outside the grid, finalised, over the values the loop above derived from the
+      // copy's zero fill: from this box where the mapped point lies in it (finalised above), else from the
+      // landing slots (a thread's first point) or global memory
+      cp_async_wait_all();
       __syncthreads();
       if (ok) {
-        const int ntop = y0 == 0 ? tw : 0, nbot = y0 + th == ny ? tw : 0;
-        const int nlft = x0 == 0 ? th : 0, nrgt = x0 + tw == nx ? th : 0;
-        const int L = ntop + nbot + nlft + nrgt;
         const T* src = pend ? raw + (size_t)((j_l - 1) & 1) * ldv : V + (size_t)(j_l - 1) * ldv;
         const T* f0 = V + (size_t)(fbase - 1) * ldv;  // the finalisation window, consecutive columns
         for (int e = tid; e < ns * L; e += kThreads) {
-          const int sp = e / L;
-          int q = e - sp * L, hy, hx;  // box row, box column (points)
-          if (q < ntop) {
-            hy = 0, hx = W + q;
-          } else if ((q -= ntop) < nbot) {
-            hy = th + 1, hx = W + q;
-          } else if ((q -= nbot) < nlft) {
-            hy = 1 + q, hx = W - 1;
+          int sp, hy, hx, mbx, mby;
+          size_t r;
+          halo_point(e, sp, hy, hx, r, mbx, mby);
+          T x;
+          if (in_box(mbx, mby)) {
+            x = sb[sp * bplane + mby * BW + mbx];
           } else {
-            q -= nlft;
-            hy = 1 + q, hx = W + tw;
-          }
-          const int gx = x0 - W + hx, gy = y0 - 1 + hy;
-          const int mx = (int)bc_index(bc, gx, nx), my = (int)bc_index(bc, gy, ny);
-          const size_t r = (size_t)sp * npts + (uint32_t)my * nx + (uint32_t)mx;
-          T x = src[r];
-          if (pend) {
-            x = fma(-fh0, f0[r], x);
-            if (fnw > 1) x = fma(-fh1, f0[r + ldv], x);
-            if (fnw > 2) x = fma(-fh2, f0[r + 2 * ldv], x);
-            x = x * frs;
+            const bool landed = e == tid;
+            x = landed ? side[0] : src[r];
+            if (pend) {
+              x = fma(-fh0, landed ? side[1] : f0[r], x);
+              if (fnw > 1) x = fma(-fh1, landed ? side[2] : f0[r + ldv], x);
+              if (fnw > 2) x = fma(-fh2, landed ? side[3] : f0[r + 2 * ldv], x);
+              x = x * frs;
+            }
           }
           sb[sp * bplane + hy * BW + hx] = x;
         }
@@ -1395,6 +1428,7 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     KIOPS_TICK(13);
     fence_proxy_async_smem();  // this stage's shared-memory accesses come before the next copies into it
     __syncthreads();
+    KIOPS_TICK(15);
     if (tid == 0 && k + S < K) issue(k + S);
   }
   // copies issued but not consumed (only after a copy timed out): wait for them, bounded, before the
