@@ -107,9 +107,9 @@ typedef struct {
   int tma_prefetch;        /* that path's L2 lookahead: tiles fetched into L2 (bulk prefetch, no shared memory)
                               this many tiles before their shared-memory copy is issued; 0 = none, -1 (default)
                               = automatic (none: measured slower with it) */
-  int tma_fixed;           /* that path with an FP32 basis, 32 x 16 tiles, two species and p = 3 on a grid of
-                              whole tiles: 1 (default) = run the kernel compiled for exactly that configuration
-                              (constant loop bounds and offsets), 0 = the general one */
+  int tma_fixed;           /* that path with an FP32 basis, 32 x 16 tiles, two species and p = 3: 1 (default) =
+                              run the kernel compiled for exactly that configuration (constant loop bounds and
+                              offsets), 0 = the general one */
 } kiops_config;
 
 typedef struct {

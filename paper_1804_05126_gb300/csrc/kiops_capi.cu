@@ -307,7 +307,7 @@ bool setup_tma(kiops_ctx* ctx, void* fn, void* fn_fixed, int blocks, int threads
   for (auto [tw, th] : cand)
   for (int variant = 0; variant < 2; ++variant) {  // the fixed-shape kernel first, where it applies
     const bool fixed = variant == 0;
-    if (fixed && !(fn_fixed && es == 4 && tw == 32 && th == 16 && ns == 2 && p == 3 && nx % 32 == 0 && ny % 16 == 0))
+    if (fixed && !(fn_fixed && es == 4 && tw == 32 && th == 16 && ns == 2 && p == 3))
       continue;
     void* f = fixed ? fn_fixed : fn;
     const int Sv = S;
@@ -621,7 +621,7 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
     }
   }
   void* fn_tma = (A->d.kind == OP_ST2D && threads == kThreads) ? kiops_k::solve_kernel_tma(fp32) : nullptr;
-  // the instantiation compiled for 32 x 16 tiles, two species and p = 3 (FP32 basis, grid of whole tiles)
+  // the instantiation compiled for 32 x 16 tiles, two species and p = 3 (FP32 basis)
   void* fn_fixed = fn_tma && fp32 && ctx->cfg.tma_fixed != 0 ? kiops_k::solve_kernel_tma_fixed() : nullptr;
   bool use_fixed = false;
   if (engine == KIOPS_ENGINE_GRID && fn_tma && prepare_kernel(ctx, fn_tma) == KIOPS_OK &&

@@ -33,7 +33,7 @@ namespace KIOPS_DEV_NS {
 constexpr int kThreads = KIOPS_THREADS;  // threads per block (256 or 512)
 constexpr int kWarps = kThreads / 32;
 // Kernel variants of the 2D several-tiles path with bulk tensor copies: none, any tile shape / species
-// count / p, or compiled for 32 x 16 tiles, two species and p = 3 (grids that are whole multiples of it).
+// count / p, or compiled for 32 x 16 tiles, two species and p = 3.
 constexpr int kTmaNone = 0, kTmaGeneral = 1, kTmaFixed = 2;
 // blocks per SM the register budget is sized for (two of 256 threads or one of 512: 128 registers a thread)
 constexpr int kMinBlocks = kThreads <= 256 ? 2 : 1;
@@ -1109,14 +1109,16 @@ __device__ __forceinline__ void stg16(double* p, const Vec16<double>& v) {
 //   own-point boxes: the B columns and the coupling fields.
 // Points outside the grid arrive as zeros from the copy, which is the Dirichlet value; for periodic and
 // reflected boundaries the halo points the stencil reads there (one row above or below the tile, one column
-// left or right of it) are finalised from global memory at their mapped index, in a separate pass over the
-// edge tiles only (so that the main loops carry no boundary test).
+// left or right of it) take the finalised value at their mapped index in a separate pass over the edge tiles
+// only (so that the main loops carry no boundary test): from the tile's own box where the mapped point lies
+// in it, else from per-thread slots that cp.async copies fill before the tile's wait.
 // The loops take 16 bytes of consecutive points per item (tile widths are multiples of that): 128-bit
 // shared-memory loads and global stores, coefficients and B-block weights held in registers.  Per element
 // the arithmetic and its order are those of fused_st2d_tiles; the elements are accumulated in another order.
-// CTW, CTH, CNS, CP > 0 (CP >= 0) fix the tile shape, the species count and p at compile time (an
-// instantiation for grids that are whole multiples of the tile): the loop bounds, the shared-memory offsets
-// and the B-block loop are then constants.  0 (CP = -1): taken from the arguments.
+// CTW, CTH, CNS, CP > 0 (CP >= 0) fix the tile shape, the species count and p at compile time (a kernel
+// instantiation of its own): the loop bounds, the shared-memory offsets and the B-block loop are then
+// constants, and a ragged tile at the grid's right or bottom edge runs the whole box with the points beyond
+// the grid left out of the stores and the dots.  0 (CP = -1): taken from the arguments.
 template <typename T, int CTW = 0, int CTH = 0, int CNS = 0, int CP = -1>
 __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0,
                                                int nwin, T* V, size_t ldv, double* smem, DotAcc<T>& acc,
@@ -1225,8 +1227,11 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     const unsigned par = ((q0 + (unsigned)k) / (unsigned)S) & 1u;
     char* base = sm + (size_t)st * stage_bytes;
     const int x0 = (tile % gxn) * TW, y0 = (tile / gxn) * TH;
-    const int tw = kFixed ? TW : min(TW, nx - x0), th = kFixed ? TH : min(TH, ny - y0);  // tw: a multiple of W
-    const int tv = tw / W;                                     // own vectors per row
+    const int tw = min(TW, nx - x0), th = min(TH, ny - y0);  // the tile's extent in the grid (tw: a multiple of W)
+    const int tv = tw / W;                                   // own vectors per row
+    // the loops' extent: with a fixed shape always the whole box, also on a ragged tile at the grid's right or
+    // bottom edge, whose points beyond the grid are the copy's zero fill (computed, never stored or summed)
+    const int tvl = kFixed ? TW / W : tv, thl = kFixed ? TH : th;
     const bool edge = bc != 0 && (x0 == 0 || y0 == 0 || x0 + tw == nx || y0 + th == ny);
     // Edge tile of a periodic or reflected grid: the halo points outside the grid that the stencil reads
     // (the row above / below the tile, the column left / right of it; no corners), point e of
@@ -1277,13 +1282,13 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     // v_j = (x_j - sum h v) / s over the tile and its halo, in place in the source box: box rows 0..th+1,
     // vectors 0..tv+1 of each row (box vector c covers the points x0 - W + c W ...)
     if (ok) {
-      const int rv = tv + 2, tot = ns * (th + 2) * rv;
-      TileWalk wk(tid, rv, th + 2);
+      const int rv = tvl + 2, tot = ns * (thl + 2) * rv;
+      TileWalk wk(tid, rv, thl + 2);
       for (int e = tid; e < tot; e += kThreads, wk.next()) {
         const int sp = wk.s, hy = wk.y, cv = wk.x;
         const int bi = sp * bplane + hy * BW + cv * W;
         const int gy = y0 - 1 + hy, gxv = x0 - W + cv * W;
-        const bool own = hy >= 1 && hy <= th && cv >= 1 && cv <= tv;
+        const bool own = hy >= 1 && hy <= th && cv >= 1 && cv <= tv;  // in the grid: the tile's actual extent
         Vec16<T> v = ld16(sb + bi);
         if (pend) {
           Vec16<T> g0 = ld16(fb + bi), g1, g2;
@@ -1340,10 +1345,11 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
     KIOPS_TICK(12);
     // A~ v_j on the tile's own points and the step's dots, every operand from the stage
     {
-      const int tot = ns * th * tv;
-      TileWalk wk(tid, tv, th);
+      const int tot = ns * thl * tvl;
+      TileWalk wk(tid, tvl, thl);
       for (int e = tid; e < tot; e += kThreads, wk.next()) {
         const int sp = wk.s, ly = wk.y, cv = wk.x;
+        if (kFixed && (ly >= th || cv >= tv)) continue;  // beyond the grid (ragged tile)
         const int bi = sp * bplane + (ly + 1) * BW + W + cv * W;
         const int pi = ly * TW + cv * W;
         const int fo = sp ? fo_s[1] : fo_s[0], ft = sp ? ft_s[1] : ft_s[0];
@@ -1474,7 +1480,7 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
   const int ring_valid_from = nr > 0 ? max(c.ring_lo, j - nr + 1) : (1 << 30);
   const int ntiles = a.tile_gx * a.tile_gy;
   if (TMA != 0 && ntiles > nblk && a.tma_on) {
-    if constexpr (TMA == kTmaFixed)  // 32 x 16 tiles, two species, p = 3 (grids of whole tiles)
+    if constexpr (TMA == kTmaFixed)  // 32 x 16 tiles, two species, p = 3
       fused_st2d_tma<T, 32, 16, 2, 3>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);
     else if constexpr (TMA != 0)
       fused_st2d_tma<T>(a, c, rank, nblk, j, i0, nwin, V, ldv, smem, acc, prof_on);

@@ -1,6 +1,6 @@
 // The grid-engine kernel for 2D stencils with the bulk-tensor-copy several-tiles path compiled for one
 // configuration: 32 x 16 tiles, two species, p = 3, FP32 basis (loop bounds, shared-memory offsets and the
-// B-block loop are constants).  Used for grids that are whole multiples of the tile.
+// B-block loop are constants; ragged edge tiles run the whole box and mask what lies beyond the grid).
 #include "kiops_device.cuh"
 #include "kiops_kernels.h"
 
