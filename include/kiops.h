@@ -74,7 +74,9 @@ typedef struct {
   int grid_blocks;         /* grid engine block count; 0 = as many as are co-resident */
   int profile;             /* 1: fill kiops_stats.phase_cycles (device cycle counters, rank-0 view) */
   int fuse_stencil;        /* 1 (default): 2D stencils on the grid engine normalise v_{j+1} inside the next
-                              step's tiles (one grid barrier per Krylov step); 0: separate normalise pass */
+                              step's tiles (one grid barrier per Krylov step), and so do 3D stencils with an
+                              FP32 basis on grids with more 3D tiles than blocks (tma > 0); 0: separate
+                              normalise pass */
   int batch_team_blocks;   /* kiops_solve_batch: blocks per team (0 = automatic, 1 = one block per request) */
   int fused_smem;          /* tiled 2D path: shared-memory extras, a bitmask of 1 = the finalised tiles of the
                               last m_o + 1 basis vectors, 2 = the next raw tile prefetched (cp.async) during
@@ -132,8 +134,9 @@ typedef struct {
   int64_t phase_cycles[16];
   /* 2D stencils on the grid engine: how the Krylov step ran.  tile_path 0 = not tiled (or one tile per
    * block), 1 = several tiles per block with per-element loads, 2 = several tiles per block staged by bulk
-   * tensor copies, 3 = as 2 with the kernel compiled for 32 x 16 tiles, two species and p = 3; tile_w,
-   * tile_h = the tile shape of paths 1 to 3 (0 otherwise). */
+   * tensor copies, 3 = as 2 with the kernel compiled for 32 x 16 tiles, two species and p = 3; 3D stencils
+   * with an FP32 basis: 4 = 3D tiles staged by bulk tensor copies with lagged normalisation (no separate
+   * normalise pass); tile_w, tile_h = the tile's x and y extent for paths 1 to 4 (0 otherwise). */
   int tile_path, tile_w, tile_h;
 } kiops_stats;
 

@@ -362,10 +362,117 @@ bool setup_tma(kiops_ctx* ctx, void* fn, void* fn_fixed, int blocks, int threads
   return false;
 }
 
+// 3D stencils with an FP32 basis: lagged normalisation on 3D tiles whose operands are staged by bulk tensor
+// copies (fused_st3d_tma).  Stage: halo'd boxes of raw x_j and of the m_o window vectors, (tile_w + 8) x
+// (tile_h + 2) x (tile_d + 2) points each, and the own-point box of the reaction field if the operator has one;
+// the B columns go through per-thread slots (cp.async).  Candidate tiles give each thread one 16-byte item of own
+// points; the first whose stages fit at the launch's block count is taken.  Needs more tiles than blocks and
+// rows of a multiple of 16 bytes.
+// fn_fixed (or null): the instantiation compiled for 32 x 8 x 4 tiles; *use_fixed tells which to launch.
+bool setup_tma3d(kiops_ctx* ctx, void* fn, void* fn_fixed, int blocks, int threads, Prepared& P, bool* use_fixed) {
+  SolveArgs& a = P.args;
+  if (ctx->cfg.tma <= 0 || !ctx->cfg.fuse_stencil || a.op.kind != OP_ST3D || !a.prec || a.m_o > kChunk) return false;
+  const int64_t nx = a.op.nx, ny = a.op.ny, nz = a.op.nz;
+  if (nx % 4 != 0 || nx * ny * nz >= ((int64_t)1 << 31) || !tensor_map_encoder()) return false;
+  const bool hasf = a.op.diag[0][0] != nullptr;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device) != cudaSuccess) return false;
+  const int S = ctx->cfg.tma_stages >= 3 && ctx->cfg.tma_stages <= 6 ? ctx->cfg.tma_stages : 2;
+  auto up = [](size_t x) { return (x + 127) & ~(size_t)127; };
+  const int shapes[][3] = {{32, 8, 4}, {64, 4, 4}, {16, 8, 8}, {32, 4, 8}};
+  for (auto& sh : shapes)
+  for (int variant = 0; variant < 2; ++variant) {  // the fixed-shape kernel first, where it applies
+    const int tw = sh[0], th = sh[1], td = sh[2];
+    const bool fixed = variant == 0;
+    if (fixed && !(fn_fixed && tw == 32 && th == 8 && td == 4)) continue;
+    void* f = fixed ? fn_fixed : fn;
+    const int64_t gx = (nx + tw - 1) / tw, gy = (ny + th - 1) / th, gz = (nz + td - 1) / td;
+    if (gx * gy * gz <= blocks || gx * gy * gz > INT32_MAX) continue;
+    const int bw = tw + 8, bh = th + 2, bd = td + 2;
+    const size_t box = up((size_t)bw * bh * bd * 4);
+    const size_t off_f = box, off_d = off_f + (size_t)a.m_o * box;
+    const size_t stage = up(off_d + (hasf ? (size_t)tw * th * td * 4 : 0));
+    const size_t bar_off = std::max((size_t)S * stage, up(kDynSmem));
+    const size_t side_off = bar_off + 64;                      // per-thread B slots: four 16-byte vectors
+    const size_t dyn = side_off + (size_t)threads * 64 + 128;  // alignment slack
+    if (dyn > (size_t)optin) continue;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) continue;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, dyn) != cudaSuccess) continue;
+    if ((int64_t)per_sm * ctx->sms < blocks) continue;
+    *use_fixed = fixed;
+    a.fused = 1;
+    a.tma_on = 1;
+    a.tma_stages = S;
+    a.tma_prefetch = 0;
+    a.tma_pad = 4;
+    a.tma_bw = bw;
+    a.tma_bh = bh;
+    a.tma_bd = bd;
+    a.tma_nf = hasf ? 1 : 0;
+    a.tma_stage_bytes = (int)stage;
+    a.tma_box_bytes = (int)box;
+    a.tma_off_f = (int)off_f;
+    a.tma_off_b = (int)off_d;
+    a.tma_off_d = (int)off_d;
+    a.tma_bar_off = (int)bar_off;
+    a.tma_side_off = (int)side_off;
+    a.tile_w = tw;
+    a.tile_h = th;
+    a.tile_d = td;
+    a.tile_gx = (int)gx;
+    a.tile_gy = (int)gy;
+    a.tile_gz = (int)gz;
+    P.dyn_smem = dyn;
+    return true;
+  }
+  cudaGetLastError();
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+  return false;
+}
+
 // The four tensor maps of the TMA path (basis, raw ring, B columns, coupling fields) for the bound
 // workspace, into P.maps (passed to the kernel as a grid-constant parameter).
+// Tensor maps of the 3D staged path (FP32 basis): the basis and the raw ring as 4D {nx, ny, nz, column} with
+// halo'd boxes, the reaction field (its FP32 copy) as 3D with own-point boxes.
+kiops_status encode_tma_maps_3d(kiops_ctx* ctx, Prepared& P) {
+  SolveArgs& a = P.args;
+  std::memset(&P.maps, 0, sizeof(P.maps));
+  CUtensorMap* m = (CUtensorMap*)P.maps.m;
+  auto enc = tensor_map_encoder();
+  const cuuint64_t nx = (cuuint64_t)a.op.nx, ny = (cuuint64_t)a.op.ny, nz = (cuuint64_t)a.op.nz, es = 4;
+  const cuuint32_t one[4] = {1, 1, 1, 1};
+  auto check = [&](CUresult r, const char* what) -> kiops_status {
+    if (r != CUDA_SUCCESS) return fail(ctx, KIOPS_ECUDA, "tensor map of the %s: error %d", what, (int)r);
+    return KIOPS_OK;
+  };
+  const cuuint64_t st[3] = {nx * es, nx * ny * es, (cuuint64_t)a.ldv * es};
+  const cuuint32_t box[4] = {(cuuint32_t)a.tma_bw, (cuuint32_t)a.tma_bh, (cuuint32_t)a.tma_bd, 1};
+  const cuuint64_t dv[4] = {nx, ny, nz, (cuuint64_t)a.m_max + 1};
+  kiops_status r = check(enc(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.V, dv, st, box, one,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE), "basis");
+  if (r) return r;
+  const cuuint64_t dr[4] = {nx, ny, nz, 2};
+  r = check(enc(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.raw, dr, st, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE),
+            "raw vectors");
+  if (r) return r;
+  if (a.tma_nf > 0) {
+    const cuuint64_t sf[2] = {nx * es, nx * ny * es};
+    const cuuint32_t bf[3] = {(cuuint32_t)a.tile_w, (cuuint32_t)a.tile_h, (cuuint32_t)a.tile_d};
+    const cuuint64_t df[3] = {nx, ny, nz};
+    r = check(enc(&m[3], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.df, df, sf, bf, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE),
+              "reaction field");
+    if (r) return r;
+  }
+  return KIOPS_OK;
+}
+
 kiops_status encode_tma_maps(kiops_ctx* ctx, Prepared& P) {
   SolveArgs& a = P.args;
+  if (a.op.kind == OP_ST3D) return encode_tma_maps_3d(ctx, P);
   a.tma_b = a.prec ? (void*)a.bf : (void*)(P.base + P.tma_b);
   a.tma_f = P.base + P.tma_f;
   std::memset(&P.maps, 0, sizeof(P.maps));
@@ -628,6 +735,13 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
       (!fn_fixed || prepare_kernel(ctx, fn_fixed) == KIOPS_OK) &&
       setup_tma(ctx, fn_tma, fn_fixed, blocks, threads, P, &use_fixed)) {
     fn = use_fixed ? fn_fixed : fn_tma;  // an instantiation with the bulk-tensor-copy path
+  } else if (void* fn3 = (engine == KIOPS_ENGINE_GRID && A->d.kind == OP_ST3D && fp32 && threads == kThreads)
+                             ? kiops_k::solve_kernel_tma3d() : nullptr;
+             fn3 && prepare_kernel(ctx, fn3) == KIOPS_OK &&
+             (ctx->cfg.tma_fixed == 0 || prepare_kernel(ctx, kiops_k::solve_kernel_tma3d_fixed()) == KIOPS_OK) &&
+             setup_tma3d(ctx, fn3, ctx->cfg.tma_fixed != 0 ? kiops_k::solve_kernel_tma3d_fixed() : nullptr, blocks,
+                         threads, P, &use_fixed)) {
+    fn = use_fixed ? kiops_k::solve_kernel_tma3d_fixed() : fn3;  // 3D tiles staged by bulk tensor copies
   } else if (engine == KIOPS_ENGINE_GRID)
     enable_fused_smem(ctx, fn, blocks, P, threads);
   st = ensure_workspace(ctx, P.L.total);
@@ -683,7 +797,11 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   const double* hsd = (const double*)(hs + 10);
   fill_stats(stats, hs, hsd, engine, blocks);
   if (stats && ctx->cfg.profile) std::memcpy(stats->phase_cycles, hprof, 16 * 8);
-  if (stats && P.args.fused && (int64_t)P.args.tile_gx * P.args.tile_gy > blocks) {
+  if (stats && P.args.fused && P.args.op.kind == OP_ST3D) {
+    stats->tile_path = 4;  // 3D tiles staged by bulk tensor copies
+    stats->tile_w = P.args.tile_w;
+    stats->tile_h = P.args.tile_h;
+  } else if (stats && P.args.fused && (int64_t)P.args.tile_gx * P.args.tile_gy > blocks) {
     stats->tile_path = !P.args.tma_on ? 1 : (fn == fn_tma ? 2 : 3);
     stats->tile_w = P.args.tile_w;
     stats->tile_h = P.args.tile_h;

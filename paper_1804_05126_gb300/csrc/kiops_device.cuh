@@ -165,6 +165,7 @@ struct SolveArgs {
   int tma_fidx[2][2];        // plane of the coupling field (s, q) among the staged ones, -1 if none
   int tma_stage_bytes, tma_box_bytes, tma_off_f, tma_off_b, tma_off_d, tma_bar_off;
   int tma_side_off;          // kThreads x 4 elements: per-thread landing slots of an edge tile's wrapped halo
+  int tile_d, tile_gz, tma_bd;  // 3D stencils: tile depth, tiles along z, box depth (tile_d + 2)
   const void* tmaps;         // the kernel parameter's tensor maps (basis, raw ring, B columns, coupling fields)
   void* tma_b;               // B columns b_{p-t} at t * ldv in the basis precision (FP32: bf; FP64: a copy)
   void* tma_f;               // coupling fields in the basis precision, tma_nf planes of nx * ny points
@@ -637,6 +638,11 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Asynchronous global -> shared copy of 16 bytes, cached in L2 only (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 
 // ---- bulk tensor copies (TMA) completed through shared-memory barriers --------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1678,6 +1684,336 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
   }
 }
 
+// Fused step for 3D 7-point stencils with an FP32 basis on grids with more tiles than blocks, operands staged
+// by bulk tensor copies: the 3D counterpart of fused_st2d_tma.  Block `rank` takes tiles rank, rank + nblk, ...;
+// thread 0 issues each tile's copies into one of tma_stages shared-memory stages, tma_stages tiles ahead.
+// Per tile (tile_w x tile_h x tile_d points): halo'd boxes (one-point halo in y and z, 16-byte aligned start in
+// x) of raw x_j (or v_j itself on the first step of a substep) and of the window vectors of its finalisation;
+// an own-point box of the reaction field.  The B columns (first four) of each thread's products item are
+// copied by 16-byte cp.async into per-thread slots before the tile's wait, so that their latency overlaps the
+// wait and the finalisation; further columns are read from global memory in the products.  v_j is finalised over the box in shared memory (lagged
+// normalisation: no separate normalise pass and no second grid barrier per step), its own points stored;
+// then x_{j+1} = A~ v_j on the own points, stored raw, and the step's dots.  Points outside the grid arrive as
+// zeros (the Dirichlet value); for periodic or reflected boundaries the halo points the stencil reads there
+// (one face layer per side, no edges or corners) are filled after the finalisation from the box, where the
+// mapped point lies in it, else from global memory, finalised.
+// CTW, CTH, CTD > 0 fix the tile shape at compile time (a kernel instantiation of its own): loop bounds and
+// shared-memory offsets are constants, and a ragged tile at the grid's far faces runs the whole box with the
+// points beyond the grid left out of the stores and the dots.  0: taken from the arguments.
+template <typename T, int CTW = 0, int CTH = 0, int CTD = 0>
+__device__ void fused_st3d_tma(const SolveArgs& a, Ctl& c, int rank, int nblk, int j, int i0, int nwin, bool lead,
+                               T* V, size_t ldv, double* smem, DotAcc<T>& acc, bool prof_on) {
+  constexpr int W = Vec16<T>::W;
+  const OpDesc& op = a.op;
+  const int nx = (int)op.nx, ny = (int)op.ny, nz = (int)op.nz;
+  const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+  const int64_t N = a.N;
+  const int p = a.p;
+  const int tid = threadIdx.x;
+  const int bc = op.bc;
+  T* raw = (T*)a.raw;
+  const T* bf = (const T*)a.bf;  // B columns in the basis precision, column t at t * ldv
+  const bool pend = c.fin_pending != 0;
+  T* vj = V + (size_t)(j - 1) * ldv;
+  T* xo = raw + (size_t)(j & 1) * ldv;  // raw x_{j+1}
+  const int fnw = pend ? c.fin_nwin : 0;
+  const T fh0 = fnw > 0 ? T(c.fin_h[0]) : T(0), fh1 = fnw > 1 ? T(c.fin_h[1]) : T(0),
+          fh2 = fnw > 2 ? T(c.fin_h[2]) : T(0);
+  const T frs = pend ? T(c.fin_rs) : T(1);
+  const int fbase = pend ? c.fin_i0 : i0;
+  const int nfb = pend ? fnw : nwin - 1;
+  const int wslot0 = i0 - fbase, wslot1 = i0 + 1 - fbase;  // window entries i0, i0 + 1 (when below j)
+  T cf[7], ntr[4];
+  {
+    const T* cp = coef_ptr<T>(op, 0);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) cf[k] = cp[k];
+    const T* nt = ntail_ptr<T>(c);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) ntr[t] = t < p ? nt[t] : T(0);
+  }
+  const T* ntp = ntail_ptr<T>(c);
+  constexpr bool kFixed = CTW > 0 && CTH > 0 && CTD > 0;
+  const int S = a.tma_stages, A = W;
+  const int TW = kFixed ? CTW : a.tile_w, TH = kFixed ? CTH : a.tile_h, TD = kFixed ? CTD : a.tile_d;
+  const int BW = kFixed ? CTW + 2 * W : a.tma_bw, BH = kFixed ? CTH + 2 : a.tma_bh;
+  const int bplane = BW * BH;
+  // elements between window boxes (box bytes rounded up to 128)
+  const int fst = kFixed ? (bplane * (CTD + 2) * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T)
+                         : a.tma_box_bytes / (int)sizeof(T);
+  const int gxn = a.tile_gx, gyn = a.tile_gy, ntiles = a.tile_gx * a.tile_gy * a.tile_gz;
+  const int K = rank < ntiles ? (ntiles - rank + nblk - 1) / nblk : 0;
+  const int nwin_l = nwin, i0_l = i0, j_l = j;
+  char* sm = (char*)smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+  uint64_t* bars = (uint64_t*)(sm + a.tma_bar_off);
+  T* bslot = (T*)(sm + a.tma_side_off) + (size_t)tid * 16;  // four 16-byte B vectors of this thread's item
+  const char* maps = (const char*)a.tmaps;  // 128 bytes each: basis, raw ring, (unused), reaction field
+  const bool hasf = a.tma_nf > 0;
+  const int off_f = a.tma_off_f, off_d = a.tma_off_d;
+  const int stage_bytes = a.tma_stage_bytes;
+  const long long timeout_ns = a.timeout_ns;
+  const int BD = kFixed ? CTD + 2 : a.tma_bd;
+  const unsigned expect = (unsigned)(bplane * BD * (int)sizeof(T) * (1 + nfb)) +
+                          (hasf ? (unsigned)(TW * TH * TD * (int)sizeof(T)) : 0u);
+  if (tid == 0 && !c.tma_init) {
+    for (int s = 0; s < S; ++s) mbar_init(bars + s, 1);
+    mbar_init_fence();
+    c.tma_init = 1;
+  }
+  // raw x_j and v_j - 1 were written by every block before the barrier that opened this step
+  fence_proxy_async_all();
+  __syncthreads();
+  const unsigned q0 = c.tma_seq;
+  auto origin = [&](int tile, int& x0, int& y0, int& z0) {
+    const int tx = tile % gxn, r = tile / gxn;
+    x0 = tx * TW;
+    y0 = (r % gyn) * TH;
+    z0 = (r / gyn) * TD;
+  };
+  auto issue = [&](int k) {  // thread 0: the copies of this block's k-th tile of the step
+    const int tile = rank + k * nblk;
+    const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
+    char* base = sm + (size_t)st * stage_bytes;
+    uint64_t* bar = bars + st;
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
+    mbar_arrive_expect_tx(bar, expect);
+    if (pend) tma_load_4d(base, maps + 128, x0 - A, y0 - 1, z0 - 1, (j_l - 1) & 1, bar);
+    else tma_load_4d(base, maps, x0 - A, y0 - 1, z0 - 1, j_l - 1, bar);
+    for (int u = 0; u < nfb; ++u)
+      tma_load_4d(base + off_f + (size_t)u * fst * sizeof(T), maps, x0 - A, y0 - 1, z0 - 1, fbase + u - 1, bar);
+    if (hasf) tma_load_3d(base + off_d, maps + 384, x0, y0, z0, bar);
+  };
+  if (tid == 0)
+    for (int k = 0; k < K && k < S; ++k) issue(k);
+  int done = 0;
+  for (int k = 0; k < K; ++k) {
+    const int tile = rank + k * nblk;
+    const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
+    const unsigned par = ((q0 + (unsigned)k) / (unsigned)S) & 1u;
+    char* base = sm + (size_t)st * stage_bytes;
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
+    const int tw = min(TW, nx - x0), th = min(TH, ny - y0), td = min(TD, nz - z0);  // tw: a multiple of W
+    const int tv = tw / W;
+    // the loops' extent: with a fixed shape the whole box, also on a ragged tile (beyond the grid: the copy's
+    // zero fill, computed, never stored or summed)
+    const int tvl = kFixed ? TW / W : tv, thl = kFixed ? TH : th, tdl = kFixed ? TD : td;
+    const bool edge = bc != 0 && (x0 == 0 || y0 == 0 || z0 == 0 || x0 + tw == nx || y0 + th == ny || z0 + td == nz);
+    // this thread's first products item: its B vectors into the slots now (consumed after the finalisation)
+    const int pitems = tdl * thl * tvl;
+    const int plz = tid / (tvl * thl), prem = tid - plz * (tvl * thl), ply = prem / tvl, pcv = prem - ply * tvl;
+    if (tid < pitems && plz < td && ply < th && pcv < tv) {
+      const size_t r = (size_t)(z0 + plz) * nxy + (uint32_t)(y0 + ply) * nx + (uint32_t)(x0 + pcv * W);
+      for (int t = 0; t < p && t < 4; ++t) cp_async_16(bslot + 4 * t, bf + (size_t)t * ldv + r);
+    }
+    const bool ok = mbar_wait(bars + st, par, timeout_ns);
+    KIOPS_TICK(14);
+    T* sb = (T*)base;
+    const T* fb = (const T*)(base + off_f);
+    const T* db = (const T*)(base + off_d);
+    // v_j over the box: planes 0..td+1, rows 0..th+1, vectors 0..tv+1 (box vector c covers x0 - W + c W ...)
+    if (ok) {
+      const int rv = tvl + 2, tot = (tdl + 2) * (thl + 2) * rv;
+      TileWalk wk(tid, rv, thl + 2);
+      for (int e = tid; e < tot; e += kThreads, wk.next()) {
+        const int hz = wk.s, hy = wk.y, cv = wk.x;
+        const int bi = hz * bplane + hy * BW + cv * W;
+        Vec16<T> v = ld16(sb + bi);
+        if (pend) {
+          Vec16<T> g0 = ld16(fb + bi), g1, g2;
+          if (fnw > 1) g1 = ld16(fb + fst + bi);
+          if (fnw > 2) g2 = ld16(fb + 2 * fst + bi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            T x = fma(-fh0, g0.e[u], v.e[u]);
+            if (fnw > 1) x = fma(-fh1, g1.e[u], x);
+            if (fnw > 2) x = fma(-fh2, g2.e[u], x);
+            v.e[u] = x * frs;
+          }
+        }
+        st16(sb + bi, v);
+        const bool own = hz >= 1 && hz <= td && hy >= 1 && hy <= th && cv >= 1 && cv <= tv;
+        if (pend && own)
+          stg16(vj + (size_t)(z0 - 1 + hz) * nxy + (uint32_t)(y0 - 1 + hy) * nx + (uint32_t)(x0 - W + cv * W), v);
+      }
+    }
+    if (edge) {  // uniform over the block
+      // halo points outside the grid that the stencil reads: one layer per face of the tile
+      __syncthreads();
+      if (ok) {
+        const int nxl = x0 == 0 ? th * td : 0, nxh = x0 + tw == nx ? th * td : 0;
+        const int nyl = y0 == 0 ? tw * td : 0, nyh = y0 + th == ny ? tw * td : 0;
+        const int nzl = z0 == 0 ? tw * th : 0, nzh = z0 + td == nz ? tw * th : 0;
+        const int L = nxl + nxh + nyl + nyh + nzl + nzh;
+        const T* src = pend ? raw + (size_t)((j_l - 1) & 1) * ldv : V + (size_t)(j_l - 1) * ldv;
+        const T* f0 = V + (size_t)(fbase - 1) * ldv;  // the finalisation window, consecutive columns
+        for (int e = tid; e < L; e += kThreads) {
+          int q = e, hx, hy, hz;  // box coordinates (points)
+          if (q < nxl + nxh) {  // x faces: (ly, lz) over th x td
+            const bool hi = q >= nxl;
+            if (hi) q -= nxl;
+            hy = 1 + q % th, hz = 1 + q / th, hx = hi ? W + tw : W - 1;
+          } else if ((q -= nxl + nxh) < nyl + nyh) {  // y faces: (lx, lz) over tw x td
+            const bool hi = q >= nyl;
+            if (hi) q -= nyl;
+            hx = W + q % tw, hz = 1 + q / tw, hy = hi ? th + 1 : 0;
+          } else {  // z faces: (lx, ly) over tw x th
+            q -= nyl + nyh;
+            const bool hi = q >= nzl;
+            if (hi) q -= nzl;
+            hx = W + q % tw, hy = 1 + q / tw, hz = hi ? td + 1 : 0;
+          }
+          const int mx = (int)bc_index(bc, x0 - W + hx, nx), my = (int)bc_index(bc, y0 - 1 + hy, ny),
+                    mz = (int)bc_index(bc, z0 - 1 + hz, nz);
+          const int mbx = mx - (x0 - W), mby = my - (y0 - 1), mbz = mz - (z0 - 1);
+          T x;
+          if (mx < 0 || my < 0 || mz < 0) {
+            x = T(0);  // no mapped point (a reflected axis of one point)
+          } else if (mbx >= 0 && mbx < tw + 2 * W && mby >= 0 && mby < th + 2 && mbz >= 0 && mbz < td + 2) {
+            x = sb[mbz * bplane + mby * BW + mbx];  // inside the box (reflection): finalised above
+          } else {
+            const size_t r = (size_t)mz * nxy + (uint32_t)my * nx + (uint32_t)mx;
+            x = src[r];
+            if (pend) {
+              x = fma(-fh0, f0[r], x);
+              if (fnw > 1) x = fma(-fh1, f0[r + ldv], x);
+              if (fnw > 2) x = fma(-fh2, f0[r + 2 * ldv], x);
+              x = x * frs;
+            }
+          }
+          sb[hz * bplane + hy * BW + hx] = x;
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      // a copy that never completed: raise the abort flag (the step's barrier then stops every block)
+      if (tid == 0 && a.abort_flag) atomicExch(a.abort_flag, ST_ETIMEOUT);
+      break;
+    }
+    done = k + 1;
+    KIOPS_TICK(12);
+    cp_async_wait_all();  // this thread's B slots
+    // A~ v_j on the tile's own points and the step's dots
+    {
+      const int tot = tdl * thl * tvl;
+      TileWalk wk(tid, tvl, thl);
+      for (int e = tid; e < tot; e += kThreads, wk.next()) {
+        const int lz = wk.s, ly = wk.y, cv = wk.x;
+        if (kFixed && (lz >= td || ly >= th || cv >= tv)) continue;  // beyond the grid (ragged tile)
+        const int bi = (lz + 1) * bplane + (ly + 1) * BW + W + cv * W;
+        const size_t r = (size_t)(z0 + lz) * nxy + (uint32_t)(y0 + ly) * nx + (uint32_t)(x0 + cv * W);
+        const Vec16<T> ctr = ld16(sb + bi);
+        Vec16<T> out;
+#pragma unroll
+        for (int u = 0; u < W; ++u) out.e[u] = cf[0] * ctr.e[u];
+        {
+          const T wl = sb[bi - 1], er = sb[bi + W];
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(cf[1], u == 0 ? wl : ctr.e[u == 0 ? 0 : u - 1], out.e[u]);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(cf[2], u == W - 1 ? er : ctr.e[u == W - 1 ? 0 : u + 1], out.e[u]);
+        }
+        {
+          const Vec16<T> ym = ld16(sb + bi - BW);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(cf[3], ym.e[u], out.e[u]);
+        }
+        {
+          const Vec16<T> yp = ld16(sb + bi + BW);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(cf[4], yp.e[u], out.e[u]);
+        }
+        {
+          const Vec16<T> zm = ld16(sb + bi - bplane);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(cf[5], zm.e[u], out.e[u]);
+        }
+        {
+          const Vec16<T> zp = ld16(sb + bi + bplane);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(cf[6], zp.e[u], out.e[u]);
+        }
+        if (hasf) {
+          const Vec16<T> dv = ld16(db + (lz * TH + ly) * TW + cv * W);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(dv.e[u], ctr.e[u], out.e[u]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < p) {
+            const Vec16<T> bv = e == tid ? ld16(bslot + 4 * t) : ld16(bf + (size_t)t * ldv + r);
+#pragma unroll
+            for (int u = 0; u < W; ++u) out.e[u] = fma(ntr[t], bv.e[u], out.e[u]);
+          }
+        for (int t = 4; t < p; ++t) {
+          const Vec16<T> bv = ld16(bf + (size_t)t * ldv + r);
+#pragma unroll
+          for (int u = 0; u < W; ++u) out.e[u] = fma(ntp[t], bv.e[u], out.e[u]);
+        }
+        stg16(xo + r, out);
+        {  // the step's dots
+          Vec16<T> g;
+          if (i0_l != j_l) g = ld16(fb + wslot0 * fst + bi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const T v0 = (i0_l == j_l) ? ctr.e[u] : g.e[u];
+            acc.add(0, v0, out.e[u]);
+            acc.add(kChunk, ctr.e[u], v0);
+          }
+        }
+        if (nwin_l > 1) {
+          Vec16<T> g;
+          if (i0_l + 1 != j_l) g = ld16(fb + wslot1 * fst + bi);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const T v1 = (i0_l + 1 == j_l) ? ctr.e[u] : g.e[u];
+            acc.add(1, v1, out.e[u]);
+            acc.add(kChunk + 1, ctr.e[u], v1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          if (nwin_l > 2) {  // i0 + 2 == j
+            acc.add(2, ctr.e[u], out.e[u]);
+            acc.add(kChunk + 2, ctr.e[u], ctr.e[u]);
+          }
+          acc.add(2 * kChunk, out.e[u], out.e[u]);
+        }
+      }
+    }
+    KIOPS_TICK(13);
+    fence_proxy_async_smem();  // this stage's shared-memory accesses come before the next copies into it
+    __syncthreads();
+    KIOPS_TICK(15);
+    if (tid == 0 && k + S < K) issue(k + S);
+  }
+  // copies issued but not consumed (only after a copy timed out): wait for them, bounded
+  cp_async_wait_all();
+  for (int k = done; k < K && k < done + S; ++k) {
+    const int st = (int)((q0 + (unsigned)k) % (unsigned)S);
+    mbar_wait(bars + st, ((q0 + (unsigned)k) / (unsigned)S) & 1u, timeout_ns);
+  }
+  __syncthreads();
+  if (tid == 0) c.tma_seq = q0 + (unsigned)K;
+  if (lead && tid < p) {  // tail rows: finalised tail of v_j (c.tail) and the shift K of Theorem 1
+    const int64_t rr = N + tid;
+    if (pend) vj[rr] = (T)c.tail[tid];
+    const T xv = tid + 1 < p ? (T)c.tail[tid + 1] : T(0);
+    xo[rr] = xv;
+    const T vjt = (T)c.tail[tid];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      if (u < nwin) {
+        const T vi = (i0 + u == j) ? vjt : V[(size_t)(i0 + u - 1) * ldv + rr];
+        acc.add(u, vi, xv);
+        acc.add(kChunk + u, vjt, vi);
+      }
+    }
+    acc.add(2 * kChunk, xv, xv);
+  }
+}
+
 // Fused path: issue the asynchronous copies of raw x_jn (written by every block before the barrier that
 // was passed) over this block's tile + halo into the stage, from the halo index table.  Threads below
 // `first` issue none (thread 0 computes the step's coefficients meanwhile); the copies are waited for
@@ -1962,7 +2298,8 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
   const size_t ldv = (size_t)a.ldv;
   const int ldh = a.m_max + 2;
   const bool prof_on = a.prof != nullptr && lead;
-  const bool fused = KIND == OP_ST2D && a.fused != 0;
+  // lagged normalisation: 2D grids (tiles), 3D grids with an FP32 basis staged in 3D tiles (TMA kernels)
+  const bool fused = (KIND == OP_ST2D || (KIND == OP_ST3D && TMA != 0 && sizeof(T) == 4)) && a.fused != 0;
 
   if (tid == 0) {
     c.status = ST_OK;
@@ -2145,7 +2482,14 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       if (fused) {
         DotAcc<T> dacc;
         dacc.zero();
-        fused_st2d_phase<T, TMA>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+        if constexpr (KIND == OP_ST3D) {
+          if constexpr (TMA == kTmaFixed && sizeof(T) == 4)  // 32 x 8 x 4 tiles
+            fused_st3d_tma<T, 32, 8, 4>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+          else if constexpr (TMA != 0 && sizeof(T) == 4)
+            fused_st3d_tma<T>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+        } else {
+          fused_st2d_phase<T, TMA>(a, c, team.rank, team.size, j, i0, nwin, lead, V, ldv, smem_dyn, dacc, prof_on);
+        }
         __syncthreads();
         if (tid == 0) {
           c.ring_lo = (c.ring_lo <= j - 1) ? c.ring_lo : j;  // v_j is now in the ring

@@ -11,6 +11,8 @@ int wide_threads();                 // block size of solve_kernel_f64_wide
 void* solve_kernel_f32(int kind);   // grid engine, FP32 basis
 void* solve_kernel_tma(bool fp32);  // grid engine, 2D stencils, with the bulk-tensor-copy several-tiles path
 void* solve_kernel_tma_fixed();     // the same, FP32, for 32 x 16 tiles, two species and p = 3
+void* solve_kernel_tma3d();         // grid engine, 3D stencils, FP32 basis, 3D tiles staged by bulk tensor copies
+void* solve_kernel_tma3d_fixed();   // the same compiled for 32 x 8 x 4 tiles
 void* team_kernel_f64(int kind);    // batch team engine, FP64 basis
 void* team_kernel_f32(int kind);    // batch team engine, FP32 basis
 void* noalloc_kernel(int kind);     // single block, argument block by value (FP64)

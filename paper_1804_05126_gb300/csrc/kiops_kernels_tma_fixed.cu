@@ -8,4 +8,6 @@ using namespace kiops_dev;
 
 namespace kiops_k {
 void* solve_kernel_tma_fixed() { return (void*)kiops_solve_kernel<float, OP_ST2D, true, kTmaFixed>; }
+// 3D stencils, FP32 basis: the staged 3D tile path compiled for 32 x 8 x 4 tiles
+void* solve_kernel_tma3d_fixed() { return (void*)kiops_solve_kernel<float, OP_ST3D, true, kTmaFixed>; }
 }  // namespace kiops_k

@@ -513,6 +513,36 @@ def test_tma_edge_pass_on_a_one_tile_wide_grid(bc):
     assert rel(wf, w_ref) <= 10 * P.tol
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic", "neumann"])
+@pytest.mark.parametrize("n,m_o,p,field,blocks", [(48, 1, 3, False, 3), (48, 2, 4, False, 3), (48, 3, 0, False, 3),
+                                                  (48, 2, 6, False, 3), (52, 2, 4, True, 3), (96, 2, 4, False, 0)])
+def test_tma_3d_tiles_fp32(bc, n, m_o, p, field, blocks):
+    """3D 7-point stencils with an FP32 basis on grids with more tiles than blocks take the staged 3D tile path
+    (kiops_stats tile_path 4: halo'd boxes of x_j and the finalisation window copied by bulk tensor copies, v_j
+    finalised in shared memory, no separate normalise pass): each boundary treatment, orthogonalisation
+    lengths 1 to 3, p = 0 (plain exponential), 3, 4 and 6 (B weights beyond the four held in registers), 52^3
+    (ragged tiles along all three axes, and a pointwise reaction field staged as an own-point box), 48^3 over
+    3 blocks and 96^3 over the default grid.  Against the separate-normalise path (fuse_stencil off) within
+    tol and against the oracle within 10 tol; the kernel compiled for 32 x 8 x 4 tiles (the default) and the
+    general one (tma_fixed off) both."""
+    op = dict(W.adr3d(n, -20.0, (5.0, -3.0, 7.0)), bc=bc)
+    rng = np.random.default_rng(50 + 7 * p + n)
+    if field:
+        op["diag"] = rng.uniform(-20.0, 0.0, n ** 3)
+    P = W.Problem(f"adr3d_{n}_{bc}", op, rng.standard_normal((p + 1, n ** 3)), 1e-2, 1e-6, precision="fp32_basis")
+    out = {}
+    for name, kw in (("staged", {}), ("general", dict(tma_fixed=0)), ("separate", dict(fuse_stencil=False))):
+        s = kiops.Solver(device=0, grid_blocks=blocks, **kw)
+        out[name] = gpu_solve(s, P, m_o=m_o)
+        s.close()
+    (wf, sf), (wn, sn), (wg, sg) = out["staged"], out["general"], out["separate"]
+    assert sf["status"] == 0 and sn["status"] == 0 and sg["status"] == 0
+    assert sf["tile_path"] == 4 and sn["tile_path"] == 4 and sg["tile_path"] == 0
+    assert rel(wf, wg) <= P.tol and rel(wn, wg) <= P.tol
+    w_ref, _, _ = oracle_solve(P, m_o=m_o)
+    assert rel(wf, w_ref) <= 10 * P.tol
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32_basis", 1e-6)])
 def test_2048_grid_several_tiles_vs_dst_closed_form(solver, precision, tol):
     """Full-size pin of the several-tiles path: 2048^2 Dirichlet diffusion + shift (N = 4.2 M, 4 or 2 tiles
