@@ -451,8 +451,9 @@ STEP_PHASES = (2, 3, 4, 5, 11, 12, 13, 14, 15)  # phase counters of the Krylov s
 
 def measure_beyond_l2(dev):
     """The Krylov step on grids whose step working set exceeds the 129 MB L2: 2048^2 Gray-Scott with the FP32
-    basis (N = 8.4 M) and 2048^2 ADR in FP64 (N = 4.2 M, tau = 1e-2 / 16 so that the Krylov work stays near
-    the 512^2 solve's).  Step time = event-timed solve x the step's share of the device phase counters of a
+    basis (N = 8.4 M), 2048^2 ADR in FP64 (N = 4.2 M, tau = 1e-2 / 16 so that the Krylov work stays near
+    the 512^2 solve's) and a 160^3 7-point ADR operator of the served mix's largest size with the FP32 basis
+    (N = 4.1 M, p = 4, tau = 1e-2, tol 1e-6).  Step time = event-timed solve x the step's share of the device phase counters of a
     profiled solve / matvecs.  Algorithmic bytes of one step (Algorithm 2, m_o = 2): read v_j, v_{j-1} and
     the p columns of B, write v_{j+1}: (p + 3) s N, plus the operator's pointwise fields (ns s N)."""
     import dataclasses
@@ -462,8 +463,12 @@ def measure_beyond_l2(dev):
     from paper_1804_05126_gb300 import kiops, tune
 
     hbm = peaks().get("hbm_gbs", 6768.1)
+    n3 = 160
+    adr3d = W.Problem("adr3d_160", W.adr3d(n3, -20.0, (5.0, -3.0, 7.0)),
+                      np.random.default_rng(5).standard_normal((5, n3 ** 3)), 1e-2, 1e-6, precision="fp32_basis")
     cases = [("gray_scott_2048_fp32_basis", W.problem_gray_scott(n=2048), "fp32_basis", 4, 2),
-             ("adr2d_2048_fp64", dataclasses.replace(W.problem_adr2d(n=2048), tau=1e-2 / 16), "fp64", 8, 1)]
+             ("adr2d_2048_fp64", dataclasses.replace(W.problem_adr2d(n=2048), tau=1e-2 / 16), "fp64", 8, 1),
+             ("adr3d_160_fp32_basis", adr3d, "fp32_basis", 4, 0)]
     res = {}
     for name, P, prec, s_bytes, nfields in cases:
         sol = kiops.Solver(device=dev.index)
@@ -492,7 +497,7 @@ def measure_beyond_l2(dev):
         res[name] = {"N": P.n, "p": P.p, "ms_per_solve": ms, "matvecs": st["matvecs"], "substeps": st["substeps"],
                      "step_us": step_us, "step_share_of_solve": share, "bytes_per_step": bytes_step,
                      "step_gbs": gbs, "step_hbm_frac": gbs / hbm, "grid_blocks": st["grid_blocks"],
-                     "tuned_launch_shape": best, "tuning_ms_per_solve": tuning}
+                     "tile_path": st["tile_path"], "tuned_launch_shape": best, "tuning_ms_per_solve": tuning}
         sol.close()
         prof.close()
     res["note"] = ("step_hbm_frac: algorithmic step bytes / step time / measured copy bandwidth; the FP64 case "
