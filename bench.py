@@ -455,7 +455,9 @@ def measure_beyond_l2(dev):
     the 512^2 solve's) and a 160^3 7-point ADR operator of the served mix's largest size with the FP32 basis
     (N = 4.1 M, p = 4, tau = 1e-2, tol 1e-6).  Step time = event-timed solve x the step's share of the device phase counters of a
     profiled solve / matvecs.  Algorithmic bytes of one step (Algorithm 2, m_o = 2): read v_j, v_{j-1} and
-    the p columns of B, write v_{j+1}: (p + 3) s N, plus the operator's pointwise fields (ns s N)."""
+    the p columns of B, write v_{j+1}: (p + 3) s N, plus the operator's pointwise field planes of one grid
+    point each (s bytes a point and plane: ADR's reaction field; Gray-Scott's two shared fields v0^2 and
+    2 u0 v0, s N together)."""
     import dataclasses
 
     import torch
@@ -470,7 +472,7 @@ def measure_beyond_l2(dev):
              ("adr2d_2048_fp64", dataclasses.replace(W.problem_adr2d(n=2048), tau=1e-2 / 16), "fp64", 8, 1),
              ("adr3d_160_fp32_basis", adr3d, "fp32_basis", 4, 0)]
     res = {}
-    for name, P, prec, s_bytes, nfields in cases:
+    for name, P, prec, s_bytes, planes in cases:
         sol = kiops.Solver(device=dev.index)
         prof = kiops.Solver(device=dev.index, profile=True)
         op, pop = sol.operator(P.op), prof.operator(P.op)
@@ -492,16 +494,25 @@ def measure_beyond_l2(dev):
         cyc = pst["phase_cycles"]
         share = sum(cyc[k] for k in STEP_PHASES) / max(1, sum(cyc))
         step_us = 1e3 * ms * share / st["matvecs"]
-        bytes_step = (P.p + 3) * s_bytes * P.n + nfields * s_bytes * P.n
+        npts = P.n // int(P.op.get("nspecies", 1))
+        bytes_step = (P.p + 3) * s_bytes * P.n + planes * s_bytes * npts
         gbs = bytes_step / (step_us * 1e-6) / 1e9
+        # the one-barrier schedule (lagged normalisation, every tiled path) also reads the second
+        # finalisation-window vector and writes v_j besides x_{j+1}
+        lagged = (bytes_step + 2 * s_bytes * P.n) if st["tile_path"] > 0 else None
         res[name] = {"N": P.n, "p": P.p, "ms_per_solve": ms, "matvecs": st["matvecs"], "substeps": st["substeps"],
                      "step_us": step_us, "step_share_of_solve": share, "bytes_per_step": bytes_step,
-                     "step_gbs": gbs, "step_hbm_frac": gbs / hbm, "grid_blocks": st["grid_blocks"],
+                     "step_gbs": gbs, "step_hbm_frac": gbs / hbm,
+                     "bytes_per_step_one_barrier": lagged,
+                     "step_hbm_frac_one_barrier": (lagged / (step_us * 1e-6) / 1e9 / hbm) if lagged else None,
+                     "grid_blocks": st["grid_blocks"],
                      "tile_path": st["tile_path"], "tuned_launch_shape": best, "tuning_ms_per_solve": tuning}
         sol.close()
         prof.close()
-    res["note"] = ("step_hbm_frac: algorithmic step bytes / step time / measured copy bandwidth; the FP64 case "
-                   "is bound by the FP64 pipe, not by HBM")
+    res["note"] = ("step_hbm_frac: algorithmic step bytes ((p + 3) s N + field planes) / step time / measured "
+                   "copy bandwidth; *_one_barrier: the bytes the lagged-normalisation schedule must move (two more "
+                   "vectors: the second finalisation-window vector and v_j); the FP64 case is bound by the FP64 "
+                   "pipe, not by HBM")
     return res
 
 

@@ -167,13 +167,33 @@ enum { KIOPS_BC_DIRICHLET = 0, KIOPS_BC_PERIODIC = 1, KIOPS_BC_NEUMANN = 2 };
  *   (A x)_s(ix,iy) = coef[s][0] x_s(ix,iy) + coef[s][1] x_s(ix-1,iy) + coef[s][2] x_s(ix+1,iy)
  *                  + coef[s][3] x_s(ix,iy-1) + coef[s][4] x_s(ix,iy+1) + sum_r diag[s][r][pt] x_r(ix,iy)
  * with x outside the grid given by bc.  diag[s][r] are device pointers of nx*ny FP64 values or NULL
- * (= 0).  This covers the Jacobians of the paper's 2D ADR and Gray-Scott test problems (section 4). */
+ * (= 0).  This covers the Jacobians of the paper's 2D ADR and Gray-Scott test problems (section 4).
+ *
+ * Shared coupling fields (optional; zero the members below when not used, e.g. by memset of the whole
+ * descriptor).  With nfields = 1 or 2 the entries of the pointwise block are affine in fields that several
+ * entries share, and diag must be all NULL:
+ *   diag[s][r](pt) = fma(dweight[s][r], field[dfield[s][r]][pt], dconst[s][r])   if dfield[s][r] >= 0,
+ *   diag[s][r](pt) = dconst[s][r]                                                 if dfield[s][r] = -1,
+ * evaluated in FP64 (one rounding).  field[f] are device pointers of nx*ny FP64 values, borrowed like diag.
+ * The Gray-Scott Jacobian of section 4 has this form with the two fields v0^2 and 2 u0 v0 (entries
+ * -F - v0^2, -2 u0 v0, v0^2 and 2 u0 v0 - (F + k)).  The operator writes the entries once into device
+ * memory it owns (8 bytes per point and nonzero entry, freed by kiops_op_destroy) for the paths that read
+ * whole entries; the staged several-tiles step with an FP32 basis (kiops_stats.tile_path 2 or 3) reads the
+ * nfields planes instead, and forms the entries in FP32 (so its results differ from those of the same block
+ * given by diag by the FP32 rounding of the entries).  Errors: KIOPS_EINVAL for nfields outside 0..2, a
+ * NULL field, diag given as well, or dfield outside -1..nfields-1 on an entry of the block; KIOPS_ENOMEM
+ * or KIOPS_ECUDA if the entries cannot be allocated or written. */
 typedef struct {
   int64_t nx, ny;
   int nspecies;            /* 1 or 2 */
   int bc;                  /* KIOPS_BC_* */
   double coef[2][5];
   const double* diag[2][2];
+  int nfields;             /* 0 (diag gives the block), 1 or 2 */
+  int dfield[2][2];
+  double dconst[2][2];
+  double dweight[2][2];
+  const double* field[2];
 } kiops_stencil2d_desc;
 
 /* 7-point 3D stencil, one species, x-fastest (index = (iz*ny + iy)*nx + ix):

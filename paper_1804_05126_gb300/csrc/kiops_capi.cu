@@ -58,7 +58,8 @@ struct kiops_ctx {
 struct kiops_op {
   kiops_ctx* ctx;
   OpDesc d;
-  double nz = 0.0;  // stored nonzeros (the cost model's nz(A))
+  double nz = 0.0;         // stored nonzeros (the cost model's nz(A))
+  double* owned = nullptr; // entries of a block given by shared coupling fields (written at creation)
 };
 
 namespace {
@@ -288,10 +289,37 @@ bool setup_tma(kiops_ctx* ctx, void* fn, void* fn_fixed, int blocks, int threads
   const int ns = a.op.nspecies, p = a.p;
   if ((nx * (int64_t)es) % 16 != 0 || (npts * (int64_t)es) % 16 != 0 || nx > (1 << 30) || ny > (1 << 30)) return false;
   if (!tensor_map_encoder()) return false;
+  // staged planes and the constants that turn them into the block's entries (SolveArgs::tma_aff_*)
   int nf = 0, fidx[2][2] = {{-1, -1}, {-1, -1}};
-  for (int sp = 0; sp < ns; ++sp)
-    for (int q = 0; q < ns; ++q)
-      if (a.op.diag[sp][q]) fidx[sp][q] = nf++;
+  double aff[2][4] = {};
+  for (int sp = 0; sp < ns; ++sp) {
+    double* f = aff[sp];
+    f[0] = a.op.coef[sp][0];
+    f[1] = f[3] = 1.0;
+  }
+  if (a.op.nfields > 0) {  // shared coupling fields: one plane per field
+    nf = a.op.nfields;
+    for (int sp = 0; sp < ns; ++sp)
+      for (int q = 0; q < ns; ++q) {
+        const int k = a.op.dfield[sp][q];
+        const double c0 = a.op.dconst[sp][q], w = a.op.dweight[sp][q];
+        if (q == sp) {
+          if (k >= 0) {
+            fidx[sp][q] = k;
+            aff[sp][1] = w;
+          }
+          aff[sp][0] += c0;  // the own entry's constant joins the centre coefficient
+        } else if (k >= 0 || c0 != 0.0) {
+          fidx[sp][q] = k >= 0 ? k : 0;  // a constant entry: any plane with weight 0
+          aff[sp][2] = c0;
+          aff[sp][3] = k >= 0 ? w : 0.0;
+        }
+      }
+  } else {
+    for (int sp = 0; sp < ns; ++sp)
+      for (int q = 0; q < ns; ++q)
+        if (a.op.diag[sp][q]) fidx[sp][q] = nf++;
+  }
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device) != cudaSuccess) return false;
   const int S = ctx->cfg.tma_stages >= 3 && ctx->cfg.tma_stages <= 6 ? ctx->cfg.tma_stages : 2;
@@ -337,8 +365,13 @@ bool setup_tma(kiops_ctx* ctx, void* fn, void* fn_fixed, int blocks, int threads
     a.tma_bw = bw;
     a.tma_bh = bh;
     a.tma_nf = nf;
-    for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < 2; ++sp) {
       for (int q = 0; q < 2; ++q) a.tma_fidx[sp][q] = fidx[sp][q];
+      for (int k = 0; k < 4; ++k) {
+        a.tma_aff_d[sp][k] = aff[sp][k];
+        a.tma_aff_f[sp][k] = (float)aff[sp][k];
+      }
+    }
     a.tma_stage_bytes = (int)stage;
     a.tma_box_bytes = (int)box;
     a.tma_off_f = (int)off_f;
@@ -815,6 +848,12 @@ kiops_status run_single(kiops_ctx* ctx, const kiops_op* A, double tau, int p, co
   return KIOPS_OK;
 }
 
+// Entry of a pointwise coupling block given by a shared field: out = fma(w, f, c), or c without a field.
+__global__ void coupling_entry_kernel(const double* f, double w, double c, double* out, int64_t n) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    out[r] = f ? fma(w, __ldg(f + r), c) : c;
+}
+
 template <int KIND>
 __global__ void op_apply_kernel(OpDesc op, const double* x, double* y) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < op.n; r += (int64_t)gridDim.x * blockDim.x)
@@ -1003,6 +1042,57 @@ kiops_status kiops_op_stencil2d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
     for (int k = 0; k < 7; ++k) o->d.coef_f[s][k] = (float)o->d.coef[s][k];
     for (int r = 0; r < 2; ++r) o->d.diag[s][r] = (s < d->nspecies && r < d->nspecies) ? d->diag[s][r] : nullptr;
   }
+  if (d->nfields != 0) {  // shared coupling fields: check, then write the block's entries once
+    std::unique_ptr<kiops_op> guard(o);
+    const int ns = d->nspecies, nf = d->nfields;
+    if (nf < 0 || nf > 2) return fail(ctx, KIOPS_EINVAL, "nfields %d: shared coupling fields take 0, 1 or 2", nf);
+    for (int f = 0; f < nf; ++f)
+      if (!d->field[f]) return fail(ctx, KIOPS_EINVAL, "shared coupling field %d is NULL", f);
+    int nent = 0;
+    for (int s = 0; s < ns; ++s)
+      for (int r = 0; r < ns; ++r) {
+        if (d->diag[s][r]) return fail(ctx, KIOPS_EINVAL, "diag and shared coupling fields given together");
+        if (d->dfield[s][r] < -1 || d->dfield[s][r] >= nf)
+          return fail(ctx, KIOPS_EINVAL, "dfield[%d][%d] = %d outside -1..%d", s, r, d->dfield[s][r], nf - 1);
+        if (d->dfield[s][r] >= 0 || d->dconst[s][r] != 0.0) ++nent;
+      }
+    const int64_t npts = d->nx * d->ny;
+    if (nent > 0) {
+      if (cudaMalloc(&o->owned, (size_t)nent * npts * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KIOPS_ENOMEM, "no device memory for the coupling block's entries (%d x %lld points)",
+                    nent, (long long)npts);
+      }
+      struct Owned {  // frees the entries if a later step fails
+        kiops_op* op;
+        ~Owned() { if (op && op->owned) cudaFree(op->owned); }
+      } owned_guard{o};
+      int e = 0;
+      const int blocks = (int)std::min<int64_t>((npts + 255) / 256, (int64_t)ctx->sms * 8);
+      for (int s = 0; s < ns; ++s)
+        for (int r = 0; r < ns; ++r) {
+          const int k = d->dfield[s][r];
+          if (k < 0 && d->dconst[s][r] == 0.0) continue;
+          double* out = o->owned + (size_t)e++ * npts;
+          coupling_entry_kernel<<<blocks, 256, 0, ctx->stream>>>(k >= 0 ? d->field[k] : nullptr, d->dweight[s][r],
+                                                               d->dconst[s][r], out, npts);
+          o->d.diag[s][r] = out;
+        }
+      KCHECK(ctx, cudaGetLastError());
+      KCHECK(ctx, cudaStreamSynchronize(ctx->stream));
+      owned_guard.op = nullptr;
+    }
+    o->d.nfields = nf;
+    for (int f = 0; f < 2; ++f) o->d.field[f] = f < nf ? d->field[f] : nullptr;
+    for (int s = 0; s < 2; ++s)
+      for (int r = 0; r < 2; ++r) {
+        const bool in = s < ns && r < ns;
+        o->d.dfield[s][r] = in ? d->dfield[s][r] : -1;
+        o->d.dconst[s][r] = in ? d->dconst[s][r] : 0.0;
+        o->d.dweight[s][r] = in ? d->dweight[s][r] : 0.0;
+      }
+    guard.release();
+  }
   o->nz = 5.0 * (double)o->d.n;
   for (int s = 0; s < 2; ++s)
     for (int r = 0; r < 2; ++r)
@@ -1040,6 +1130,7 @@ kiops_status kiops_op_stencil3d(kiops_ctx* ctx, kiops_op** op, const kiops_stenc
 
 kiops_status kiops_op_destroy(kiops_op* op) {
   if (!op) return KIOPS_EINVAL;
+  if (op->owned) cudaFree(op->owned);
   delete op;
   return KIOPS_OK;
 }

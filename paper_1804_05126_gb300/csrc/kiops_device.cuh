@@ -70,6 +70,13 @@ struct OpDesc {
   double coef[2][7];
   float coef_f[2][7];        // the same coefficients rounded to FP32 (FP32 basis)
   const double* diag[2][2];
+  // 2D stencils with shared coupling fields: entry (s, q) of the pointwise block is
+  // fma(dweight[s][q], field[dfield[s][q]], dconst[s][q]) (dconst alone for dfield -1); diag then points at
+  // these entries as the operator wrote them, and the staged tile path reads the nfields planes instead.
+  int nfields;
+  int dfield[2][2];
+  double dconst[2][2], dweight[2][2];
+  const double* field[2];
 };
 
 // Stencil coefficients in the basis precision (FP64 -> FP32 conversions run at the FP64 rate on this GPU,
@@ -163,6 +170,11 @@ struct SolveArgs {
   int tma_bw, tma_bh;
   int tma_nf;                // coupling-field planes staged per tile
   int tma_fidx[2][2];        // plane of the coupling field (s, q) among the staged ones, -1 if none
+  // per species, in the basis precision: the centre coefficient plus the constant of the own entry, the weight
+  // of the own entry's plane, the constant and the weight of the other species' entry (a plane given as the
+  // entry itself: the centre coefficient, 1, 0, 1)
+  alignas(16) float tma_aff_f[2][4];
+  alignas(16) double tma_aff_d[2][4];
   int tma_stage_bytes, tma_box_bytes, tma_off_f, tma_off_b, tma_off_d, tma_bar_off;
   int tma_side_off;          // kThreads x 4 elements: per-thread landing slots of an edge tile's wrapped halo
   int tile_d, tile_gz, tma_bd;  // 3D stencils: tile depth, tiles along z, box depth (tile_d + 2)
@@ -1136,6 +1148,23 @@ __device__ __forceinline__ void stg16(double* p, const Vec16<double>& v) {
   __stcg((double2*)p, make_double2(v.e[0], v.e[1]));
 }
 
+// The staged path's centre and coupling constants of species sp (SolveArgs::tma_aff_*), one 16-byte
+// shared-memory read (two with an FP64 basis).
+template <typename T>
+struct Aff4 {
+  T cc, wo, ct, wt;
+};
+template <typename T>
+__device__ __forceinline__ Aff4<T> tma_aff(const SolveArgs& a, int sp) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *(const float4*)a.tma_aff_f[sp];
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    const double2 u = *(const double2*)a.tma_aff_d[sp], v = *(const double2*)(a.tma_aff_d[sp] + 2);
+    return {u.x, u.y, v.x, v.y};
+  }
+}
+
 // Fused step on grids with more tiles than blocks, operands staged by bulk tensor copies (TMA).  Block `rank`
 // takes tiles rank, rank + nblk, ... in turn; one thread issues each tile's copies into one of tma_stages
 // shared-memory stages (completed through that stage's barrier), tma_stages tiles ahead of the tile being
@@ -1390,17 +1419,19 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
         const int bi = sp * bplane + (ly + 1) * BW + W + cv * W;
         const int pi = ly * TW + cv * W;
         const int fo = sp ? fo_s[1] : fo_s[0], ft = sp ? ft_s[1] : ft_s[0];
-        const T c0 = sp ? cfr[1][0] : cfr[0][0], c1 = sp ? cfr[1][1] : cfr[0][1], c2 = sp ? cfr[1][2] : cfr[0][2];
+        const T c1 = sp ? cfr[1][1] : cfr[0][1], c2 = sp ? cfr[1][2] : cfr[0][2];
         const T c3 = sp ? cfr[1][3] : cfr[0][3], c4 = sp ? cfr[1][4] : cfr[0][4];
+        const Aff4<T> af = tma_aff<T>(a, sp);  // centre and coupling constants (one shared-memory read)
         // each operand vector is read right before its terms are added (short live ranges); per element the
-        // terms are added in the order of fused_st2d_tiles
+        // terms are added in the order of fused_st2d_tiles (a plane that is the entry itself has weight 1 and
+        // no constant, so that fma(1, d, c) = c + d)
         const Vec16<T> ctr = ld16(sb + bi);
         Vec16<T> out;
         {
           Vec16<T> dow;
           if (fo >= 0) dow = ld16(db + fo * oplane + pi);
 #pragma unroll
-          for (int u = 0; u < W; ++u) out.e[u] = (fo >= 0 ? c0 + dow.e[u] : c0) * ctr.e[u];
+          for (int u = 0; u < W; ++u) out.e[u] = (fo >= 0 ? fma(af.wo, dow.e[u], af.cc) : af.cc) * ctr.e[u];
         }
         {
           const T wl = sb[bi - 1], er = sb[bi + W];
@@ -1422,7 +1453,7 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
         if (ft >= 0) {
           const Vec16<T> oth = ld16(sb + bi + (1 - 2 * sp) * bplane), dth = ld16(db + ft * oplane + pi);
 #pragma unroll
-          for (int u = 0; u < W; ++u) out.e[u] = fma(dth.e[u], oth.e[u], out.e[u]);
+          for (int u = 0; u < W; ++u) out.e[u] = fma(fma(af.wt, dth.e[u], af.ct), oth.e[u], out.e[u]);
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t)
@@ -2364,11 +2395,16 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
       const int64_t pchunk = (npts + team.size - 1) / team.size;
       const int64_t q0 = (int64_t)team.rank * pchunk, q1 = q0 + pchunk < npts ? q0 + pchunk : npts;
       T* tf = (T*)a.tma_f;
-      for (int sp = 0; sp < ns; ++sp)
-        for (int q = 0; q < ns; ++q)
-          if (a.tma_fidx[sp][q] >= 0)
-            for (int64_t pt = q0 + tid; pt < q1; pt += kThreads)
-              tf[(size_t)a.tma_fidx[sp][q] * npts + pt] = (T)__ldg(a.op.diag[sp][q] + pt);
+      if (a.op.nfields > 0) {  // shared coupling fields: the planes are the fields
+        for (int f = 0; f < a.op.nfields; ++f)
+          for (int64_t pt = q0 + tid; pt < q1; pt += kThreads) tf[(size_t)f * npts + pt] = (T)__ldg(a.op.field[f] + pt);
+      } else {
+        for (int sp = 0; sp < ns; ++sp)
+          for (int q = 0; q < ns; ++q)
+            if (a.tma_fidx[sp][q] >= 0)
+              for (int64_t pt = q0 + tid; pt < q1; pt += kThreads)
+                tf[(size_t)a.tma_fidx[sp][q] * npts + pt] = (T)__ldg(a.op.diag[sp][q] + pt);
+      }
     }
     if (p > 0) {
       if (!finish_reduce<Team>(team, c, a.partials, parity, p)) goto stop;

@@ -72,7 +72,9 @@ def bc_code(desc: dict) -> int:
 
 class kiops_stencil2d_desc(C.Structure):
     _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nspecies", C.c_int), ("bc", C.c_int),
-                ("coef", (C.c_double * 5) * 2), ("diag", (C.c_void_p * 2) * 2)]
+                ("coef", (C.c_double * 5) * 2), ("diag", (C.c_void_p * 2) * 2), ("nfields", C.c_int),
+                ("dfield", (C.c_int * 2) * 2), ("dconst", (C.c_double * 2) * 2), ("dweight", (C.c_double * 2) * 2),
+                ("field", C.c_void_p * 2)]
 
 
 class kiops_stencil3d_desc(C.Structure):
@@ -411,9 +413,11 @@ def kiops_workspace_size(ctx, op, p, m_o, prec) -> int:
 
 # ---------------------------------------------------------------- torch convenience layer
 class Operator:
-    """A device operator built from a workload description (see workloads.py); owns its device arrays."""
+    """A device operator built from a workload description (see workloads.py); owns its device arrays.
+    A 2D description with "shared_fields" passes its coupling block in that form unless shared_fields is
+    False (then its "diag" entries are passed)."""
 
-    def __init__(self, solver: "Solver", desc: dict):
+    def __init__(self, solver: "Solver", desc: dict, shared_fields: bool = True):
         import torch
         self.solver = solver
         self.desc = desc
@@ -436,9 +440,20 @@ class Operator:
             for s in range(d.nspecies):
                 for c in range(5):
                     d.coef[s][c] = float(desc["coef"][s][c])
-            for (r, c), arr in desc.get("diag", {}).items():
-                if arr is not None:
-                    d.diag[r][c] = put(arr, torch.float64)
+            shared = desc.get("shared_fields") if shared_fields else None
+            if shared is not None:  # entries affine in fields that several entries share
+                d.nfields = len(shared["fields"])
+                for f, arr in enumerate(shared["fields"]):
+                    d.field[f] = put(arr, torch.float64)
+                for s in range(2):
+                    for c in range(2):
+                        d.dfield[s][c] = -1
+                for (r, c), (f, const, weight) in shared["entries"].items():
+                    d.dfield[r][c], d.dconst[r][c], d.dweight[r][c] = int(f), float(const), float(weight)
+            else:
+                for (r, c), arr in desc.get("diag", {}).items():
+                    if arr is not None:
+                        d.diag[r][c] = put(arr, torch.float64)
             self.handle = kiops_op_stencil2d(ctx, d)
         elif k == "stencil3d":
             d = kiops_stencil3d_desc()
@@ -509,8 +524,8 @@ class Solver:
         self.cfg = cfg
         return old
 
-    def operator(self, desc: dict) -> Operator:
-        return Operator(self, desc)
+    def operator(self, desc: dict, shared_fields: bool = True) -> Operator:
+        return Operator(self, desc, shared_fields)
 
     @staticmethod
     def _prec(precision) -> int:

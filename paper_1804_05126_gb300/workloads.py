@@ -10,7 +10,9 @@ An operator description is a plain dict:
 * ``{"kind": "stencil2d", "nx", "ny", "nspecies" (1|2), "periodic" (bool) or "bc" ("dirichlet" |
   "periodic" | "neumann"), "coef" (nspecies x 5:
   centre, -x, +x, -y, +y), "diag" {(r, c): float64 array of nx*ny}}`` — unknowns are species-blocked
-  ``[u; v]``, each x-fastest; ``diag[(r, c)]`` couples species c into species r pointwise.
+  ``[u; v]``, each x-fastest; ``diag[(r, c)]`` couples species c into species r pointwise.  Optionally
+  ``"shared_fields": {"fields": [float64 arrays of nx*ny], "entries": {(r, c): (field index or -1, const,
+  weight)}}``, the same block with entry (r, c) = const + weight * fields[index].
 * ``{"kind": "stencil3d", "nx", "ny", "nz", "periodic", "coef" (7: centre, -x, +x, -y, +y, -z, +z),
   "diag": float64 array of nx*ny*nz or None}``
 * ``{"kind": "dense", "n", "a" (n x n float64)}``
@@ -135,8 +137,13 @@ def gray_scott2d(n: int, rng: np.random.Generator, du: float = 2e-5, dv: float =
     coef = [[-4.0 * cu, cu, cu, cu, cu], [-4.0 * cv, cv, cv, cv, cv]]
     diag = {(0, 0): -(v0 * v0 + F), (0, 1): -2.0 * u0 * v0, (1, 0): v0 * v0,
             (1, 1): 2.0 * u0 * v0 - (F + k)}
+    # the same block from the two fields v0^2 and 2 u0 v0 that its entries share: entry (r, c) =
+    # const + weight * field (weights +-1, so each entry equals the one above exactly)
+    shared = {"fields": [v0 * v0, 2.0 * u0 * v0],
+              "entries": {(0, 0): (0, -F, -1.0), (0, 1): (1, 0.0, -1.0), (1, 0): (0, 0.0, 1.0),
+                          (1, 1): (1, -(F + k), 1.0)}}
     return {"kind": "stencil2d", "nx": n, "ny": n, "nspecies": 2, "periodic": True,
-            "coef": np.asarray(coef, dtype=np.float64), "diag": diag, "u0": u0, "v0": v0}
+            "coef": np.asarray(coef, dtype=np.float64), "diag": diag, "shared_fields": shared, "u0": u0, "v0": v0}
 
 
 def adr3d(n: int, shift: float, adv=(0.0, 0.0, 0.0), diff: float = 1.0) -> dict:

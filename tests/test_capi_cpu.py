@@ -65,3 +65,52 @@ def test_status_strings_and_null_handling(libpath):
     assert L.kiops_destroy(None) == 1          # EINVAL, no crash
     assert L.kiops_last_error(None) == b"NULL context"
     assert L.kiops_config_default(None) == 1
+
+
+MIRRORED = ["kiops_config", "kiops_stats", "kiops_trace_rec", "kiops_stencil2d_desc", "kiops_stencil3d_desc",
+            "kiops_server_config", "kiops_request", "kiops_pde", "kiops_integrate_stats"]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the Python binding mirrors has the header's size and member offsets (a C program built
+    with the host compiler prints them)."""
+    import shutil
+    import subprocess
+
+    from paper_1804_05126_gb300 import kiops
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kiops.h"', "int main(void) {"]
+    for name in MIRRORED:
+        cls = getattr(kiops, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        name, member, value = ln.split()
+        got[(name, member)] = int(value)
+    for name in MIRRORED:
+        cls = getattr(kiops, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_gray_scott_shared_fields_describe_the_same_block():
+    """The Gray-Scott workload's coupling block in its two forms: const + weight * field (weights +-1) gives
+    every entry of "diag" exactly."""
+    import numpy as np
+
+    from paper_1804_05126_gb300 import workloads as W
+    op = W.problem_gray_scott(n=48, seed=3).op
+    sh = op["shared_fields"]
+    assert len(sh["fields"]) == 2 and set(sh["entries"]) == set(op["diag"])
+    for rc, (f, const, weight) in sh["entries"].items():
+        assert np.array_equal(const + weight * sh["fields"][f], op["diag"][rc]), rc

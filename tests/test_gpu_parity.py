@@ -4,6 +4,8 @@ Bar: relative 2-norm difference <= 10 * tol for FP64 solves (the stated toleranc
 for the FP32-basis mode <= 10 * tol with tol the request's tolerance.  Decision traces (Krylov dimension
 of every iteration, accept/reject) are compared where both sides take the decisions in FP64.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -473,6 +475,111 @@ def test_tma_fixed_shape_kernel(n, bc, m_o):
     assert rel(wf, we) <= P.tol
     w_ref, _, _ = oracle_solve(P, m_o=m_o)
     assert rel(wf, w_ref) <= 10 * P.tol
+
+
+def _shared_field_problem(n, ns, seed, precision, tol):
+    """A 2D operator whose coupling block is given by shared fields, with weights other than +-1, an own entry
+    that is a constant alone and an off-diagonal entry that is a constant alone (two species; one species: a
+    reaction gamma + (-2 gamma) u0, Dirichlet).  "diag" holds the same entries written out by numpy in FP64
+    (const + weight * field), which the oracle reads."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    if ns == 2:
+        fields = [rng.uniform(0.0, 1.0, n * n), rng.uniform(0.0, 1.0, n * n)]
+        entries = {(0, 0): (0, -3.0, -2.5), (0, 1): (-1, 0.7, 0.0), (1, 0): (1, 0.0, 1.5), (1, 1): (-1, -4.0, 0.0)}
+        cu, cv = 2e-5 / (h * h), 1e-5 / (h * h)
+        coef = [[-4.0 * cu, cu, cu, cu, cu], [-4.0 * cv, cv, cv, cv, cv]]
+        bc = "periodic"
+    else:
+        fields = [W.smooth_field(rng, n, n, periodic=False)]
+        entries = {(0, 0): (0, 100.0, -200.0)}
+        d = 0.01 * (n + 1) ** 2
+        a = -10.0 * (n + 1) / 2.0
+        coef = [[-4.0 * d, d + a, d - a, d + a, d - a]]
+        bc = "dirichlet"
+    diag = {rc: (c + w * fields[f] if f >= 0 else np.full(n * n, c)) for rc, (f, c, w) in entries.items()}
+    op = {"kind": "stencil2d", "nx": n, "ny": n, "nspecies": ns, "bc": bc, "coef": np.asarray(coef),
+          "diag": diag, "shared_fields": {"fields": fields, "entries": entries}}
+    tau = 1.0 if ns == 2 else 1e-2
+    return W.Problem(f"shared_{ns}_{n}", op, rng.standard_normal((4, ns * n * n)), tau, tol, precision=precision)
+
+
+def test_shared_coupling_fields_write_the_same_entries():
+    """Gray-Scott's block given by its two shared fields (v0^2, 2 u0 v0; weights +-1) against the same block
+    given by its four entries: the operator writes the entries exactly (same bits), so A x and the FP64
+    solve are the same bits; with the FP32 basis on the staged tiles (both staged kernels, which form the
+    entries in FP32 from the two planes) within tol of the four-plane run, and within 10 tol of the oracle."""
+    P = W.problem_gray_scott(n=64, seed=13, precision="fp64", tol=1e-8, tau=1.0)
+    s = kiops.Solver(device=0)
+    sh, di = s.operator(P.op), s.operator(P.op, shared_fields=False)
+    x = torch.randn(P.n, dtype=torch.float64, device="cuda:0")
+    assert torch.equal(sh.apply(x), di.apply(x))
+    b = torch.as_tensor(P.b, device="cuda:0")
+    w_sh, st_sh = s.solve(sh, P.tau, b, P.tol, precision="fp64")
+    w_di, st_di = s.solve(di, P.tau, b, P.tol, precision="fp64")
+    assert torch.equal(w_sh, w_di) and st_sh["matvecs"] == st_di["matvecs"]
+    s.close()
+    P = W.problem_gray_scott(n=200, seed=14, precision="fp32_basis", tol=1e-6, tau=1.0)
+    w_ref, _, _ = oracle_solve(P)
+    for kw, path in ((dict(), 3), (dict(tma_fixed=0), 2)):
+        s = kiops.Solver(device=0, grid_blocks=3, **kw)
+        b = torch.as_tensor(P.b, device="cuda:0")
+        w_sh, st_sh = s.solve(s.operator(P.op), P.tau, b, P.tol, precision="fp32_basis")
+        w_di, st_di = s.solve(s.operator(P.op, shared_fields=False), P.tau, b, P.tol, precision="fp32_basis")
+        s.close()
+        assert st_sh["status"] == st_di["status"] == 0
+        assert st_sh["tile_path"] == st_di["tile_path"] == path
+        w_sh, w_di = w_sh.cpu().numpy(), w_di.cpu().numpy()
+        assert rel(w_sh, w_di) <= P.tol
+        assert rel(w_sh, w_ref) <= 10 * P.tol
+
+
+@pytest.mark.parametrize("ns,n", [(2, 192), (2, 200), (1, 256)])
+def test_shared_coupling_fields_general_blocks(ns, n):
+    """Shared-field blocks with general weights and constant-only entries, several tiles per block (3 blocks):
+    FP64 on the per-element tile path and the FP32 basis on the staged tiles (two species: the fixed-shape
+    kernel, ragged at n = 200; one species: the general kernel) against the oracle, which reads the entries
+    written out by numpy, within 10 tol; the FP64 run against the same block given by its entries up to
+    rounding (fma against two roundings per entry)."""
+    for prec, tol, path in (("fp64", 1e-8, 1), ("fp32_basis", 1e-6, 3 if ns == 2 else 2)):
+        P = _shared_field_problem(n, ns, seed=50 + n, precision=prec, tol=tol)
+        s = kiops.Solver(device=0, grid_blocks=3)
+        w, st = gpu_solve(s, P)
+        wd, std = gpu_solve(s, dataclasses.replace(P, op={k: v for k, v in P.op.items() if k != "shared_fields"}))
+        s.close()
+        w_ref, _, _ = oracle_solve(P)
+        assert st["status"] == std["status"] == 0
+        assert st["tile_path"] == path, (prec, st["tile_path"])
+        assert rel(w, w_ref) <= 10 * tol, prec
+        assert rel(w, wd) <= (1e-12 if prec == "fp64" else tol)
+
+
+def test_shared_coupling_fields_rejected_descriptors(solver):
+    """kiops_op_stencil2d refuses, with KIOPS_EINVAL: more than two shared fields, a NULL field, a field index
+    beyond nfields - 1, and diag given together with shared fields."""
+    n = 32
+    f = torch.rand(n * n, dtype=torch.float64, device="cuda:0")
+
+    def desc(nfields=1, fields=(f.data_ptr(), None), dfield=0, with_diag=False):
+        d = kiops.kiops_stencil2d_desc()
+        d.nx = d.ny = n
+        d.nspecies, d.bc = 1, kiops.BC_PERIODIC
+        d.coef[0][0] = -4.0
+        d.nfields = nfields
+        for k, ptr in enumerate(fields):
+            d.field[k] = ptr
+        d.dfield[0][0], d.dweight[0][0] = dfield, 1.0
+        if with_diag:
+            d.diag[0][0] = f.data_ptr()
+        return d
+
+    good = kiops.kiops_op_stencil2d(solver.ctx, desc())
+    kiops.kiops_op_destroy(good)
+    for bad in (desc(nfields=3), desc(fields=(None, None)), desc(dfield=1), desc(with_diag=True),
+                desc(dfield=-2)):
+        with pytest.raises(kiops.KiopsError) as e:
+            kiops.kiops_op_stencil2d(solver.ctx, bad)
+        assert e.value.status == 1
 
 
 def _two_species_strip(nx, ny, bc, seed):
