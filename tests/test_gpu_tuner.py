@@ -1,6 +1,6 @@
 """The launch-shape autotuner of single solves on the GPU: it times the candidate tile shapes of the 2D
-stencil step (and the per-element path), keeps the fastest, and the shapes change the result only through
-the order of partial sums."""
+stencil step (and the per-element path), keeps the fastest, and the tile shapes change the result only
+through the order of partial sums."""
 import json
 
 import numpy as np
@@ -18,7 +18,10 @@ from paper_1804_05126_gb300 import kiops, tune, workloads as W  # noqa: E402
 def test_solve_tuner_chooses_among_tile_shapes():
     """2048^2 Gray-Scott with the FP32 basis (several tiles per block, the staged path): four tile shapes and
     the per-element path are timed; re-timed afterwards, the tuner's choice is within 2 % of the fastest
-    candidate; every candidate's result agrees with the others within the solve's tolerance."""
+    candidate; the staged candidates agree with one another within the solve's tolerance (they differ in the
+    order of partial sums), and the per-element path within 10 tol, the FP32 basis's parity bar (it rounds the
+    coupling entries, written in FP64, to FP32, where the staged path forms them in FP32 from Gray-Scott's two
+    shared fields, so its rounding errors are not those of the staged runs)."""
     from paper_1804_05126_gb300 import build
     build.build()
     P = W.problem_gray_scott(n=2048)
@@ -39,5 +42,6 @@ def test_solve_tuner_chooses_among_tile_shapes():
     assert again[json.dumps(best, sort_keys=True)] <= 1.02 * min(again.values()), (best, again)
     ref = results[json.dumps(best, sort_keys=True)]
     for key, w in results.items():
-        assert np.linalg.norm(w - ref) <= P.tol * np.linalg.norm(ref), key
+        bar = P.tol if json.loads(key)["tma"] else 10 * P.tol
+        assert np.linalg.norm(w - ref) <= bar * np.linalg.norm(ref), key
     s.close()
