@@ -546,6 +546,12 @@ struct DotAcc<double> {
     for (int k = 0; k < kRegK; ++k) v[k] = 0.0;
   }
   __device__ __forceinline__ void add(int k, double a, double b) { v[k] = fma(a, b, v[k]); }
+  // the W products of one 16-byte item (the same as W calls of add)
+  template <int W>
+  __device__ __forceinline__ void add_item(int k, const double* a, const double* b) {
+#pragma unroll
+    for (int u = 0; u < W; ++u) v[k] = fma(a[u], b[u], v[k]);
+  }
   __device__ __forceinline__ void to_double(double (&out)[kRegK]) const {
 #pragma unroll
     for (int k = 0; k < kRegK; ++k) out[k] = v[k];
@@ -566,6 +572,22 @@ struct DotAcc<float> {
     const float se = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(pr, z));  // hi + pr = t + se exactly
     hi[k] = t;
     lo[k] = __fadd_rn(lo[k], __fadd_rn(se, pe));
+  }
+  // The W products of one 16-byte item (W = 4 consecutive points): their sum s is formed in FP32 by a
+  // chain of FMAs (at most W - 1 roundings, each relative to a partial sum of W terms), then added to
+  // (hi, lo) without error as above.  The sum's error is at most about (W - 1) u sum |a b| over the item,
+  // and these item errors do not grow with the number of items as a plain FP32 sum's would; it takes
+  // 11 FP32 operations per item instead of 10 per product.
+  template <int W>
+  __device__ __forceinline__ void add_item(int k, const float* a, const float* b) {
+    float s = __fmul_rn(a[0], b[0]);
+#pragma unroll
+    for (int u = 1; u < W; ++u) s = __fmaf_rn(a[u], b[u], s);
+    const float t = __fadd_rn(hi[k], s);
+    const float z = __fsub_rn(t, hi[k]);
+    const float se = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(s, z));
+    hi[k] = t;
+    lo[k] = __fadd_rn(lo[k], se);
   }
   __device__ __forceinline__ void to_double(double (&out)[kRegK]) const {
 #pragma unroll
@@ -1180,7 +1202,8 @@ __device__ __forceinline__ Aff4<T> tma_aff(const SolveArgs& a, int sp) {
 // in it, else from per-thread slots that cp.async copies fill before the tile's wait.
 // The loops take 16 bytes of consecutive points per item (tile widths are multiples of that): 128-bit
 // shared-memory loads and global stores, coefficients and B-block weights held in registers.  Per element
-// the arithmetic and its order are those of fused_st2d_tiles; the elements are accumulated in another order.
+// the arithmetic and its order are those of fused_st2d_tiles; the step's dots take each item's products as
+// one sum (DotAcc::add_item), accumulated in another order.
 // CTW, CTH, CNS, CP > 0 (CP >= 0) fix the tile shape, the species count and p at compile time (a kernel
 // instantiation of its own): the loop bounds, the shared-memory offsets and the B-block loop are then
 // constants, and a ragged tile at the grid's right or bottom edge runs the whole box with the points beyond
@@ -1472,31 +1495,26 @@ __device__ __forceinline__ void fused_st2d_tma(const SolveArgs& a, Ctl& c, int r
         {  // the step's dots
           Vec16<T> g;
           if (i0_l != j_l) g = ld16(fb + wslot0 * fst + bi);
+          T v0[W];
 #pragma unroll
-          for (int u = 0; u < W; ++u) {
-            const T v0 = (i0_l == j_l) ? ctr.e[u] : g.e[u];
-            acc.add(0, v0, out.e[u]);
-            acc.add(kChunk, ctr.e[u], v0);
-          }
+          for (int u = 0; u < W; ++u) v0[u] = (i0_l == j_l) ? ctr.e[u] : g.e[u];
+          acc.template add_item<W>(0, v0, out.e);
+          acc.template add_item<W>(kChunk, ctr.e, v0);
         }
         if (nwin_l > 1) {
           Vec16<T> g;
           if (i0_l + 1 != j_l) g = ld16(fb + wslot1 * fst + bi);
+          T v1[W];
 #pragma unroll
-          for (int u = 0; u < W; ++u) {
-            const T v1 = (i0_l + 1 == j_l) ? ctr.e[u] : g.e[u];
-            acc.add(1, v1, out.e[u]);
-            acc.add(kChunk + 1, ctr.e[u], v1);
-          }
+          for (int u = 0; u < W; ++u) v1[u] = (i0_l + 1 == j_l) ? ctr.e[u] : g.e[u];
+          acc.template add_item<W>(1, v1, out.e);
+          acc.template add_item<W>(kChunk + 1, ctr.e, v1);
         }
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-          if (nwin_l > 2) {  // i0 + 2 == j
-            acc.add(2, ctr.e[u], out.e[u]);
-            acc.add(kChunk + 2, ctr.e[u], ctr.e[u]);
-          }
-          acc.add(2 * kChunk, out.e[u], out.e[u]);
+        if (nwin_l > 2) {  // i0 + 2 == j
+          acc.template add_item<W>(2, ctr.e, out.e);
+          acc.template add_item<W>(kChunk + 2, ctr.e, ctr.e);
         }
+        acc.template add_item<W>(2 * kChunk, out.e, out.e);
       }
     }
     KIOPS_TICK(13);
@@ -1724,7 +1742,8 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
 // copied by 16-byte cp.async into per-thread slots before the tile's wait, so that their latency overlaps the
 // wait and the finalisation; further columns are read from global memory in the products.  v_j is finalised over the box in shared memory (lagged
 // normalisation: no separate normalise pass and no second grid barrier per step), its own points stored;
-// then x_{j+1} = A~ v_j on the own points, stored raw, and the step's dots.  Points outside the grid arrive as
+// then x_{j+1} = A~ v_j on the own points, stored raw, and the step's dots (each item's products as one sum,
+// DotAcc::add_item).  Points outside the grid arrive as
 // zeros (the Dirichlet value); for periodic or reflected boundaries the halo points the stencil reads there
 // (one face layer per side, no edges or corners) are filled after the finalisation from the box, where the
 // mapped point lies in it, else from global memory, finalised.
@@ -1986,31 +2005,26 @@ __device__ void fused_st3d_tma(const SolveArgs& a, Ctl& c, int rank, int nblk, i
         {  // the step's dots
           Vec16<T> g;
           if (i0_l != j_l) g = ld16(fb + wslot0 * fst + bi);
+          T v0[W];
 #pragma unroll
-          for (int u = 0; u < W; ++u) {
-            const T v0 = (i0_l == j_l) ? ctr.e[u] : g.e[u];
-            acc.add(0, v0, out.e[u]);
-            acc.add(kChunk, ctr.e[u], v0);
-          }
+          for (int u = 0; u < W; ++u) v0[u] = (i0_l == j_l) ? ctr.e[u] : g.e[u];
+          acc.template add_item<W>(0, v0, out.e);
+          acc.template add_item<W>(kChunk, ctr.e, v0);
         }
         if (nwin_l > 1) {
           Vec16<T> g;
           if (i0_l + 1 != j_l) g = ld16(fb + wslot1 * fst + bi);
+          T v1[W];
 #pragma unroll
-          for (int u = 0; u < W; ++u) {
-            const T v1 = (i0_l + 1 == j_l) ? ctr.e[u] : g.e[u];
-            acc.add(1, v1, out.e[u]);
-            acc.add(kChunk + 1, ctr.e[u], v1);
-          }
+          for (int u = 0; u < W; ++u) v1[u] = (i0_l + 1 == j_l) ? ctr.e[u] : g.e[u];
+          acc.template add_item<W>(1, v1, out.e);
+          acc.template add_item<W>(kChunk + 1, ctr.e, v1);
         }
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-          if (nwin_l > 2) {  // i0 + 2 == j
-            acc.add(2, ctr.e[u], out.e[u]);
-            acc.add(kChunk + 2, ctr.e[u], ctr.e[u]);
-          }
-          acc.add(2 * kChunk, out.e[u], out.e[u]);
+        if (nwin_l > 2) {  // i0 + 2 == j
+          acc.template add_item<W>(2, ctr.e, out.e);
+          acc.template add_item<W>(kChunk + 2, ctr.e, ctr.e);
         }
+        acc.template add_item<W>(2 * kChunk, out.e, out.e);
       }
     }
     KIOPS_TICK(13);
