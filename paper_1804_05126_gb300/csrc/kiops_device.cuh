@@ -546,6 +546,7 @@ struct DotAcc<double> {
     for (int k = 0; k < kRegK; ++k) v[k] = 0.0;
   }
   __device__ __forceinline__ void add(int k, double a, double b) { v[k] = fma(a, b, v[k]); }
+  __device__ __forceinline__ void add_sum(int k, double s) { v[k] += s; }
   // the W products of one 16-byte item (the same as W calls of add)
   template <int W>
   __device__ __forceinline__ void add_item(int k, const double* a, const double* b) {
@@ -572,6 +573,13 @@ struct DotAcc<float> {
     const float se = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(pr, z));  // hi + pr = t + se exactly
     hi[k] = t;
     lo[k] = __fadd_rn(lo[k], __fadd_rn(se, pe));
+  }
+  // s (a sum of products formed in FP32) added without error: TwoSum into (hi, lo)
+  __device__ __forceinline__ void add_sum(int k, float s) {
+    const float t = __fadd_rn(hi[k], s);
+    const float z = __fsub_rn(t, hi[k]);
+    lo[k] = __fadd_rn(lo[k], __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(s, z)));
+    hi[k] = t;
   }
   // The W products of one 16-byte item (W = 4 consecutive points): their sum s is formed in FP32 by a
   // chain of FMAs (at most W - 1 roundings, each relative to a partial sum of W terms), then added to
@@ -1655,6 +1663,26 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
         // A~ v_j on the own points and the step's dots; CACHE: B and coupling values from shared memory
         auto compute = [&](auto cache_tag) {
           constexpr bool CACHE = decltype(cache_tag)::value;
+          // FP32 basis: the products of up to kGroup of this thread's points are summed by FMAs in part[]
+          // and added to the float-float accumulators by one TwoSum (DotAcc::add_item's bound, per group)
+          constexpr bool kPart = sizeof(T) == 4;
+          constexpr int kGroup = 4;
+          T part[2 * kChunk + 1];
+#pragma unroll
+          for (int k = 0; k <= 2 * kChunk; ++k) part[k] = T(0);
+          int npart = 0;
+          auto dot = [&](int k, T x, T y) {
+            if constexpr (kPart) part[k] = fma(x, y, part[k]);
+            else acc.add(k, x, y);
+          };
+          auto flush = [&]() {
+#pragma unroll
+            for (int k = 0; k <= 2 * kChunk; ++k) {
+              acc.add_sum(k, part[k]);
+              part[k] = T(0);
+            }
+            npart = 0;
+          };
           TileWalk wk(tid, tw, th);
           for (int e = tid; e < E; e += kThreads, wk.next()) {
             const int sp = wk.s, ly = wk.y, lx = wk.x;
@@ -1696,19 +1724,23 @@ __device__ void fused_st2d_phase(const SolveArgs& a, Ctl& c, int rank, int nblk,
             }
             xo[r] = xv;
             const T v0 = (i0 == j) ? ctr : (rw0 ? q0[h] : w0[r]);
-            acc.add(0, v0, xv);
-            acc.add(kChunk, ctr, v0);
+            dot(0, v0, xv);
+            dot(kChunk, ctr, v0);
             if (nwin > 1) {
               const T v1 = (i0 + 1 == j) ? ctr : (rw1 ? q1[h] : w1[r]);
-              acc.add(1, v1, xv);
-              acc.add(kChunk + 1, ctr, v1);
+              dot(1, v1, xv);
+              dot(kChunk + 1, ctr, v1);
             }
             if (nwin > 2) {  // i0 + 2 == j
-              acc.add(2, ctr, xv);
-              acc.add(kChunk + 2, ctr, ctr);
+              dot(2, ctr, xv);
+              dot(kChunk + 2, ctr, ctr);
             }
-            acc.add(2 * kChunk, xv, xv);
+            dot(2 * kChunk, xv, xv);
+            if constexpr (kPart)
+              if (++npart == kGroup) flush();
           }
+          if constexpr (kPart)
+            if (npart > 0) flush();
         };
         if (a.cache_on) compute(std::true_type{});
         else compute(std::false_type{});
