@@ -629,9 +629,12 @@ def test_tma_3d_tiles_fp32(bc, n, m_o, p, field, blocks):
     finalised in shared memory, no separate normalise pass): each boundary treatment, orthogonalisation
     lengths 1 to 3, p = 0 (plain exponential), 3, 4 and 6 (B weights beyond the four held in registers), 52^3
     (ragged tiles along all three axes, and a pointwise reaction field staged as an own-point box), 48^3 over
-    3 blocks and 96^3 over the default grid.  Against the separate-normalise path (fuse_stencil off) within
-    tol and against the oracle within 10 tol; the kernel compiled for 32 x 8 x 4 tiles (the default) and the
-    general one (tma_fixed off) both."""
+    3 blocks and 96^3 over the default grid.  The kernel compiled for 32 x 8 x 4 tiles (the default) and the
+    general one (tma_fixed off) agree within tol (the same arithmetic per item, sums in another order); both
+    and the separate-normalise path (fuse_stencil off) against the oracle within 10 tol, and the staged
+    kernels against the separate path within 10 tol: the staged kernels add each item's four products as one
+    FP32 sum to the dot accumulators where the separate path splits every product, and FP32-basis results
+    that round differently differ at the level of their error against the oracle, not below tol."""
     op = dict(W.adr3d(n, -20.0, (5.0, -3.0, 7.0)), bc=bc)
     rng = np.random.default_rng(50 + 7 * p + n)
     if field:
@@ -645,9 +648,10 @@ def test_tma_3d_tiles_fp32(bc, n, m_o, p, field, blocks):
     (wf, sf), (wn, sn), (wg, sg) = out["staged"], out["general"], out["separate"]
     assert sf["status"] == 0 and sn["status"] == 0 and sg["status"] == 0
     assert sf["tile_path"] == 4 and sn["tile_path"] == 4 and sg["tile_path"] == 0
-    assert rel(wf, wg) <= P.tol and rel(wn, wg) <= P.tol
+    assert rel(wf, wn) <= P.tol
+    assert rel(wf, wg) <= 10 * P.tol and rel(wn, wg) <= 10 * P.tol
     w_ref, _, _ = oracle_solve(P, m_o=m_o)
-    assert rel(wf, w_ref) <= 10 * P.tol
+    assert rel(wf, w_ref) <= 10 * P.tol and rel(wn, w_ref) <= 10 * P.tol and rel(wg, w_ref) <= 10 * P.tol
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32_basis", 1e-6)])
