@@ -2582,8 +2582,9 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
         block_reduce_dots<T>(c, dacc, 2 * kChunk + 1, nwin);  // compact layout straight into blk
       } else if (nwin <= kChunk) {
         // single pass: R rows per thread in flight (four for FP32 3D stencils, else two), every load issued
-        // before the stores; the dots take the rows last to first.  (The two-row case keeps its own
-        // straight-line code: written as the R-row loop it ran 2.6 % slower on 160^3 FP64.)
+        // before the stores; the four-row case adds each dot's R products as one item (DotAcc::add_item),
+        // the two-row case takes the rows last to first.  (The two-row case keeps its own straight-line
+        // code: written as the R-row loop it ran 2.6 % slower on 160^3 FP64.)
         constexpr int R = (KIND == OP_ST3D && sizeof(T) == 4) ? 4 : 2;
         DotAcc<T> dacc;
         dacc.zero();
@@ -2655,24 +2656,18 @@ __device__ void solve_body(const SolveArgs& a, Team& team, Ctl& c, double* smem_
 #pragma unroll
             for (int q = 0; q < R; ++q)
               if (has[q]) xo[rb + (int64_t)q * kThreads] = xr[q];
-#pragma unroll
-            for (int q = R - 1; q >= 0; --q) dacc.add(0, w0q[q], xr[q]);
-#pragma unroll
-            for (int q = R - 1; q >= 0; --q) dacc.add(kChunk, vq[q], w0q[q]);
+            // the pass's R rows as one item of the dot accumulators (rows beyond r1 hold zeros)
+            dacc.template add_item<R>(0, w0q, xr);
+            dacc.template add_item<R>(kChunk, vq, w0q);
             if (nwin > 1) {
-#pragma unroll
-              for (int q = R - 1; q >= 0; --q) dacc.add(1, w1q[q], xr[q]);
-#pragma unroll
-              for (int q = R - 1; q >= 0; --q) dacc.add(kChunk + 1, vq[q], w1q[q]);
+              dacc.template add_item<R>(1, w1q, xr);
+              dacc.template add_item<R>(kChunk + 1, vq, w1q);
             }
             if (nwin > 2) {
-#pragma unroll
-              for (int q = R - 1; q >= 0; --q) dacc.add(2, w2q[q], xr[q]);
-#pragma unroll
-              for (int q = R - 1; q >= 0; --q) dacc.add(kChunk + 2, vq[q], w2q[q]);
+              dacc.template add_item<R>(2, w2q, xr);
+              dacc.template add_item<R>(kChunk + 2, vq, w2q);
             }
-#pragma unroll
-            for (int q = R - 1; q >= 0; --q) dacc.add(2 * kChunk, xr[q], xr[q]);
+            dacc.template add_item<R>(2 * kChunk, xr, xr);
           }
         } else {
           for (int64_t rA = r0 + tid; rA < r1; rA += 2 * kThreads) {
