@@ -1113,9 +1113,10 @@ __device__ __forceinline__ void fused_st2d_tiles(const SolveArgs& a, Ctl& c, int
             if (nwin > 1 && i0 + 1 != j) g1v[u] = w1[r];
           }
         }
-        // the batch's U elements are one item of the dot accumulators (DotAcc::add_item: one FP32 sum per
-        // dot with an FP32 basis; with FP64 the same fused multiply-adds in the same order per dot as one by
-        // one); elements beyond E contribute zeros
+        // FP32 basis: the batch's U elements are one item of the dot accumulators (DotAcc::add_item, one
+        // FP32 sum per dot; elements beyond E contribute zeros).  FP64: each element's products are added
+        // as they come (the order of fused_st2d_phase's one-tile loop).
+        constexpr bool kItem = sizeof(T) == 4;
         T xq[U], cq[U], v0q[U], v1q[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -1140,23 +1141,41 @@ __device__ __forceinline__ void fused_st2d_tiles(const SolveArgs& a, Ctl& c, int
               if (t < p) xv = fma(nt[t], bv[u][t], xv);
             for (int t = kB; t < p; ++t) xv = fma(nt[t], bcol<T>(a, t, r), xv);
             xo[r] = xv;
-            xq[u] = xv;
-            cq[u] = ctr;
-            v0q[u] = (i0 == j) ? ctr : g0v[u];
-            if (nwin > 1) v1q[u] = (i0 + 1 == j) ? ctr : g1v[u];
+            const T v0 = (i0 == j) ? ctr : g0v[u];
+            const T v1 = (nwin > 1 && i0 + 1 != j) ? g1v[u] : ctr;
+            if constexpr (kItem) {
+              xq[u] = xv;
+              cq[u] = ctr;
+              v0q[u] = v0;
+              v1q[u] = nwin > 1 ? v1 : T(0);
+            } else {
+              acc.add(0, v0, xv);
+              acc.add(kChunk, ctr, v0);
+              if (nwin > 1) {
+                acc.add(1, v1, xv);
+                acc.add(kChunk + 1, ctr, v1);
+              }
+              if (nwin > 2) {  // i0 + 2 == j
+                acc.add(2, ctr, xv);
+                acc.add(kChunk + 2, ctr, ctr);
+              }
+              acc.add(2 * kChunk, xv, xv);
+            }
           }
         }
-        acc.template add_item<U>(0, v0q, xq);
-        acc.template add_item<U>(kChunk, cq, v0q);
-        if (nwin > 1) {
-          acc.template add_item<U>(1, v1q, xq);
-          acc.template add_item<U>(kChunk + 1, cq, v1q);
+        if constexpr (kItem) {
+          acc.template add_item<U>(0, v0q, xq);
+          acc.template add_item<U>(kChunk, cq, v0q);
+          if (nwin > 1) {
+            acc.template add_item<U>(1, v1q, xq);
+            acc.template add_item<U>(kChunk + 1, cq, v1q);
+          }
+          if (nwin > 2) {  // i0 + 2 == j
+            acc.template add_item<U>(2, cq, xq);
+            acc.template add_item<U>(kChunk + 2, cq, cq);
+          }
+          acc.template add_item<U>(2 * kChunk, xq, xq);
         }
-        if (nwin > 2) {  // i0 + 2 == j
-          acc.template add_item<U>(2, cq, xq);
-          acc.template add_item<U>(kChunk + 2, cq, cq);
-        }
-        acc.template add_item<U>(2 * kChunk, xq, xq);
       }
     }
     KIOPS_TICK(13);
