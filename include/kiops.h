@@ -178,9 +178,10 @@ enum { KIOPS_BC_DIRICHLET = 0, KIOPS_BC_PERIODIC = 1, KIOPS_BC_NEUMANN = 2 };
  * The Gray-Scott Jacobian of section 4 has this form with the two fields v0^2 and 2 u0 v0 (entries
  * -F - v0^2, -2 u0 v0, v0^2 and 2 u0 v0 - (F + k)).  The operator writes the entries once into device
  * memory it owns (8 bytes per point and nonzero entry, freed by kiops_op_destroy) for the paths that read
- * whole entries; the staged several-tiles step with an FP32 basis (kiops_stats.tile_path 2 or 3) reads the
- * nfields planes instead, and forms the entries in FP32 (so its results differ from those of the same block
- * given by diag by the FP32 rounding of the entries).  Errors: KIOPS_EINVAL for nfields outside 0..2, a
+ * whole entries; the staged several-tiles step (kiops_stats.tile_path 2 or 3, by default with an FP32
+ * basis only) reads the nfields planes instead and forms the entries in the basis precision (with an FP32
+ * basis its results differ from those of the same block given by diag by the FP32 rounding of the
+ * entries).  Errors: KIOPS_EINVAL for nfields outside 0..2, a
  * NULL field, diag given as well, or dfield outside -1..nfields-1 on an entry of the block; KIOPS_ENOMEM
  * or KIOPS_ECUDA if the entries cannot be allocated or written. */
 typedef struct {
