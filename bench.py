@@ -449,6 +449,16 @@ def measure_served_config5(dev, count=48):
 STEP_PHASES = (2, 3, 4, 5, 11, 12, 13, 14, 15)  # phase counters of the Krylov step (kiops_stats.phase_cycles)
 
 
+def beyond_l2_bytes(P, s_bytes: int, planes: int):
+    """Algorithmic bytes of one Krylov step on a stencil grid: (p + 3) s N for v_j, v_{j-1}, the p columns of B
+    and v_{j+1}, plus `planes` pointwise field planes of one grid point each (s bytes a point); and the bytes
+    of the one-barrier schedule (lagged normalisation), which also reads the second finalisation-window vector
+    and writes v_j: two more vectors."""
+    npts = P.n // int(P.op.get("nspecies", 1))
+    model = (P.p + 3) * s_bytes * P.n + planes * s_bytes * npts
+    return model, model + 2 * s_bytes * P.n
+
+
 def measure_beyond_l2(dev):
     """The Krylov step on grids whose step working set exceeds the 129 MB L2: 2048^2 Gray-Scott with the FP32
     basis (N = 8.4 M), 2048^2 ADR in FP64 (N = 4.2 M, tau = 1e-2 / 16 so that the Krylov work stays near
@@ -494,12 +504,9 @@ def measure_beyond_l2(dev):
         cyc = pst["phase_cycles"]
         share = sum(cyc[k] for k in STEP_PHASES) / max(1, sum(cyc))
         step_us = 1e3 * ms * share / st["matvecs"]
-        npts = P.n // int(P.op.get("nspecies", 1))
-        bytes_step = (P.p + 3) * s_bytes * P.n + planes * s_bytes * npts
+        bytes_step, one_barrier = beyond_l2_bytes(P, s_bytes, planes)
         gbs = bytes_step / (step_us * 1e-6) / 1e9
-        # the one-barrier schedule (lagged normalisation, every tiled path) also reads the second
-        # finalisation-window vector and writes v_j besides x_{j+1}
-        lagged = (bytes_step + 2 * s_bytes * P.n) if st["tile_path"] > 0 else None
+        lagged = one_barrier if st["tile_path"] > 0 else None  # every tiled path runs the one-barrier schedule
         res[name] = {"N": P.n, "p": P.p, "ms_per_solve": ms, "matvecs": st["matvecs"], "substeps": st["substeps"],
                      "step_us": step_us, "step_share_of_solve": share, "bytes_per_step": bytes_step,
                      "step_gbs": gbs, "step_hbm_frac": gbs / hbm,
