@@ -634,7 +634,10 @@ def run_gpu(args):
         "engine": {"blocks": st["grid_blocks"], "kind": "grid (persistent cooperative)"},
     }
     if world == 1 and not args.no_patterns:
-        out["patterns"] = measure_patterns(dev)
+        try:
+            out["patterns"] = measure_patterns(dev)
+        except Exception as e:  # a failing secondary measurement must not take the headline line with it
+            out["patterns"] = {"error": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(P)
     print(json.dumps(out), flush=True)
